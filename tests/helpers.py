@@ -1,0 +1,97 @@
+"""Small hand-built models for the pins (test infrastructure)."""
+import math
+
+import numpy as np
+
+from paper_1711_07999_gb300 import synth
+
+
+def dq_trans(t):
+    return [1.0, 0.0, 0.0, 0.0, 0.0, t[0] / 2, t[1] / 2, t[2] / 2]
+
+
+def make_model(parent, jtype, axis, offsets_t, verts, tris, bone_idx, bone_w, W=32, H=24, fx=30.0, fy=30.0,
+               cx=None, cy=None, prior_mask=None, **params):
+    L = len(parent)
+    sk = dict(parent=np.array(parent, np.int32), type=np.array(jtype, np.int32),
+              axis=np.array(axis, np.float32).reshape(L, 3),
+              offset_dq=np.array([dq_trans(t) for t in offsets_t], np.float32),
+              prior_mask=np.array(prior_mask if prior_mask is not None else [1.0] * L, np.float32))
+    mesh = dict(verts=np.array(verts, np.float32).reshape(-1, 3), tris=np.array(tris, np.int32).reshape(-1, 3),
+                bone_idx=np.array(bone_idx, np.uint8).reshape(-1, 4), bone_w=np.array(bone_w, np.float32).reshape(-1, 4))
+    cam = dict(width=W, height=H, fx=fx, fy=fy, cx=W / 2 if cx is None else cx, cy=H / 2 if cy is None else cy)
+    p = synth.default_params(fx, len(mesh["verts"]))
+    p.update(params)
+    return dict(skeleton=sk, mesh=mesh, camera=cam, params=p)
+
+
+def grid_patch(nx, ny, x0, x1, y0, y1, z, facing_camera=True):
+    """Planar grid at depth z; triangles CCW seen from the camera side when facing_camera."""
+    xs = np.linspace(x0, x1, nx)
+    ys = np.linspace(y0, y1, ny)
+    V = np.array([[x, y, z] for y in ys for x in xs])
+    T = []
+    for j in range(ny - 1):
+        for i in range(nx - 1):
+            a, b, c, d = j * nx + i, j * nx + i + 1, (j + 1) * nx + i, (j + 1) * nx + i + 1
+            if facing_camera:  # camera looks +z, y down: outward normal -z
+                T += [(a, c, b), (b, c, d)]
+            else:
+                T += [(a, b, c), (b, d, c)]
+    return V, np.array(T)
+
+
+def rot_matrix(axis, ang):
+    """Rodrigues' formula."""
+    k = np.asarray(axis, float)
+    k = k / np.linalg.norm(k)
+    Kx = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(ang) * Kx + (1 - math.cos(ang)) * Kx @ Kx
+
+
+def dq_to_matrix(h):
+    """Unit dual quaternion (w,x,y,z | w,x,y,z) -> 4x4 homogeneous matrix (rotation of the real part,
+    translation 2 q_d q_r^*)."""
+    w, x, y, z = h[:4]
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    qd = np.array(h[4:])
+    qr_conj = np.array([w, -x, -y, -z])
+    a, b = qd, qr_conj
+    t = np.array([a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                  a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                  a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]]) * 2
+    M = np.eye(4)
+    M[:3, :3] = R
+    M[:3, 3] = t
+    return M
+
+
+def chain_matrices(parent, jtype, axis, offsets_t, theta):
+    """Textbook forward kinematics with 4x4 matrices: M_j = M_parent T(offset) J(theta_j)."""
+    L = len(parent)
+    M = [None] * L
+    for j in range(L):
+        Mp = np.eye(4) if parent[j] < 0 else M[parent[j]]
+        T = np.eye(4)
+        T[:3, 3] = offsets_t[j]
+        Jm = np.eye(4)
+        if jtype[j] == 0:
+            Jm[:3, :3] = rot_matrix(axis[j], theta[j])
+        else:
+            Jm[:3, 3] = np.asarray(axis[j], float) * theta[j]
+        M[j] = Mp @ T @ Jm
+    return M
+
+
+def random_tree(rng, L=6, prism_every=3):
+    parent = [-1] + [int(rng.integers(0, j)) for j in range(1, L)]
+    jtype = [1 if (j % prism_every == 2) else 0 for j in range(L)]
+    axis = []
+    for _ in range(L):
+        a = rng.normal(size=3)
+        axis.append(a / np.linalg.norm(a))
+    offs = [rng.uniform(-0.3, 0.3, 3) for _ in range(L)]
+    offs[0] = np.array([0.0, 0.0, 2.0])
+    return parent, jtype, axis, offs

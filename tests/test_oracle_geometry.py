@@ -1,0 +1,242 @@
+"""Pins of the oracle's normals (R4), z-buffer (R5, R6), visibility (R7), projective association
+(Sec. 4.1 with R8, R9), neighbourhoods N(i) (Sec. 4.3, R16) and prior weights S (Sec. 4.2, R10), against
+brute force, closed forms and special cases."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_07999_gb300 import synth
+from tests import helpers as H
+
+
+def test_flat_grid_has_constant_normal():
+    V, T = H.grid_patch(6, 5, -0.2, 0.2, -0.1, 0.1, 2.0)
+    n, ok = oracle.normals(V, T)
+    assert ok.all()
+    assert np.allclose(n, [0, 0, -1], atol=1e-15)
+
+
+def test_capsule_normals_are_radial_within_mesh_spacing():
+    m = synth.make_model(1)
+    v = m["mesh"]["verts"].astype(np.float64)
+    n, ok = oracle.normals(v, m["mesh"]["tris"])
+    n0 = m["motion"]["bind_normals"]
+    cosang = np.einsum("ij,ij->i", n, n0)
+    assert ok.all()
+    # outward orientation everywhere, deviation of the order of the spacing / radius
+    assert cosang.min() > 0.9
+    assert np.median(cosang) > 0.995
+
+
+def _mt_depth(orig_dir, A, B, C):
+    """Moller-Trumbore: ray (0, d) against triangle ABC; returns hit distance along d or None."""
+    d = orig_dir
+    e1, e2 = B - A, C - A
+    p = np.cross(d, e2)
+    det = e1 @ p
+    if abs(det) < 1e-15:
+        return None
+    inv = 1.0 / det
+    s = -A
+    u = (s @ p) * inv
+    q = np.cross(s, e1)
+    v = (d @ q) * inv
+    if u < -1e-12 or v < -1e-12 or u + v > 1 + 1e-12:
+        return None
+    t = (e2 @ q) * inv
+    return t if t > 0 else None
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_raster_equals_brute_force_ray_casting(seed):
+    rng = np.random.default_rng(seed)
+    W, Hh, fx, fy, cx, cy = 24, 18, 20.0, 20.0, 12.0, 9.0
+    tris, verts = [], []
+    for f in range(12):
+        c = rng.uniform([-0.8, -0.6, 1.5], [0.8, 0.6, 3.0])
+        pts = c + rng.normal(0, 0.25, (3, 3))
+        verts.extend(pts)
+        tris.append([3 * f, 3 * f + 1, 3 * f + 2])
+    v = np.array(verts)
+    z, zt, amb = oracle.raster(W, Hh, fx, fy, cx, cy, 0.05, v, tris, with_amb=True)
+    for py in range(Hh):
+        for px in range(W):
+            d = np.array([(px - cx) / fx, (py - cy) / fy, 1.0])
+            best, bt = math.inf, -1
+            for f, (a, b, c) in enumerate(tris):
+                t = _mt_depth(d, v[a], v[b], v[c])
+                if t is not None and t < best:
+                    best, bt = t, f
+            if amb[py, px]:
+                continue  # coverage decided at rounding level
+            if bt < 0:
+                assert not np.isfinite(z[py, px])
+            else:
+                assert z[py, px] == pytest.approx(best, rel=1e-12)
+                assert zt[py, px] == bt
+
+
+def test_fronto_parallel_quad_has_constant_depth():
+    V, T = H.grid_patch(2, 2, -0.5, 0.5, -0.4, 0.4, 2.5)
+    z, zt, _ = oracle.raster(40, 30, 30.0, 30.0, 20.0, 15.0, 0.05, V, T)
+    covered = np.isfinite(z)
+    assert covered.sum() > 100
+    assert np.all(z[covered] == 2.5)
+
+
+def test_tilted_plane_depth_closed_form():
+    # plane z = z0 + a x: along the ray (u, v, 1) s, depth = z0 / (1 - a u)
+    z0, a = 2.0, 0.3
+    V = np.array([[-0.6, -0.5, z0 - 0.6 * a], [0.6, -0.5, z0 + 0.6 * a], [-0.6, 0.5, z0 - 0.6 * a],
+                  [0.6, 0.5, z0 + 0.6 * a]])
+    T = [[0, 2, 1], [1, 2, 3]]
+    W, Hh, f = 40, 30, 30.0
+    z, _, _ = oracle.raster(W, Hh, f, f, 20.0, 15.0, 0.05, V, T)
+    for py in range(Hh):
+        for px in range(W):
+            if np.isfinite(z[py, px]):
+                u = (px - 20.0) / f
+                assert z[py, px] == pytest.approx(z0 / (1 - a * u), rel=1e-12)
+
+
+def test_visibility_occlusion_backface_and_image_bounds():
+    front, Tf = H.grid_patch(5, 5, -0.2, 0.2, -0.2, 0.2, 2.0)
+    back, Tb = H.grid_patch(5, 5, -0.2, 0.2, -0.2, 0.2, 2.5)
+    away, Ta = H.grid_patch(3, 3, 0.3, 0.5, -0.1, 0.1, 2.0, facing_camera=False)
+    outside = np.array([[5.0, 0, 2.0], [5.1, 0, 2.0], [5.0, 0.1, 2.0]])
+    verts = np.concatenate([front, back, away, outside])
+    tris = np.concatenate([Tf, Tb + 25, Ta + 50, [[59, 61, 60]]])
+    nV = len(verts)
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, tris, [[0, 0, 0, 0]] * nV, [[1, 0, 0, 0]] * nV,
+                     W=40, H=40, fx=40.0, fy=40.0)
+    o = oracle.Oracle(m)
+    v, _ = o.skin([0.0])
+    n, ok = o.normals(v)
+    z, zt, _ = o.raster(v)
+    vis, pix, _ = o.visibility(v, n, ok, z)
+    assert vis[:25].all()                  # front plane visible
+    assert not vis[25:50].any()            # hidden 0.5 m behind it (> eps_vis)
+    assert not vis[50:59].any()            # facing away from the camera
+    assert not vis[59:].any()              # projects outside the image
+
+
+def _bruteforce_assoc(o, v, vis, pix, depth, R):
+    """Every pixel against every visible vertex whose bucket lies in the window (vectorised over vertices)."""
+    W, Hh = o.W, o.H
+    tau2 = o.params["cutoff"] ** 2
+    corr = -np.ones((Hh, W), int)
+    pu, pv = pix % W, pix // W
+    idx = np.arange(o.V)
+    for py in range(Hh):
+        for px in range(W):
+            d = float(depth[py, px])
+            if d <= 0:
+                continue
+            p = np.array([(px - o.cx) * d / o.fx, (py - o.cy) * d / o.fy, d])
+            cand = (vis > 0) & (np.abs(pu - px) <= R) & (np.abs(pv - py) <= R)
+            if not cand.any():
+                continue
+            dd = ((p - v[cand]) ** 2).sum(1)
+            ok = dd <= tau2
+            if not ok.any():
+                continue
+            ii, dd = idx[cand][ok], dd[ok]
+            corr[py, px] = ii[np.lexsort((ii, dd))[0]]
+    return corr
+
+
+@pytest.mark.parametrize("R", [1, 3, 50])
+def test_association_equals_brute_force(R):
+    m = synth.make_model(1, V=1500, width=64, height=48)
+    m["params"]["window_half"] = R
+    o = oracle.Oracle(m)
+    th = synth.gt_theta(m, 0)
+    z = o.render(th)
+    depth = synth.add_noise(z, 1, np.random.default_rng(5))
+    th2 = th + np.radians(1) * np.random.default_rng(6).normal(size=o.L)
+    P = o.pass_at(th2, None, depth)
+    ref = _bruteforce_assoc(o, P["v"], P["vis"], P["pix"], depth, R)
+    assert np.array_equal(P["corr"], ref)
+    assert (ref >= 0).sum() > 20
+    # per-vertex sums of Sec. 4.1
+    acc, cnt = o.accumulate(P["v"], depth, ref)
+    assert np.array_equal(cnt, P["cnt"]) and np.allclose(acc, P["acc"], atol=1e-15)
+
+
+def test_single_vertex_collects_every_pixel_within_cutoff():
+    verts = np.array([[0.0, 0.0, 2.0], [0.01, 0.0, 2.0], [0.0, 0.01, 2.0]])
+    # only vertex 0 is visible: give vertices 1, 2 a degenerate face so their normals are invalid
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 2, 1]], [[0, 0, 0, 0]] * 3, [[1, 0, 0, 0]] * 3,
+                     W=30, H=30, fx=200.0, fy=200.0, window_half=30, cutoff=0.05)
+    o = oracle.Oracle(m)
+    v, _ = o.skin([0.0])
+    n, ok = o.normals(v)
+    vis = np.array([1, 0, 0], np.int32)
+    u = int(math.floor(200 * 0 / 2 + 15 + 0.5))
+    pix = np.array([15 * 30 + u, -1, -1], np.int32)
+    depth = np.full((30, 30), 2.02, np.float32)
+    corr, acc, cnt, _ = o.associate(v, vis, pix, depth)
+    for py in range(30):
+        for px in range(30):
+            p = np.array([(px - 15) * 2.02 / 200, (py - 15) * 2.02 / 200, 2.02])
+            within = np.linalg.norm(p - v[0]) <= 0.05
+            assert corr[py, px] == (0 if within else -1)
+    assert cnt[0] == (corr == 0).sum()
+
+
+def test_association_ties_go_to_smaller_index():
+    verts = np.array([[-0.01, 0.0, 2.0], [0.01, 0.0, 2.0], [0.0, 0.2, 2.0]])
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 2, 1]], [[0, 0, 0, 0]] * 3, [[1, 0, 0, 0]] * 3,
+                     W=31, H=31, fx=100.0, fy=100.0, window_half=5, cutoff=0.05)
+    o = oracle.Oracle(m)
+    v = verts.astype(np.float64)
+    vis = np.array([1, 1, 0], np.int32)
+    pix = np.array([15 * 31 + 15, 15 * 31 + 16, -1], np.int32)
+    depth = np.zeros((31, 31), np.float32)
+    depth[15, 15] = 2.0  # p = (0, 0, 2): equidistant from vertices 0 and 1
+    corr, *_ = o.associate(v, vis, pix, depth)
+    assert corr[15, 15] == 0
+
+
+def test_knn_equals_brute_force():
+    m = synth.make_model(1, V=800)
+    o = oracle.Oracle(m)
+    _, _, nbr = o.derived()
+    v = m["mesh"]["verts"].astype(np.float64)
+    for i in range(0, o.V, 7):
+        d2 = ((v - v[i]) ** 2).sum(1)
+        d2[i] = np.inf
+        order = np.lexsort((np.arange(o.V), d2))[:4]
+        assert list(nbr[i]) == list(order)
+
+
+def test_knn_ties_on_a_regular_grid_go_to_smaller_index():
+    V, T = H.grid_patch(4, 4, 0.0, 0.3, 0.0, 0.3, 2.0)
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], V, T, [[0, 0, 0, 0]] * 16, [[1, 0, 0, 0]] * 16)
+    o = oracle.Oracle(m)
+    _, _, nbr = o.derived()
+    assert list(nbr[5]) == [1, 4, 6, 9]   # interior vertex: its four axis neighbours, by index
+    assert list(nbr[0]) == [1, 4, 5, 2]   # corner: two at h, then sqrt(2) h, then 2h (index 2 < 8)
+
+
+def test_prior_weights_count_subtree_vertices():
+    m = synth.make_model(1, V=900)
+    o = oracle.Oracle(m)
+    _, S, _ = o.derived()
+    sk = m["skeleton"]
+    L, V = len(sk["parent"]), o.V
+    anc = [[j] for j in range(L)]
+    for j in range(L):
+        k = sk["parent"][j]
+        while k >= 0:
+            anc[j].append(k)
+            k = sk["parent"][k]
+    for k in range(L):
+        n_k = 0
+        for i in range(V):
+            links = {int(j) for j, w in zip(m["mesh"]["bone_idx"][i], m["mesh"]["bone_w"][i]) if w > 0}
+            if any(k in anc[j] for j in links):
+                n_k += 1
+        assert S[k] == pytest.approx(float(sk["prior_mask"][k]) * n_k / V, rel=1e-15)
