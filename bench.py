@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Benchmark of the tracker on the 50k-vertex humanoid / 640x480 depth workload (one tracking session
+per GPU, a seeded synthetic 30 fps sequence; one step = one frame = 10 pose LM iterations + 2 shape
+iterations through the whole hot path).
+
+Prints one JSON line (rank 0):
+  value      frames/s over all ranks, device-timed (CUDA events on the launching stream) with the depth
+             frames already resident in HBM; L2 is flushed (a 256 MiB write) before every frame, outside
+             the timed intervals
+  latency    p50 / p99 per-frame device time, and p50 / p99 of the end-to-end call
+  e2e        frames/s through trk_track_frame with host (pinned) depth: H2D of the frame and D2H of
+             Theta, Phi and the energies inside the timed region
+  roofline   the dominant kernel's achieved rate against the measured peak of MEASURED_PEAKS.json
+  cpu_baseline  the FP64 oracle on the host, one core, a bounded sample of the same sequence
+--impl reference times the oracle itself (on host cores) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s and p99 frame latency, 50k-vert/640x480, batched vs plain, same GPU"
+WORKLOAD = "humanoid-22bone-55dof-50k-vert-640x480-30fps-sinusoidal"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), bf16=float(p["bf16_tflops"]), src="measured")
+    except (OSError, KeyError, ValueError):
+        return dict(hbm_gbs=6800.0, bf16=1900.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# algorithmic work per launch of each stage (bytes a minimal implementation must move / flops)
+# ------------------------------------------------------------------------------------------------
+def algorithmic(stage, V, F, npx, NP, nvis, nassoc_px, nA, n_valid_px, nblk):
+    if stage == "skin":  # v0, phi, bone idx, bone w in; v out; z-buffer, bucket heads, sums cleared
+        return "hbm", V * (16 + 16 + 4 + 16 + 16 + 32) + npx * (8 + 4)
+    if stage == "raster":  # triangles, posed vertices, face normals out, covered z-buffer words
+        return "hbm", F * (16 + 16) + V * 16 + n_valid_px * 8
+    if stage == "visibility":  # CSR, face normals, v, normals out, z-buffer probes, bucket records
+        return "hbm", V * (4 + 16 + 16 + 4) + 3 * F * 4 + F * 16 + nvis * (8 + 4 + 16)
+    if stage == "associate":  # depth in, corr out, bucket heads, visible records, per-vertex sums
+        return "hbm", npx * (4 + 4 + 4) + nvis * 16 + nassoc_px * 32
+    if stage == "resid_jtj":  # per-vertex streams in, block partials out
+        return "hbm", V * (32 + 16 + 4 + 16 + 16 + 16 + 16) + nblk * NP * NP * 4
+    if stage == "reduce":
+        return "hbm", nblk * NP * NP * 4 + NP * NP * 8
+    if stage == "lm_eval":
+        return "hbm", V * (32 + 16 + 16 + 16 + 16 + 4 + 16)
+    if stage == "shape":
+        return "hbm", V * (16 * 4 + 32 + 16 + 4 + 16 + 16 + 16 + 16)
+    if stage == "lm_solve":  # 6 FP64 Cholesky factorisations + solves of the P x P system
+        P = NP - 1
+        return "fp64", 6 * (P ** 3 / 3.0 + 2 * P * P)
+    return None, 0
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1711_07999_gb300", "csrc")
+    for n in sorted(os.listdir(csrc)):
+        if n.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, n), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it was captured from the
+    current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    e = t.get("kernels", {}).get(kernel)
+    return None if e is None else e.get("dram_bytes_per_launch_full_size")
+
+
+# ------------------------------------------------------------------------------------------------
+def render_sequence(model, session, n_frames, seed):
+    from paper_1711_07999_gb300 import synth
+    rng = np.random.default_rng(seed)
+    frames = np.empty((n_frames, model["camera"]["height"], model["camera"]["width"]), np.float32)
+    for f in range(n_frames):
+        t = f / 30.0
+        z = session.render_depth(synth.gt_theta(model, t), synth.gt_offsets(model, t))
+        frames[f] = synth.add_noise(z, 2, rng)
+    return frames
+
+
+def oracle_frames(model, n_frames, seed):
+    import oracle
+    from paper_1711_07999_gb300 import synth
+    o = oracle.Oracle(model)
+    rng = np.random.default_rng(seed)
+    frames = []
+    for f in range(n_frames):
+        t = f / 30.0
+        frames.append(synth.add_noise(o.render(synth.gt_theta(model, t), synth.gt_offsets(model, t)), 2, rng))
+    return o, frames
+
+
+def cpu_baseline(model, n_frames):
+    """The oracle as it stands, single-threaded FP64, on the first n_frames of the sequence."""
+    from paper_1711_07999_gb300 import synth
+    o, frames = oracle_frames(model, n_frames, seed=synth.seed_for(2, 900))
+    o.set_state(synth.gt_theta(model, 0.0), None)
+    t0 = time.perf_counter()
+    for d in frames:
+        o.track_frame(d)
+    dt = time.perf_counter() - t0
+    return dict(value=n_frames / dt, unit="frames/s", cores=1, kind="oracle",
+                sample=f"first {n_frames} frames of the sequence, 10 pose + 2 shape iterations each, FP64, 1 thread",
+                seconds=round(dt, 2))
+
+
+def run_reference(args, rank, world):
+    from paper_1711_07999_gb300 import synth
+    if rank != 0:
+        return
+    model = synth.make_model(2)
+    o, frames = oracle_frames(model, args.warmup + args.steps, seed=synth.seed_for(2, 900))
+    o.set_state(synth.gt_theta(model, 0.0), None)
+    for f in range(args.warmup):
+        o.track_frame(frames[f])
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        o.track_frame(frames[args.warmup + k])
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames": args.steps, "l2": "host"},
+            "latency_ms": {"p50": 1000 * float(np.percentile(times, 50)), "p99": 1000 * float(np.percentile(times, 99))},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} frames of the sequence, one frame per step, FP64, 1 thread"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1711_07999_gb300 import synth, trk
+
+    torch.cuda.set_device(local_rank)
+    model = synth.make_model(2, session=rank)
+    sess = trk.Session(model)
+    info = sess.info()
+    n_seq = max(args.frames, 1)
+    frames = render_sequence(model, sess, n_seq, seed=synth.seed_for(2, 500 + rank))
+    H, W = frames.shape[1:]
+    host = torch.from_numpy(frames).pin_memory()
+    dev = host.cuda()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    sess.set_pose(synth.gt_theta(model, 0.0))
+
+    def frame_dev(k):
+        sess.track_frame_device(dev[k % n_seq].data_ptr(), stream.cuda_stream)
+
+    # warm-up (also builds the CUDA graph)
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            frame_dev(k)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(stream)
+                frame_dev(args.warmup + k)
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times = np.array([a.elapsed_time(b) for a, b in ev])  # ms
+    total_ms = float(times.sum())
+    res = sess.read_result(want_offsets=False)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * args.steps / (max_ms / 1000.0)
+
+    # end to end through the public call: host pinned depth in, Theta / Phi / energies out
+    e2e_t = []
+    for k in range(args.steps):
+        flush.fill_((k + 7) & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sess.track_frame(host[(args.warmup + args.steps + k) % n_seq].numpy(), want_offsets=True)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    te = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps / float(te.item())
+
+    # per-stage kernel times (CUDA events on the launching stream, cold L2), dominant kernel, roofline
+    sess.set_depth(frames[(args.warmup + 2 * args.steps) % n_seq])
+    prof = sess.profile_iteration(reps=args.profile_reps, flush_bytes=L2_FLUSH_BYTES)
+    P, S = model["params"]["pose_iters"], model["params"]["shape_iters"]
+    per_frame = {}
+    for st, ms in prof.items():
+        n = P + S if st in ("skin", "raster", "visibility", "associate") else (S if st == "shape" else P)
+        per_frame[st] = ms * n
+    dom = max(per_frame, key=per_frame.get)
+    nvis = int((sess.read("VISPIX") >= 0).sum())
+    acc = sess.read("ACC")
+    nA = int((acc[:, 3] > 0).sum())
+    nassoc = int(acc[:, 3].sum())
+    nvalid = int((frames[0] > 0).sum())
+    NP = info["n_links"] + 1
+    nblk = (info["n_verts"] + 255) // 256
+    kind, amount = algorithmic(dom, info["n_verts"], info["n_tris"], W * H, NP, nvis, nassoc, nA, nvalid, nblk)
+    pk = peaks()
+    dur_s = prof[dom] / 1000.0
+    if kind == "hbm":
+        achieved = amount / dur_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": ncu_traffic(dom), "kernel": dom,
+                "algorithmic_bytes": amount, "peak_source": pk["src"] + " (burst copy)"}
+    else:
+        achieved = amount / dur_s / 1e12
+        fp64_peak = 1.25  # TFLOP/s, nominal dense FP64 of GB300 (no measured figure in MEASURED_PEAKS.json)
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": ncu_traffic(dom), "kernel": dom,
+                "algorithmic_flops": amount, "peak_source": "nominal FP64 rate"}
+    h2d = W * H * 4
+    d2h = info["n_links"] * 8 + (P + S) * 8 + info["n_verts"] * 12 + 8
+    line = None
+    if rank == 0:
+        cpu = cpu_baseline(model, args.cpu_frames) if (world == 1 and args.cpu_frames > 0) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_verts": info["n_verts"], "n_tris": info["n_tris"],
+                       "dof": info["n_links"], "image": f"{W}x{H}", "pose_iters": P, "shape_iters": S,
+                       "sessions_per_gpu": 1, "l2": "flushed (256 MiB write) before every frame",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99)),
+                           "e2e_p50": 1000 * float(np.percentile(e2e_t, 50)),
+                           "e2e_p99": 1000 * float(np.percentile(e2e_t, 99))},
+            "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": info["kernels_per_frame"] * args.steps,
+            "roofline": roof,
+            "stage_ms": {k: round(v, 5) for k, v in prof.items()},
+            "stage_share": {k: round(v / sum(per_frame.values()), 4) for k, v in per_frame.items()},
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "check": {"last_energy": float(res["energy"][P - 1]), "assoc_px": res["n_assoc_px"]},
+        }
+    sess.close()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=150, help="length of the pre-rendered sequence")
+    ap.add_argument("--cpu-frames", type=int, default=4, help="oracle frames of the CPU baseline sample")
+    ap.add_argument("--profile-reps", type=int, default=20)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * trk.h -- C ABI of the GB300 tracker for "Dynamic High Resolution Deformable Articulated Tracking"
+ * (Walsman, Wan, Schmidt, Fox; 3DV 2017).
+ *
+ * One session tracks one subject: a kinematic tree of 1-DoF links (Sec. 3.1), a triangle mesh attached
+ * by dual-quaternion skinning (Sec. 3.2) with per-vertex warp offsets Phi (Sec. 3.3), and a pinhole
+ * depth camera.  Each frame runs pose_iters Levenberg-Marquardt iterations on the joint values Theta
+ * (Sec. 4.2) and shape_iters per-vertex shape iterations on Phi (Sec. 4.3); every iteration re-skins,
+ * z-buffers and re-associates the depth pixels (Sec. 4.1).  Every step runs in CUDA kernels on the
+ * current device; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Plain pointers and sizes only.  "host" pointers are CPU memory, "device" pointers CUDA memory of
+ *    the device that was current when the session was created.
+ *  - Inputs are copied at the call; the caller keeps ownership of every buffer it passes.
+ *  - The session owns all of its device memory and frees it in trk_destroy.
+ *  - Every call returns a trk_status; on failure trk_last_error() returns a message (thread-local).
+ *  - Units are metres and radians; the camera looks down +z, x right, y down (world = camera).
+ *  - A session is not thread-safe: calls on one session must not overlap.
+ */
+#ifndef TRK_H_
+#define TRK_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TRK_OK = 0,
+  TRK_ERR_INVALID_ARG = 1, /* malformed model, sizes or pointers; nothing was changed           */
+  TRK_ERR_OOM = 2,         /* device or host allocation failed                                     */
+  TRK_ERR_CUDA = 3,        /* a CUDA runtime call failed (message holds cudaGetErrorString)        */
+  TRK_ERR_NO_CAPACITY = 4, /* a fixed limit was exceeded (links, server budget)                    */
+  TRK_ERR_TIMEOUT = 5,     /* a bounded wait ran out                                               */
+  TRK_ERR_NUMERIC = 6      /* non-finite input or a non-positive-definite system                   */
+} trk_status;
+
+typedef struct trk_session trk_session;
+
+/* Template mesh in the bind pose Theta = 0 (Sec. 3.2).  bone_idx/bone_w: the <= 4 nonzero entries of
+ * the weight column omega_i (Sec. 3.2); unused slots have weight 0; weights are >= 0 and sum to 1. */
+typedef struct {
+  int32_t n_verts, n_tris;
+  const float* verts;      /* host [n_verts][3]                                        */
+  const int32_t* tris;     /* host [n_tris][3], vertex indices, counter-clockwise seen from outside */
+  const uint8_t* bone_idx; /* host [n_verts][4], link indices                          */
+  const float* bone_w;     /* host [n_verts][4]                                        */
+} trk_mesh;
+
+/* Kinematic tree (Sec. 3.1): link j hangs from parent[j] < j (-1 = world) through the fixed unit
+ * dual quaternion offset H_{P(j),j} followed by its 1-DoF joint: a hinge (Eq. H_hinge) or a prismatic
+ * joint (Eq. H_prismatic) about / along axis z_j.  Multi-DoF joints are chains of links with identity
+ * offsets.  One link carries one joint value, so |Theta| = n_links (<= TRK_MAX_LINKS). */
+typedef struct {
+  int32_t n_links;
+  const int32_t* parent;    /* host [n_links]                                                 */
+  const int32_t* type;      /* host [n_links]: 0 hinge, 1 prismatic                           */
+  const float* axis;        /* host [n_links][3], normalised at create                        */
+  const float* offset_dq;   /* host [n_links][8]: (w,x,y,z | w,x,y,z), |real| = 1, <real,dual> = 0 */
+  const float* prior_mask;  /* host [n_links]: multiplies the pose-prior weight S_kk (0 = no prior) */
+} trk_skeleton;
+
+#define TRK_MAX_LINKS 79
+
+/* Pinhole intrinsics; pixel (px, py) samples the ray through image coordinates (px, py). */
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+} trk_intrinsics;
+
+/* Method constants (Secs. 4.1-4.3).  lambda_k0 starts the LM damping; lambda_s weights the pose prior
+ * (lambda_s S)^2; lambda_phi and lambda_N weight the offset damping and the neighbour smoothness of
+ * Eq. r_warp; lambda_w damps the per-vertex 3x3 systems; cutoff_m is the association cutoff tau;
+ * window_half_px the half-size W of the (2W+1)^2 bucket window; eps_vis_m the z-buffer slack of the
+ * visibility test; z_near_m the near plane; knn the neighbourhood size |N(i)| (<= 4). */
+typedef struct {
+  int32_t pose_iters, shape_iters, shape_sweeps;
+  float lambda_k0, lambda_s, lambda_phi, lambda_N, lambda_w;
+  float cutoff_m, eps_vis_m, z_near_m;
+  int32_t window_half_px, knn;
+  int32_t precision; /* 0 = FP32 (the only value accepted) */
+} trk_params;
+
+/* Per-frame outputs, written into caller (host) buffers; any pointer may be NULL. */
+typedef struct {
+  double* theta;         /* [n_links] joint values after the frame                       */
+  float* offsets;        /* [n_verts][3] warp offsets Phi after the frame                */
+  double* energy;        /* [pose_iters + shape_iters]: E_pose per pose iteration (data + prior,
+                            at that iteration's association), then E_shape per shape iteration */
+  int32_t n_assoc_px;    /* pixels associated in the last association of the frame      */
+  int32_t n_assoc_verts; /* vertices with at least one associated pixel, same pass      */
+} trk_result;
+
+/* Creates a session on the current CUDA device: validates and copies the model, derives the bind pose
+ * H^0 (Sec. 3.2), the prior weights S_kk = n_k/|V| (vertices weighted to the subtree of link k), the
+ * vertex-to-face lists and the neighbourhoods N(i) (the knn nearest bind-pose vertices, Sec. 4.3),
+ * allocates all device state and sets Theta = 0, Phi = 0.
+ * Errors: TRK_ERR_INVALID_ARG (malformed input, *out untouched), TRK_ERR_NO_CAPACITY (too many links),
+ * TRK_ERR_OOM, TRK_ERR_CUDA. */
+trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* skel, const trk_intrinsics* cam,
+                      const trk_params* params, trk_session** out);
+
+/* Sets Theta (host [n_links]) and Phi (host [n_verts][3], NULL = zero) and resets the LM damping to
+ * lambda_k0.  Synchronous.  TRK_ERR_NUMERIC on non-finite values. */
+trk_status trk_set_pose(trk_session* s, const double* theta, const float* offsets);
+
+/* Tracks one frame (Sec. 4): uploads depth (host [height][width] metres, 0 = no return), runs the
+ * frame on the session's stream, waits, and fills *out.  The state carries over to the next frame. */
+trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out);
+
+/* Enqueues one frame on cuda_stream (a cudaStream_t; NULL = the session's own stream) reading depth
+ * from device memory d_depth_m [height][width].  Returns without waiting; trk_read_result waits for
+ * the frame and copies its outputs. */
+trk_status trk_track_frame_device(trk_session* s, const float* d_depth_m, void* cuda_stream);
+trk_status trk_read_result(trk_session* s, trk_result* out);
+
+/* Renders the model's z-buffer depth at (theta, offsets) (host inputs, offsets NULL = zero) into
+ * depth_m (host [height][width], 0 where no triangle covers the pixel).  Does not change the state. */
+trk_status trk_render_depth(trk_session* s, const double* theta, const float* offsets, float* depth_m);
+
+/* Releases every resource of the session.  NULL is allowed. */
+void trk_destroy(trk_session* s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* trk_last_error(void);
+
+/* ---- Step-level calls: each runs one step of an iteration at the session's current state, so that
+ * every step can be checked on its own.  They are synchronous and leave their outputs in the session,
+ * readable with trk_read. ------------------------------------------------------------------------ */
+
+/* Copies depth (host [height][width]) into the session's depth buffer. */
+trk_status trk_set_depth(trk_session* s, const float* depth_m);
+/* Sec. 3.1 + Eqs. H_Sigma, deformation: FK of Theta and v_i = H_iSigma (v0_i + phi_i). */
+trk_status trk_step_skin(trk_session* s);
+/* z-buffer of the posed mesh (packed (depth bits << 32) | triangle, min-reduced) and face normals. */
+trk_status trk_step_raster(trk_session* s);
+/* Vertex normals (normalised sums of incident face normals), visibility against the z-buffer, and
+ * the per-pixel buckets of visible vertices (Sec. 4.1). */
+trk_status trk_step_visibility(trk_session* s);
+/* Sec. 4.1 association of every valid depth pixel with the closest visible vertex in the window,
+ * within the cutoff, and the per-vertex sums of (p_k - v_i). */
+trk_status trk_step_associate(trk_session* s);
+/* Eq. residual, the pose Jacobian (Sec. 4.2) and the reduced [J r]^T [J r] (Eqs. JTJ, JTr). */
+trk_status trk_step_normal_equations(trk_session* s);
+/* Damped least squares step with the pose prior (Sec. 4.2): up to 6 damping values are tried in
+ * order and the first one that does not raise the energy (at the fixed association) is taken. */
+trk_status trk_step_lm(trk_session* s);
+/* Sec. 4.3 shape iteration (residuals, per-vertex 3x3 solves, shape_sweeps Jacobi sweeps). */
+trk_status trk_step_shape(trk_session* s);
+
+typedef enum {
+  TRK_FIELD_VERTS = 0,    /* float[n_verts][4]: posed v_i, camera frame (w unused)          */
+  TRK_FIELD_NORMALS = 1,  /* float[n_verts][4]: n_i, w = 1 if the normal is valid           */
+  TRK_FIELD_ZBUF = 2,     /* uint64[height*width]: (float bits of depth << 32) | triangle, ~0 = empty */
+  TRK_FIELD_VISPIX = 3,   /* int32[n_verts]: pixel index of a visible vertex, -1 otherwise  */
+  TRK_FIELD_CORR = 4,     /* int32[height*width]: associated vertex, -1 = none               */
+  TRK_FIELD_ACC = 5,      /* int64[n_verts][4]: sum of (p_k - v_i) in units of 2^-30 m, count */
+  TRK_FIELD_NORMAL_EQ = 6,/* double[(n_links+1)^2]: [J r]^T [J r], row-major                  */
+  TRK_FIELD_THETA = 7,    /* double[n_links]                                                 */
+  TRK_FIELD_PHI = 8,      /* float[n_verts][4] (w unused)                                    */
+  TRK_FIELD_LAMBDA = 9,   /* double[1]: LM damping                                           */
+  TRK_FIELD_ENERGY = 10,  /* double[pose_iters + shape_iters] of the last frame              */
+  TRK_FIELD_LM_TRIALS = 11,/* double[8]: E of each attempted damping value (+inf if not tried), then
+                              the current E, then the accepted attempt index (-1 = none)          */
+  TRK_FIELD_SHAPE_RG = 12,/* float[n_verts][4]: g_i = dr_i/dphi_i and r_i of the last shape step */
+  TRK_FIELD_NEIGHBOURS = 13,/* int32[n_verts][4]: N(i), -1 pads                              */
+  TRK_FIELD_PRIOR = 14,   /* double[n_links]: (lambda_s S_kk)^2                              */
+  TRK_FIELD_COUNT = 15
+} trk_field;
+
+/* Copies a session buffer to host memory; bytes must equal the field's size exactly. */
+trk_status trk_read(trk_session* s, trk_field field, void* host_dst, size_t bytes);
+
+/* ---- Introspection and timing ------------------------------------------------------------------ */
+typedef struct {
+  int32_t n_links, n_verts, n_tris, width, height;
+  int32_t kernels_per_frame; /* kernel launches in one trk_track_frame                          */
+  size_t device_bytes;       /* device memory the session holds                                  */
+} trk_info;
+trk_status trk_get_info(trk_session* s, trk_info* out);
+
+/* Stages of one iteration, in launch order, as timed by trk_profile_iteration. */
+typedef enum {
+  TRK_STAGE_SKIN = 0, TRK_STAGE_RASTER, TRK_STAGE_VISIBILITY, TRK_STAGE_ASSOCIATE, TRK_STAGE_RESID_JTJ,
+  TRK_STAGE_REDUCE, TRK_STAGE_LM_SOLVE, TRK_STAGE_LM_EVAL, TRK_STAGE_SHAPE, TRK_STAGE_COUNT
+} trk_stage;
+
+/* Runs reps pose iterations (and reps shape steps, from the state they reach) at the session's state
+ * and depth, launching each stage's kernel(s) between CUDA events recorded on the session's stream, and
+ * writes the mean duration of each stage in milliseconds to ms (host [TRK_STAGE_COUNT]).  The state
+ * advances as in tracking.  flush_bytes > 0 overwrites a scratch buffer of that size before each stage
+ * (outside the timed interval) so that every stage starts from a cold L2. */
+trk_status trk_profile_iteration(trk_session* s, int32_t reps, size_t flush_bytes, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRK_H_ */

@@ -1,0 +1,316 @@
+// kernels_geom.cu -- forward kinematics, skinning, z-buffer, visibility / buckets and projective
+// association (Secs. 3.1-3.3, 4.1).  All streams are per-vertex, per-triangle or per-pixel and
+// HBM/L2-bound; vertex and pixel records are float4 so that each thread issues 16-byte loads.
+#include "trk_internal.cuh"
+
+namespace trk {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sec. 3.1: FK of the current Theta -> H_{j,Delta} and the joint twists Xi_j (one thread per link)
+// ---------------------------------------------------------------------------------------------
+__global__ void k_fk(Dev d) {
+  __shared__ LinkTable lt;
+  for (int t = threadIdx.x; t < (int)(sizeof(LinkTable) / 4); t += blockDim.x)
+    reinterpret_cast<int*>(&lt)[t] = reinterpret_cast<const int*>(d.links)[t];
+  __syncthreads();
+  for (int j = threadIdx.x; j < d.L; j += blockDim.x) {
+    DQ H;
+    float xi[6];
+    fk_link(lt, d.theta, j, &H, xi);
+    d.Hd[j] = H;
+    for (int c = 0; c < 6; ++c) d.xi[8 * j + c] = xi[c];
+    d.xi[8 * j + 6] = 0.f;
+    d.xi[8 * j + 7] = 0.f;
+  }
+}
+
+void launch_fk(const Dev& d, cudaStream_t st) { k_fk<<<1, 128, 0, st>>>(d); }
+
+// ---------------------------------------------------------------------------------------------
+// Eqs. H_Sigma, deformation: v_i = H_iSigma (v0_i + phi_i).  Also clears the per-pixel and
+// per-vertex accumulators of this iteration (z-buffer, bucket heads, association sums).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_skin(Dev d, int phi_buf) {
+  extern __shared__ DQ sHd[];
+  for (int j = threadIdx.x; j < d.L; j += blockDim.x) sHd[j] = d.Hd[j];
+  __syncthreads();
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int stride = gridDim.x * blockDim.x;
+  const int npx = d.cam.W * d.cam.H;
+  for (int k = tid; k < npx; k += stride) {
+    d.zbuf[k] = ~0ull;
+    d.head[k] = -1;
+  }
+  for (int k = tid; k < d.V; k += stride) d.acc[k] = Acc4{0, 0, 0, 0};
+  if (tid == 0) {
+    d.stats[0] = 0;
+    d.stats[1] = 0;
+  }
+  const float4* phi = d.phi[phi_buf];
+  for (int i = tid; i < d.V; i += stride) {
+    float sg[4];
+    const DQ H = blend_bones(sHd, d.bidx[i], d.bw[i], sg);
+    const float4 x0 = d.v0[i], p = phi[i];
+    const float3 v = dq_point(H, make_float3(x0.x + p.x, x0.y + p.y, x0.z + p.z));
+    d.v[i] = make_float4(v.x, v.y, v.z, 0.f);
+  }
+}
+
+static int grid_for(int n, int block) { return (n + block - 1) / block; }
+
+void launch_skin(const Dev& d, int phi_buf, cudaStream_t st) {
+  const int g = max(grid_for(d.V, kBlock), 152);
+  k_skin<<<g, kBlock, d.L * sizeof(DQ), st>>>(d, phi_buf);
+}
+
+// ---------------------------------------------------------------------------------------------
+// z-buffer: one thread per triangle, pixel centres at integer coordinates, inclusive edge test for
+// both windings, depth from the ray-plane intersection, min-reduced as (float bits << 32) | id.
+// Also writes the unnormalised face normal (b - a) x (c - a) used by the vertex normals.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_raster(Dev d) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.F) return;
+  const int4 t = d.tris[f];
+  const Cam c = d.cam;
+  const float3 o = make_float3(c.ox, c.oy, c.oz);
+  const float3 Al = f3(d.v[t.x]), Bl = f3(d.v[t.y]), Cl = f3(d.v[t.z]);
+  const float3 N = cross3(sub3(Bl, Al), sub3(Cl, Al));
+  d.fn[f] = make_float4(N.x, N.y, N.z, 0.f);
+  const float3 A = make_float3(Al.x + o.x, Al.y + o.y, Al.z + o.z);  // camera frame
+  const float3 B = make_float3(Bl.x + o.x, Bl.y + o.y, Bl.z + o.z);
+  const float3 C = make_float3(Cl.x + o.x, Cl.y + o.y, Cl.z + o.z);
+  if (A.z <= c.z_near || B.z <= c.z_near || C.z <= c.z_near) return;
+  const float ua = c.fx * A.x / A.z + c.cx, va = c.fy * A.y / A.z + c.cy;
+  const float ub = c.fx * B.x / B.z + c.cx, vb = c.fy * B.y / B.z + c.cy;
+  const float uc = c.fx * C.x / C.z + c.cx, vc = c.fy * C.y / C.z + c.cy;
+  if (!(isfinite(ua) && isfinite(ub) && isfinite(uc) && isfinite(va) && isfinite(vb) && isfinite(vc))) return;
+  const float area = (ub - ua) * (vc - va) - (vb - va) * (uc - ua);
+  if (area == 0.f) return;
+  const float NA = dot3(N, A);
+  const int x0 = (int)fmaxf(0.f, ceilf(fminf(ua, fminf(ub, uc))));
+  const int x1 = (int)fminf((float)(c.W - 1), floorf(fmaxf(ua, fmaxf(ub, uc))));
+  const int y0 = (int)fmaxf(0.f, ceilf(fminf(va, fminf(vb, vc))));
+  const int y1 = (int)fminf((float)(c.H - 1), floorf(fmaxf(va, fmaxf(vb, vc))));
+  for (int py = y0; py <= y1; ++py) {
+    const float fy = (float)py;
+    for (int px = x0; px <= x1; ++px) {
+      const float fx = (float)px;
+      const float w0 = (uc - ub) * (fy - vb) - (vc - vb) * (fx - ub);
+      const float w1 = (ua - uc) * (fy - vc) - (va - vc) * (fx - uc);
+      const float w2 = (ub - ua) * (fy - va) - (vb - va) * (fx - ua);
+      const bool inside = (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) || (w0 <= 0.f && w1 <= 0.f && w2 <= 0.f);
+      if (!inside) continue;
+      const float dx = (fx - c.cx) / c.fx, dy = (fy - c.cy) / c.fy;
+      const float den = N.x * dx + N.y * dy + N.z;
+      if (den == 0.f) continue;
+      const float z = NA / den;
+      if (!(z > 0.f)) continue;
+      const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)f;
+      atomicMin(&d.zbuf[py * c.W + px], key);
+    }
+  }
+}
+
+void launch_raster(const Dev& d, cudaStream_t st) {
+  if (d.F > 0) k_raster<<<grid_for(d.F, kBlock), kBlock, 0, st>>>(d);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Vertex normals (sum of incident face normals in face order, normalised), visibility (front-facing,
+// rounded pixel inside the image, not behind the z-buffer by more than eps_vis), and insertion of
+// each visible vertex into its pixel's bucket (a singly linked list: head[pixel] -> rec[i].w).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_visibility(Dev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.V) return;
+  float3 s = make_float3(0.f, 0.f, 0.f);
+  const int e = d.csr_off[i + 1];
+  for (int t = d.csr_off[i]; t < e; ++t) {
+    const float4 fn = d.fn[d.csr_face[t]];
+    s.x += fn.x; s.y += fn.y; s.z += fn.z;
+  }
+  const float len = sqrtf(dot3(s, s));
+  const bool valid = len >= 1e-12f;
+  const float3 n = valid ? make_float3(s.x / len, s.y / len, s.z / len) : make_float3(0.f, 0.f, 0.f);
+  d.n[i] = make_float4(n.x, n.y, n.z, valid ? 1.f : 0.f);
+  int vp = -1;
+  const float4 pl = d.v[i];
+  const Cam c = d.cam;
+  const float3 p = make_float3(pl.x + c.ox, pl.y + c.oy, pl.z + c.oz);  // camera frame
+  if (valid && p.z > c.z_near) {
+    const float nd = dot3(n, p);
+    const float u = c.fx * p.x / p.z + c.cx, vv = c.fy * p.y / p.z + c.cy;
+    const float fu = floorf(u + 0.5f), fv = floorf(vv + 0.5f);
+    if (nd < 0.f && fu >= 0.f && fv >= 0.f && fu < (float)c.W && fv < (float)c.H) {
+      const int k = (int)fv * c.W + (int)fu;
+      const unsigned long long key = d.zbuf[k];
+      bool ok = true;
+      if (key != ~0ull) ok = p.z <= __uint_as_float((unsigned)(key >> 32)) + c.eps_vis;
+      if (ok) {
+        vp = k;
+        const int old = atomicExch(&d.head[k], i);
+        d.rec[i] = make_float4(pl.x, pl.y, pl.z, __int_as_float(old));
+      }
+    }
+  }
+  d.vispix[i] = vp;
+}
+
+void launch_visibility(const Dev& d, cudaStream_t st) {
+  k_visibility<<<grid_for(d.V, kBlock), kBlock, 0, st>>>(d);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sec. 4.1 projective association.  Each valid pixel back-projects to p = ((px-cx) d/fx, (py-cy) d/fy, d)
+// and takes the closest visible vertex (squared distance, ties to the smaller index) among the buckets
+// of the (2W+1)^2 window, within the cutoff tau.  The window is searched in rings of growing Chebyshev
+// radius r; after ring r every unvisited vertex lies at least d (r + 1/2) kappa away (it projects at
+// least r + 1/2 pixels from the pixel, and kappa = min over axes of 1 / (f sqrt(1 + c_max^2)) turns
+// that angle into a distance from p), so the search stops once that bound exceeds the best distance
+// or tau: the result is the same argmin as the exhaustive window search.
+//
+// Rings 0..kRingsPerThread are searched by the pixel's own thread; the few pixels that need more rings
+// (no vertex within ~1-2 cm: silhouettes, holes) are finished cooperatively by their warp, one pixel at
+// a time, the lanes splitting each ring's 8r buckets and combining (d^2, index) keys with a warp-min.
+// The pixel's offset p - v_i is added to the vertex's fixed-point sums (integer atomics: the sums do
+// not depend on the order of the additions).
+// ---------------------------------------------------------------------------------------------
+constexpr int kRingsPerThread = 2;
+
+__device__ __forceinline__ void scan_bucket(const Dev& d, int q, float3 p, float tau2, int& best, float& bd2) {
+  int i = __ldg(&d.head[q]);
+  // a bucket list never holds more than |V| entries; the hop bound only guards against misuse
+  for (int hops = 0; i >= 0 && hops < d.V; ++hops) {
+    const float4 r = d.rec[i];
+    const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 <= tau2 && (best < 0 || d2 < bd2 || (d2 == bd2 && i < best))) {
+      best = i;
+      bd2 = d2;
+    }
+    i = __float_as_int(r.w);
+  }
+}
+
+// bucket t (0 <= t < 8r) of the ring of Chebyshev radius r around (px, py), or -1 outside the image
+__device__ __forceinline__ int ring_bucket(int px, int py, int r, int t, int W, int H) {
+  int x, y;
+  // top row: 2r+1 cells, bottom row: 2r+1, left column: 2r-1 (corners excluded), right column: 2r-1
+  if (t <= 2 * r) { x = px - r + t; y = py - r; }
+  else if (t <= 4 * r + 1) { x = px - r + (t - 2 * r - 1); y = py + r; }
+  else if (t <= 6 * r) { x = px - r; y = py - r + 1 + (t - 4 * r - 2); }
+  else { x = px + r; y = py - r + 1 + (t - 6 * r - 1); }
+  return (x >= 0 && y >= 0 && x < W && y < H) ? y * W + x : -1;
+}
+
+__device__ __forceinline__ unsigned long long key_of(int best, float bd2) {
+  return best < 0 ? ~0ull : (((unsigned long long)__float_as_uint(bd2) << 32) | (unsigned)best);
+}
+
+__global__ void __launch_bounds__(kBlock) k_associate(Dev d) {
+  const Cam c = d.cam;
+  const int lane = threadIdx.x & 31;
+  const int px = blockIdx.x * 16 + (threadIdx.x & 15);
+  const int py = blockIdx.y * 16 + (threadIdx.x >> 4);
+  const bool inimg = px < c.W && py < c.H;
+  const int k = py * c.W + px;
+  const float dep = inimg ? d.depth[k] : 0.f;
+  const float tau2 = c.tau * c.tau;
+  int best = -1;
+  float bd2 = 0.f;
+  float3 p = make_float3(0.f, 0.f, 0.f);
+  bool open = false;  // still searching after the thread-owned rings
+  if (dep > 0.f) {
+    // back-projection in FP64, then moved into the session-local frame (exact up to one FP32 rounding)
+    p = make_float3((float)(((double)px - (double)c.cx) * (double)dep * c.inv_fx - (double)c.ox),
+                    (float)(((double)py - (double)c.cy) * (double)dep * c.inv_fy - (double)c.oy),
+                    (float)((double)dep - (double)c.oz));
+    open = true;
+    const int rmax = min(c.R, kRingsPerThread);
+    for (int r = 0; r <= rmax; ++r) {
+      if (r == 0) {
+        scan_bucket(d, k, p, tau2, best, bd2);
+      } else {
+        for (int t = 0; t < 8 * r; ++t) {
+          const int q = ring_bucket(px, py, r, t, c.W, c.H);
+          if (q >= 0) scan_bucket(d, q, p, tau2, best, bd2);
+        }
+      }
+      const float lb = dep * ((float)r + 0.499f) * c.kappa;
+      if (lb > c.tau || (best >= 0 && lb * lb > bd2) || r == c.R) { open = false; break; }
+    }
+  }
+  // warp-cooperative completion of the open pixels, one at a time
+  unsigned pending = __ballot_sync(0xffffffffu, open);
+  while (pending) {
+    const int src = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const int sx = __shfl_sync(0xffffffffu, px, src), sy = __shfl_sync(0xffffffffu, py, src);
+    const float sdep = __shfl_sync(0xffffffffu, dep, src);
+    const float3 sp = make_float3(__shfl_sync(0xffffffffu, p.x, src), __shfl_sync(0xffffffffu, p.y, src),
+                                  __shfl_sync(0xffffffffu, p.z, src));
+    int wb = -1;
+    float wd2 = 0.f;
+    unsigned long long key = key_of(__shfl_sync(0xffffffffu, best, src), __shfl_sync(0xffffffffu, bd2, src));
+    for (int r = kRingsPerThread + 1; r <= c.R; ++r) {
+      for (int t = lane; t < 8 * r; t += 32) {
+        const int q = ring_bucket(sx, sy, r, t, c.W, c.H);
+        if (q >= 0) scan_bucket(d, q, sp, tau2, wb, wd2);
+      }
+      unsigned long long kk = key_of(wb, wd2);
+      kk = kk < key ? kk : key;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, kk, o);
+        kk = other < kk ? other : kk;
+      }
+      key = kk;
+      const float lb = sdep * ((float)r + 0.499f) * c.kappa;
+      const float kd2 = key == ~0ull ? 0.f : __uint_as_float((unsigned)(key >> 32));
+      if (lb > c.tau || (key != ~0ull && lb * lb > kd2)) break;
+    }
+    if (lane == src && key != ~0ull) {
+      best = (int)(unsigned)(key & 0xffffffffu);
+      bd2 = __uint_as_float((unsigned)(key >> 32));
+    }
+  }
+  if (inimg) d.corr[k] = best;
+  if (best >= 0) {
+    const float4 vb = d.v[best];
+    unsigned long long* a = reinterpret_cast<unsigned long long*>(&d.acc[best]);
+    atomicAdd(a + 0, (unsigned long long)__float2ll_rn((p.x - vb.x) * kFix));
+    atomicAdd(a + 1, (unsigned long long)__float2ll_rn((p.y - vb.y) * kFix));
+    atomicAdd(a + 2, (unsigned long long)__float2ll_rn((p.z - vb.z) * kFix));
+    atomicAdd(a + 3, 1ull);
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, best >= 0);
+  if (lane == 0 && m) atomicAdd(&d.stats[0], __popc(m));
+}
+
+void launch_associate(const Dev& d, cudaStream_t st) {
+  dim3 g((d.cam.W + 15) / 16, (d.cam.H + 15) / 16);
+  k_associate<<<g, kBlock, 0, st>>>(d);
+}
+
+__global__ void k_depth_from_zbuf(Dev d, float* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.cam.W * d.cam.H) return;
+  const unsigned long long key = d.zbuf[k];
+  out[k] = key == ~0ull ? 0.f : __uint_as_float((unsigned)(key >> 32));
+}
+
+void launch_depth_from_zbuf(const Dev& d, float* out, cudaStream_t st) {
+  k_depth_from_zbuf<<<grid_for(d.cam.W * d.cam.H, kBlock), kBlock, 0, st>>>(d, out);
+}
+
+}  // namespace trk

@@ -1,0 +1,673 @@
+// trk_api.cu -- host side of the C ABI declared in include/trk.h: validation, derived model data
+// (bind pose, prior weights, vertex-to-face lists, neighbourhoods), device allocation, the per-frame
+// CUDA graph and the step-level calls.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/trk.h"
+#include "trk_internal.cuh"
+
+using namespace trk;
+
+namespace {
+
+thread_local std::string g_err;
+
+trk_status fail(trk_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(e_ == cudaErrorMemoryAllocation ? TRK_ERR_OOM : TRK_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+  } while (0)
+
+// ---- host dual quaternions in FP64 (bind pose only) ----------------------------------------------
+struct HQ { double w, x, y, z; };
+struct HDQ { HQ r, d; };
+HQ hmul(HQ a, HQ b) {
+  return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z, a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+          a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x, a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+HQ hadd(HQ a, HQ b) { return {a.w + b.w, a.x + b.x, a.y + b.y, a.z + b.z}; }
+HDQ hdmul(const HDQ& a, const HDQ& b) { return {hmul(a.r, b.r), hadd(hmul(a.r, b.d), hmul(a.d, b.r))}; }
+
+// Exact knn nearest other vertices (squared distance of the float coordinates in FP64, ties to the
+// smaller index) with a uniform grid: cells are visited in rings of growing Chebyshev radius rho; once
+// knn candidates are held and the k-th distance is below (rho * cell)^2, no farther cell can beat it.
+void knn_grid(int V, const float* xyz, int K, std::vector<int>& nbr) {
+  nbr.assign((size_t)V * 4, -1);
+  if (K <= 0 || V <= 1) return;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < V; ++i)
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::min(lo[c], (double)xyz[3 * i + c]);
+      hi[c] = std::max(hi[c], (double)xyz[3 * i + c]);
+    }
+  double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  double cell = std::max(ext / std::max(1.0, std::cbrt((double)V / 2.0)), 1e-9);
+  int n[3];
+  for (int c = 0; c < 3; ++c) n[c] = std::max(1, (int)std::floor((hi[c] - lo[c]) / cell) + 1);
+  auto cidx = [&](int i, int c) { return std::min(n[c] - 1, (int)std::floor((xyz[3 * i + c] - lo[c]) / cell)); };
+  std::vector<int> start((size_t)n[0] * n[1] * n[2] + 1, 0), list(V);
+  for (int i = 0; i < V; ++i) start[((size_t)cidx(i, 2) * n[1] + cidx(i, 1)) * n[0] + cidx(i, 0) + 1]++;
+  for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+  std::vector<int> fill(start.begin(), start.end() - 1);
+  for (int i = 0; i < V; ++i) list[fill[((size_t)cidx(i, 2) * n[1] + cidx(i, 1)) * n[0] + cidx(i, 0)]++] = i;
+  const int maxr = std::max(n[0], std::max(n[1], n[2]));
+  for (int i = 0; i < V; ++i) {
+    double bd[4];
+    int bi[4], cnt = 0;
+    const int ci[3] = {cidx(i, 0), cidx(i, 1), cidx(i, 2)};
+    for (int rho = 0; rho <= maxr; ++rho) {
+      for (int z = ci[2] - rho; z <= ci[2] + rho; ++z) {
+        if (z < 0 || z >= n[2]) continue;
+        for (int y = ci[1] - rho; y <= ci[1] + rho; ++y) {
+          if (y < 0 || y >= n[1]) continue;
+          for (int x = ci[0] - rho; x <= ci[0] + rho; ++x) {
+            if (x < 0 || x >= n[0]) continue;
+            if (std::max(std::abs(x - ci[0]), std::max(std::abs(y - ci[1]), std::abs(z - ci[2]))) != rho) continue;
+            const size_t q = ((size_t)z * n[1] + y) * n[0] + x;
+            for (int t = start[q]; t < start[q + 1]; ++t) {
+              const int j = list[t];
+              if (j == i) continue;
+              const double dx = (double)xyz[3 * j] - (double)xyz[3 * i];
+              const double dy = (double)xyz[3 * j + 1] - (double)xyz[3 * i + 1];
+              const double dz = (double)xyz[3 * j + 2] - (double)xyz[3 * i + 2];
+              const double d2 = dx * dx + dy * dy + dz * dz;
+              if (cnt == K && (d2 > bd[K - 1] || (d2 == bd[K - 1] && j > bi[K - 1]))) continue;
+              int pos = cnt < K ? cnt++ : K - 1;
+              while (pos > 0 && (bd[pos - 1] > d2 || (bd[pos - 1] == d2 && bi[pos - 1] > j))) {
+                bd[pos] = bd[pos - 1];
+                bi[pos] = bi[pos - 1];
+                --pos;
+              }
+              bd[pos] = d2;
+              bi[pos] = j;
+            }
+          }
+        }
+      }
+      const double reach = rho * cell;
+      if (cnt == K && bd[K - 1] < reach * reach * (1.0 - 1e-12)) break;
+    }
+    for (int k = 0; k < cnt; ++k) nbr[(size_t)i * 4 + k] = bi[k];
+  }
+}
+
+}  // namespace
+
+struct trk_session {
+  Dev d{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  trk_params prm{};
+  std::vector<void*> allocs;
+  size_t device_bytes = 0;
+  double* h_pinned = nullptr;  // pinned staging for results
+  float* d_render = nullptr;
+  int phi_cur = 0;
+};
+
+namespace {
+
+template <typename T>
+trk_status dalloc(trk_session* s, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? TRK_ERR_OOM : TRK_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                cudaGetErrorString(e));
+  s->allocs.push_back(q);
+  s->device_bytes += bytes;
+  *p = static_cast<T*>(q);
+  return TRK_OK;
+}
+
+#define TRY(x)                         \
+  do {                                 \
+    trk_status st_ = (x);              \
+    if (st_ != TRK_OK) return st_;     \
+  } while (0)
+
+trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsics* c, const trk_params* p) {
+  if (!m || !k || !c || !p) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  if (k->n_links <= 0) return fail(TRK_ERR_INVALID_ARG, "n_links must be positive");
+  if (k->n_links > TRK_MAX_LINKS) return fail(TRK_ERR_NO_CAPACITY, "n_links %d > %d", k->n_links, TRK_MAX_LINKS);
+  if (m->n_verts <= 0 || m->n_tris < 0) return fail(TRK_ERR_INVALID_ARG, "bad mesh sizes");
+  if (!m->verts || !m->bone_idx || !m->bone_w || (m->n_tris && !m->tris)) return fail(TRK_ERR_INVALID_ARG, "NULL mesh array");
+  if (!k->parent || !k->type || !k->axis || !k->offset_dq || !k->prior_mask)
+    return fail(TRK_ERR_INVALID_ARG, "NULL skeleton array");
+  if (c->width <= 0 || c->height <= 0 || !(c->fx > 0) || !(c->fy > 0) || !std::isfinite(c->cx) || !std::isfinite(c->cy))
+    return fail(TRK_ERR_INVALID_ARG, "bad intrinsics");
+  if ((long long)c->width * c->height > (1ll << 28)) return fail(TRK_ERR_NO_CAPACITY, "image too large");
+  if (p->precision != 0) return fail(TRK_ERR_INVALID_ARG, "precision %d not supported", p->precision);
+  if (p->pose_iters < 0 || p->shape_iters < 0 || p->shape_sweeps < 1 || p->knn < 0 || p->knn > 4 ||
+      p->window_half_px < 0 || !(p->cutoff_m > 0) || !(p->lambda_k0 > 0) || p->lambda_s < 0 || p->lambda_phi < 0 ||
+      p->lambda_N < 0 || p->lambda_w < 0 || !(p->z_near_m > 0) || !(p->eps_vis_m >= 0))
+    return fail(TRK_ERR_INVALID_ARG, "bad params");
+  const int L = k->n_links;
+  for (int j = 0; j < L; ++j) {
+    if (k->parent[j] >= j || k->parent[j] < -1) return fail(TRK_ERR_INVALID_ARG, "parent[%d] must be in [-1, %d)", j, j);
+    if (k->type[j] != 0 && k->type[j] != 1) return fail(TRK_ERR_INVALID_ARG, "type[%d]", j);
+    const float* a = k->axis + 3 * j;
+    const double an = std::sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
+    if (!(an > 0.5 && an < 2.0)) return fail(TRK_ERR_INVALID_ARG, "axis[%d] not unit", j);
+    const float* o = k->offset_dq + 8 * j;
+    double nr = 0, od = 0;
+    for (int q = 0; q < 4; ++q) { nr += (double)o[q] * o[q]; od += (double)o[q] * o[4 + q]; }
+    if (std::fabs(nr - 1.0) > 1e-5 || std::fabs(od) > 1e-5) return fail(TRK_ERR_INVALID_ARG, "offset_dq[%d] not unit", j);
+    if (!std::isfinite(k->prior_mask[j])) return fail(TRK_ERR_INVALID_ARG, "prior_mask[%d]", j);
+  }
+  for (long long t = 0; t < 3ll * m->n_tris; ++t)
+    if (m->tris[t] < 0 || m->tris[t] >= m->n_verts) return fail(TRK_ERR_INVALID_ARG, "tris[%lld] out of range", t);
+  for (int i = 0; i < m->n_verts; ++i) {
+    double sw = 0;
+    for (int q = 0; q < 4; ++q) {
+      const float w = m->bone_w[4 * i + q];
+      if (!(w >= 0) || m->bone_idx[4 * i + q] >= L) return fail(TRK_ERR_INVALID_ARG, "bone slot %d of vertex %d", q, i);
+      sw += w;
+    }
+    if (std::fabs(sw - 1.0) > 1e-4) return fail(TRK_ERR_INVALID_ARG, "weights of vertex %d sum to %g", i, sw);
+    for (int c2 = 0; c2 < 3; ++c2)
+      if (!std::isfinite(m->verts[3 * i + c2])) return fail(TRK_ERR_NUMERIC, "vertex %d not finite", i);
+  }
+  return TRK_OK;
+}
+
+// Records the whole frame (pose iterations, then shape iterations) on st.
+void enqueue_frame(trk_session* s, cudaStream_t st) {
+  const Dev& d = s->d;
+  const int P = s->prm.pose_iters, S = s->prm.shape_iters;
+  int cur = 0;
+  for (int it = 0; it < P; ++it) {
+    launch_skin(d, cur, st);
+    launch_raster(d, st);
+    launch_visibility(d, st);
+    launch_associate(d, st);
+    launch_normal_equations(d, cur, it, st);
+    launch_lm(d, cur, st);
+  }
+  for (int it = 0; it < S; ++it) {
+    launch_skin(d, cur, st);
+    launch_raster(d, st);
+    launch_visibility(d, st);
+    launch_associate(d, st);
+    cur = launch_shape(d, cur, P + it, st);
+  }
+  if (cur != 0) cudaMemcpyAsync(d.phi[0], d.phi[cur], sizeof(float4) * d.V, cudaMemcpyDeviceToDevice, st);
+}
+
+trk_status ensure_graph(trk_session* s) {
+  if (s->graph) return TRK_OK;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_frame(s, s->stream);
+  CK(cudaStreamEndCapture(s->stream, &g));
+  cudaError_t e = cudaGraphInstantiate(&s->graph, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  return TRK_OK;
+}
+
+trk_status fetch_result(trk_session* s, cudaStream_t st, trk_result* out) {
+  if (!out) return TRK_OK;
+  const Dev& d = s->d;
+  const int ne = s->prm.pose_iters + s->prm.shape_iters;
+  double* h = s->h_pinned;  // [L] theta, [ne] energy, [1] stats
+  CK(cudaMemcpyAsync(h, d.theta, sizeof(double) * d.L, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + d.L, d.energy, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + d.L + ne, d.stats, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+  std::vector<float4> phi;
+  if (out->offsets) {
+    phi.resize(d.V);
+    CK(cudaMemcpyAsync(phi.data(), d.phi[0], sizeof(float4) * d.V, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  if (out->theta) std::memcpy(out->theta, h, sizeof(double) * d.L);
+  if (out->energy) std::memcpy(out->energy, h + d.L, sizeof(double) * ne);
+  int stats[2];
+  std::memcpy(stats, h + d.L + ne, sizeof(stats));
+  out->n_assoc_px = stats[0];
+  out->n_assoc_verts = stats[1];
+  if (out->offsets)
+    for (int i = 0; i < d.V; ++i) {
+      out->offsets[3 * i] = phi[i].x;
+      out->offsets[3 * i + 1] = phi[i].y;
+      out->offsets[3 * i + 2] = phi[i].z;
+    }
+  return TRK_OK;
+}
+
+trk_status sync_check(trk_session* s) {
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s->stream));
+  return TRK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* trk_last_error(void) { return g_err.c_str(); }
+
+void trk_destroy(trk_session* s) {
+  if (!s) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->h_pinned) cudaFreeHost(s->h_pinned);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  cudaSetDevice(cur);
+  delete s;
+}
+
+trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_intrinsics* cam, const trk_params* prm,
+                      trk_session** out) {
+  g_err.clear();
+  if (!out) return fail(TRK_ERR_INVALID_ARG, "out is NULL");
+  TRY(validate(mesh, sk, cam, prm));
+  trk_session* s = new trk_session();
+  struct Guard {
+    trk_session*& s;
+    ~Guard() { if (s) trk_destroy(s); }
+  } guard{s};
+  CK(cudaGetDevice(&s->device));
+  static bool configured[64] = {false};
+  if (s->device < 64 && !configured[s->device]) {
+    configure_kernels();
+    configured[s->device] = true;
+  }
+  CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+  s->prm = *prm;
+  const int L = sk->n_links, V = mesh->n_verts, F = mesh->n_tris, W = cam->width, H = cam->height;
+  Dev& d = s->d;
+  d.V = V; d.F = F; d.L = L; d.NP = L + 1;
+  d.pose_iters = prm->pose_iters; d.shape_iters = prm->shape_iters; d.shape_sweeps = prm->shape_sweeps;
+  d.knn = prm->knn;
+  d.lambda_phi = prm->lambda_phi; d.lambda_N = prm->lambda_N; d.lambda_w = prm->lambda_w;
+  d.cam.W = W; d.cam.H = H; d.cam.fx = cam->fx; d.cam.fy = cam->fy; d.cam.cx = cam->cx; d.cam.cy = cam->cy;
+  d.cam.z_near = prm->z_near_m; d.cam.eps_vis = prm->eps_vis_m; d.cam.tau = prm->cutoff_m; d.cam.R = prm->window_half_px;
+  {  // ring bound: a vertex whose rounded pixel is >= r+1 away projects >= r+1/2 px away, i.e. at an angle
+     // whose distance from p is >= d (r+1/2) / (f sqrt(1 + c_max^2)), c_max = largest |x/z| in the image
+    const double cmx = std::max(cam->cx + 0.5, W - 0.5 - cam->cx) / cam->fx;
+    const double cmy = std::max(cam->cy + 0.5, H - 0.5 - cam->cy) / cam->fy;
+    const double kx = 1.0 / (cam->fx * std::sqrt(1.0 + cmx * cmx)), ky = 1.0 / (cam->fy * std::sqrt(1.0 + cmy * cmy));
+    d.cam.kappa = (float)(std::min(kx, ky) * (1.0 - 1e-4));
+  }
+  // ---- session-local frame: origin at the bind-pose centroid of the template -----------------------
+  double org[3] = {0, 0, 0};
+  for (int i = 0; i < V; ++i)
+    for (int c = 0; c < 3; ++c) org[c] += mesh->verts[3 * i + c];
+  for (int c = 0; c < 3; ++c) org[c] = (double)(float)(org[c] / V);
+  d.cam.ox = (float)org[0]; d.cam.oy = (float)org[1]; d.cam.oz = (float)org[2];
+  d.cam.inv_fx = 1.0 / (double)cam->fx;
+  d.cam.inv_fy = 1.0 / (double)cam->fy;
+  const HDQ pre{{1, 0, 0, 0}, {0, -0.5 * org[0], -0.5 * org[1], -0.5 * org[2]}};  // T(-c)
+  // ---- link table: normalised axes, offsets, conj(bind) from FK at Theta = 0 in FP64 ----------------
+  LinkTable lt{};
+  lt.L = L;
+  lt.pre.r = make_float4(1.f, 0.f, 0.f, 0.f);
+  lt.pre.d = make_float4(0.f, (float)pre.d.x, (float)pre.d.y, (float)pre.d.z);
+  std::vector<HDQ> bind(L);
+  for (int j = 0; j < L; ++j) {
+    lt.parent[j] = sk->parent[j];
+    lt.type[j] = sk->type[j];
+    const float* a = sk->axis + 3 * j;
+    const double an = std::sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
+    for (int c = 0; c < 3; ++c) lt.axis[j][c] = (float)(a[c] / an);
+    const float* o = sk->offset_dq + 8 * j;
+    lt.off[j].r = make_float4(o[0], o[1], o[2], o[3]);
+    lt.off[j].d = make_float4(o[4], o[5], o[6], o[7]);
+    HDQ off{{o[0], o[1], o[2], o[3]}, {o[4], o[5], o[6], o[7]}};
+    HDQ par = sk->parent[j] < 0 ? pre : bind[sk->parent[j]];
+    bind[j] = hdmul(par, off);  // the joint is the identity at theta = 0
+    lt.bindc[j].r = make_float4((float)bind[j].r.w, (float)-bind[j].r.x, (float)-bind[j].r.y, (float)-bind[j].r.z);
+    lt.bindc[j].d = make_float4((float)bind[j].d.w, (float)-bind[j].d.x, (float)-bind[j].d.y, (float)-bind[j].d.z);
+  }
+  // ---- prior weights: (lambda_s S_kk)^2, S_kk = mask_k n_k / |V| --------------------------------------
+  std::vector<double> prior2(L, 0.0);
+  {
+    std::vector<int> stamp(L, -1);
+    std::vector<double> cnt(L, 0.0);
+    for (int i = 0; i < V; ++i)
+      for (int q = 0; q < 4; ++q) {
+        if (!(mesh->bone_w[4 * i + q] > 0)) continue;
+        for (int k = mesh->bone_idx[4 * i + q]; k >= 0; k = sk->parent[k])
+          if (stamp[k] != i) { stamp[k] = i; cnt[k] += 1.0; }
+      }
+    for (int k = 0; k < L; ++k) {
+      const double S = (double)sk->prior_mask[k] * cnt[k] / (double)V;
+      prior2[k] = ((double)prm->lambda_s * S) * ((double)prm->lambda_s * S);
+    }
+  }
+  // ---- vertex -> face lists (faces in ascending order) ---------------------------------------------
+  std::vector<int> csr_off(V + 1, 0), csr_face((size_t)3 * F);
+  for (long long t = 0; t < 3ll * F; ++t) csr_off[mesh->tris[t] + 1]++;
+  for (int i = 0; i < V; ++i) csr_off[i + 1] += csr_off[i];
+  {
+    std::vector<int> fill(csr_off.begin(), csr_off.end() - 1);
+    for (int f = 0; f < F; ++f)
+      for (int c = 0; c < 3; ++c) csr_face[fill[mesh->tris[3 * f + c]]++] = f;
+  }
+  std::vector<int> nbr;
+  knn_grid(V, mesh->verts, prm->knn, nbr);
+  // ---- host staging of per-vertex / per-face arrays -----------------------------------------------
+  std::vector<float4> v0(V), bw(V);
+  std::vector<uchar4> bidx(V);
+  std::vector<int4> tris(F), nb(V);
+  for (int i = 0; i < V; ++i) {
+    v0[i] = make_float4((float)(mesh->verts[3 * i] - org[0]), (float)(mesh->verts[3 * i + 1] - org[1]),
+                        (float)(mesh->verts[3 * i + 2] - org[2]), 0.f);
+    bw[i] = make_float4(mesh->bone_w[4 * i], mesh->bone_w[4 * i + 1], mesh->bone_w[4 * i + 2], mesh->bone_w[4 * i + 3]);
+    bidx[i] = make_uchar4(mesh->bone_idx[4 * i], mesh->bone_idx[4 * i + 1], mesh->bone_idx[4 * i + 2], mesh->bone_idx[4 * i + 3]);
+    nb[i] = make_int4(nbr[4 * i], nbr[4 * i + 1], nbr[4 * i + 2], nbr[4 * i + 3]);
+  }
+  for (int f = 0; f < F; ++f) tris[f] = make_int4(mesh->tris[3 * f], mesh->tris[3 * f + 1], mesh->tris[3 * f + 2], 0);
+  // ---- device allocation ------------------------------------------------------------------------
+  const int NP = L + 1;
+  const size_t npx = (size_t)W * H;
+  d.nblk_jtj = (V + 255) / 256;
+  d.nblk_v = (V + 255) / 256;
+  LinkTable* dlt;
+  float4 *dv0, *dbw, *phi0buf, *phi1buf;
+  uchar4* dbidx;
+  int4 *dtris, *dnb;
+  int *dcsr_off, *dcsr_face;
+  double* dprior;
+  TRY(dalloc(s, &dlt, 1));
+  TRY(dalloc(s, &dv0, V)); TRY(dalloc(s, &dbw, V)); TRY(dalloc(s, &dbidx, V));
+  TRY(dalloc(s, &dtris, F)); TRY(dalloc(s, &dnb, V));
+  TRY(dalloc(s, &dcsr_off, V + 1)); TRY(dalloc(s, &dcsr_face, (size_t)3 * F));
+  TRY(dalloc(s, &dprior, L));
+  TRY(dalloc(s, &phi0buf, V)); TRY(dalloc(s, &phi1buf, V));
+  TRY(dalloc(s, &d.theta, L)); TRY(dalloc(s, &d.lam, 1));
+  TRY(dalloc(s, &d.energy, std::max(1, prm->pose_iters + prm->shape_iters)));
+  TRY(dalloc(s, &d.Hd, L)); TRY(dalloc(s, &d.xi, (size_t)8 * L));
+  TRY(dalloc(s, &d.theta_c, (size_t)kCandidates * L)); TRY(dalloc(s, &d.Hd_c, (size_t)kCandidates * L));
+  TRY(dalloc(s, &d.xi_c, (size_t)kCandidates * L * 8)); TRY(dalloc(s, &d.lm_trials, 8));
+  TRY(dalloc(s, &d.lm_ok, kCandidates));
+  TRY(dalloc(s, &d.v, V)); TRY(dalloc(s, &d.n, V)); TRY(dalloc(s, &d.fn, F)); TRY(dalloc(s, &d.rec, V));
+  TRY(dalloc(s, &d.head, npx)); TRY(dalloc(s, &d.zbuf, npx)); TRY(dalloc(s, &d.corr, npx));
+  TRY(dalloc(s, &d.acc, V)); TRY(dalloc(s, &d.vispix, V)); TRY(dalloc(s, &d.rg, V)); TRY(dalloc(s, &d.phi0, V));
+  float* ddepth;
+  TRY(dalloc(s, &ddepth, npx));
+  TRY(dalloc(s, &s->d_render, npx));
+  TRY(dalloc(s, &d.partial, (size_t)d.nblk_jtj * NP * NP));
+  TRY(dalloc(s, &d.A, (size_t)NP * NP));
+  TRY(dalloc(s, &d.epart, (size_t)std::max(d.nblk_v, 1) * 8));
+  TRY(dalloc(s, &d.counter, 4));
+  TRY(dalloc(s, &d.stats, 4));
+  d.links = dlt; d.v0 = dv0; d.bw = dbw; d.bidx = dbidx; d.tris = dtris; d.nbr = dnb;
+  d.csr_off = dcsr_off; d.csr_face = dcsr_face; d.prior2 = dprior; d.phi[0] = phi0buf; d.phi[1] = phi1buf;
+  d.depth = ddepth;
+  CK(cudaMallocHost(&s->h_pinned, sizeof(double) * (L + prm->pose_iters + prm->shape_iters + 4)));
+  cudaStream_t st = s->stream;
+  CK(cudaMemcpyAsync(dlt, &lt, sizeof(lt), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dv0, v0.data(), sizeof(float4) * V, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dbw, bw.data(), sizeof(float4) * V, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dbidx, bidx.data(), sizeof(uchar4) * V, cudaMemcpyHostToDevice, st));
+  if (F) CK(cudaMemcpyAsync(dtris, tris.data(), sizeof(int4) * F, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dnb, nb.data(), sizeof(int4) * V, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dcsr_off, csr_off.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, st));
+  if (F) CK(cudaMemcpyAsync(dcsr_face, csr_face.data(), sizeof(int) * 3 * F, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dprior, prior2.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d.counter, 0, sizeof(unsigned) * 4, st));
+  CK(cudaMemsetAsync(d.stats, 0, sizeof(int) * 4, st));
+  CK(cudaMemsetAsync(d.energy, 0, sizeof(double) * std::max(1, prm->pose_iters + prm->shape_iters), st));
+  CK(cudaMemsetAsync(d.lm_trials, 0, sizeof(double) * 8, st));
+  CK(cudaMemsetAsync(ddepth, 0, sizeof(float) * npx, st));
+  CK(cudaStreamSynchronize(st));
+  std::vector<double> zero(L, 0.0);
+  TRY(trk_set_pose(s, zero.data(), nullptr));
+  *out = s;
+  s = nullptr;  // disarm the guard
+  return TRK_OK;
+}
+
+trk_status trk_set_pose(trk_session* s, const double* theta, const float* offsets) {
+  if (!s || !theta) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  Dev& d = s->d;
+  for (int j = 0; j < d.L; ++j)
+    if (!std::isfinite(theta[j])) return fail(TRK_ERR_NUMERIC, "theta[%d] not finite", j);
+  std::vector<float4> phi(d.V, make_float4(0.f, 0.f, 0.f, 0.f));
+  if (offsets)
+    for (int i = 0; i < d.V; ++i) {
+      if (!std::isfinite(offsets[3 * i]) || !std::isfinite(offsets[3 * i + 1]) || !std::isfinite(offsets[3 * i + 2]))
+        return fail(TRK_ERR_NUMERIC, "offset %d not finite", i);
+      phi[i] = make_float4(offsets[3 * i], offsets[3 * i + 1], offsets[3 * i + 2], 0.f);
+    }
+  const double lam = s->prm.lambda_k0;
+  CK(cudaMemcpyAsync(d.theta, theta, sizeof(double) * d.L, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(d.phi[0], phi.data(), sizeof(float4) * d.V, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(d.lam, &lam, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  launch_fk(d, s->stream);
+  return sync_check(s);
+}
+
+trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out) {
+  if (!s || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  TRY(ensure_graph(s));
+  const Dev& d = s->d;
+  CK(cudaMemcpyAsync(const_cast<float*>(d.depth), depth_m, sizeof(float) * d.cam.W * d.cam.H, cudaMemcpyHostToDevice,
+                     s->stream));
+  CK(cudaGraphLaunch(s->graph, s->stream));
+  s->last_stream = s->stream;
+  TRY(fetch_result(s, s->stream, out));
+  return sync_check(s);
+}
+
+trk_status trk_track_frame_device(trk_session* s, const float* d_depth_m, void* cuda_stream) {
+  if (!s || !d_depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  TRY(ensure_graph(s));
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : s->stream;
+  const Dev& d = s->d;
+  CK(cudaMemcpyAsync(const_cast<float*>(d.depth), d_depth_m, sizeof(float) * d.cam.W * d.cam.H,
+                     cudaMemcpyDeviceToDevice, st));
+  CK(cudaGraphLaunch(s->graph, st));
+  CK(cudaGetLastError());
+  s->last_stream = st;
+  return TRK_OK;
+}
+
+trk_status trk_read_result(trk_session* s, trk_result* out) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = s->last_stream ? s->last_stream : s->stream;
+  TRY(fetch_result(s, st, out));
+  CK(cudaGetLastError());
+  return TRK_OK;
+}
+
+trk_status trk_render_depth(trk_session* s, const double* theta, const float* offsets, float* depth_m) {
+  if (!s || !theta || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  Dev r = s->d;  // scratch view: FK tables and offsets in candidate / sweep buffers, state untouched
+  r.theta = s->d.theta_c;
+  r.Hd = s->d.Hd_c;
+  r.xi = s->d.xi_c;
+  r.phi[0] = s->d.phi0;
+  std::vector<float4> phi(r.V, make_float4(0.f, 0.f, 0.f, 0.f));
+  if (offsets)
+    for (int i = 0; i < r.V; ++i) phi[i] = make_float4(offsets[3 * i], offsets[3 * i + 1], offsets[3 * i + 2], 0.f);
+  CK(cudaMemcpyAsync(r.theta, theta, sizeof(double) * r.L, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(r.phi[0], phi.data(), sizeof(float4) * r.V, cudaMemcpyHostToDevice, s->stream));
+  launch_fk(r, s->stream);
+  launch_skin(r, 0, s->stream);
+  launch_raster(r, s->stream);
+  launch_depth_from_zbuf(r, s->d_render, s->stream);
+  CK(cudaMemcpyAsync(depth_m, s->d_render, sizeof(float) * r.cam.W * r.cam.H, cudaMemcpyDeviceToHost, s->stream));
+  return sync_check(s);
+}
+
+trk_status trk_set_depth(trk_session* s, const float* depth_m) {
+  if (!s || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  CK(cudaMemcpyAsync(const_cast<float*>(s->d.depth), depth_m, sizeof(float) * s->d.cam.W * s->d.cam.H,
+                     cudaMemcpyHostToDevice, s->stream));
+  return sync_check(s);
+}
+
+trk_status trk_step_skin(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  launch_fk(s->d, s->stream);
+  launch_skin(s->d, 0, s->stream);
+  return sync_check(s);
+}
+trk_status trk_step_raster(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  launch_raster(s->d, s->stream);
+  return sync_check(s);
+}
+trk_status trk_step_visibility(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  // empty buckets first, so that calling this step twice cannot insert a vertex twice
+  CK(cudaMemsetAsync(s->d.head, 0xFF, sizeof(int) * s->d.cam.W * s->d.cam.H, s->stream));
+  launch_visibility(s->d, s->stream);
+  return sync_check(s);
+}
+trk_status trk_step_associate(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  launch_associate(s->d, s->stream);
+  return sync_check(s);
+}
+trk_status trk_step_normal_equations(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  launch_normal_equations(s->d, 0, 0, s->stream);
+  return sync_check(s);
+}
+trk_status trk_step_lm(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  launch_lm(s->d, 0, s->stream);
+  return sync_check(s);
+}
+trk_status trk_step_shape(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  const int cur = launch_shape(s->d, 0, s->prm.pose_iters, s->stream);
+  if (cur != 0)
+    CK(cudaMemcpyAsync(s->d.phi[0], s->d.phi[cur], sizeof(float4) * s->d.V, cudaMemcpyDeviceToDevice, s->stream));
+  return sync_check(s);
+}
+
+trk_status trk_read(trk_session* s, trk_field field, void* dst, size_t bytes) {
+  if (!s || !dst) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  const Dev& d = s->d;
+  const size_t V = d.V, npx = (size_t)d.cam.W * d.cam.H, L = d.L, NP = d.NP;
+  const void* src = nullptr;
+  size_t need = 0;
+  switch (field) {
+    case TRK_FIELD_VERTS: src = d.v; need = V * 16; break;
+    case TRK_FIELD_NORMALS: src = d.n; need = V * 16; break;
+    case TRK_FIELD_ZBUF: src = d.zbuf; need = npx * 8; break;
+    case TRK_FIELD_VISPIX: src = d.vispix; need = V * 4; break;
+    case TRK_FIELD_CORR: src = d.corr; need = npx * 4; break;
+    case TRK_FIELD_ACC: src = d.acc; need = V * 32; break;
+    case TRK_FIELD_NORMAL_EQ: src = d.A; need = NP * NP * 8; break;
+    case TRK_FIELD_THETA: src = d.theta; need = L * 8; break;
+    case TRK_FIELD_PHI: src = d.phi[0]; need = V * 16; break;
+    case TRK_FIELD_LAMBDA: src = d.lam; need = 8; break;
+    case TRK_FIELD_ENERGY: src = d.energy; need = (size_t)(s->prm.pose_iters + s->prm.shape_iters) * 8; break;
+    case TRK_FIELD_LM_TRIALS: src = d.lm_trials; need = 64; break;
+    case TRK_FIELD_SHAPE_RG: src = d.rg; need = V * 16; break;
+    case TRK_FIELD_NEIGHBOURS: src = d.nbr; need = V * 16; break;
+    case TRK_FIELD_PRIOR: src = d.prior2; need = L * 8; break;
+    default: return fail(TRK_ERR_INVALID_ARG, "unknown field %d", (int)field);
+  }
+  if (bytes != need) return fail(TRK_ERR_INVALID_ARG, "field %d needs %zu bytes, got %zu", (int)field, need, bytes);
+  if (need) CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, s->stream));
+  TRY(sync_check(s));
+  if (field == TRK_FIELD_VERTS) {  // session-local frame -> camera frame
+    float4* v = static_cast<float4*>(dst);
+    for (size_t i = 0; i < V; ++i) {
+      v[i].x += d.cam.ox;
+      v[i].y += d.cam.oy;
+      v[i].z += d.cam.oz;
+    }
+  }
+  return TRK_OK;
+}
+
+trk_status trk_get_info(trk_session* s, trk_info* out) {
+  if (!s || !out) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  const Dev& d = s->d;
+  out->n_links = d.L;
+  out->n_verts = d.V;
+  out->n_tris = d.F;
+  out->width = d.cam.W;
+  out->height = d.cam.H;
+  const int per_assoc = (d.F > 0 ? 4 : 3);  // skin, raster, visibility, associate
+  out->kernels_per_frame = s->prm.pose_iters * (per_assoc + 4) + s->prm.shape_iters * (per_assoc + s->prm.shape_sweeps);
+  out->device_bytes = s->device_bytes;
+  return TRK_OK;
+}
+
+trk_status trk_profile_iteration(trk_session* s, int32_t reps, size_t flush_bytes, float* ms) {
+  if (!s || !ms || reps <= 0) return fail(TRK_ERR_INVALID_ARG, "bad argument");
+  const Dev& d = s->d;
+  cudaStream_t st = s->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  void* flush = nullptr;
+  if (flush_bytes) CK(cudaMalloc(&flush, flush_bytes));
+  double acc[TRK_STAGE_COUNT] = {0};
+  int flushes = 0;
+  auto timed = [&](int stage, auto&& fn) -> cudaError_t {
+    if (flush) cudaMemsetAsync(flush, (flushes++) & 0xFF, flush_bytes, st);
+    cudaEventRecord(e0, st);
+    fn();
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) return e;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    acc[stage] += t;
+    return cudaGetLastError();
+  };
+  cudaError_t err = cudaSuccess;
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    err = timed(TRK_STAGE_SKIN, [&] { launch_skin(d, 0, st); });
+    if (!err) err = timed(TRK_STAGE_RASTER, [&] { launch_raster(d, st); });
+    if (!err) err = timed(TRK_STAGE_VISIBILITY, [&] { launch_visibility(d, st); });
+    if (!err) err = timed(TRK_STAGE_ASSOCIATE, [&] { launch_associate(d, st); });
+    if (!err) err = timed(TRK_STAGE_RESID_JTJ, [&] { launch_resid_jtj(d, 0, st); });
+    if (!err) err = timed(TRK_STAGE_REDUCE, [&] { launch_reduce_jtj(d, -1, st); });
+    if (!err) err = timed(TRK_STAGE_LM_SOLVE, [&] { launch_lm_solve(d, st); });
+    if (!err) err = timed(TRK_STAGE_LM_EVAL, [&] { launch_lm_eval(d, 0, st); });
+  }
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    launch_skin(d, 0, st);
+    launch_raster(d, st);
+    launch_visibility(d, st);
+    launch_associate(d, st);
+    int cur = 0;
+    err = timed(TRK_STAGE_SHAPE, [&] { cur = launch_shape(d, 0, -1, st); });
+    if (!err && cur != 0) err = cudaMemcpyAsync(d.phi[0], d.phi[cur], sizeof(float4) * d.V, cudaMemcpyDeviceToDevice, st);
+  }
+  cudaStreamSynchronize(st);
+  if (flush) cudaFree(flush);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(err);
+  for (int k = 0; k < TRK_STAGE_COUNT; ++k) ms[k] = (float)(acc[k] / reps);
+  return TRK_OK;
+}
+
+}  // extern "C"

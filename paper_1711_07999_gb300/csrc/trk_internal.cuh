@@ -1,0 +1,247 @@
+// trk_internal.cuh -- device data layout and dual-quaternion arithmetic shared by the tracker's kernels.
+//
+// Layout in device memory (one session):
+//   links      : LinkTable (parent, type, axis, offset DQ, conj(bind DQ)) -- a few KB, read into shared memory
+//   per vertex : v0[V] float4, phi[2][V] float4 (Jacobi double buffer), bones[V] (uchar4 idx + float4 w),
+//                v[V] float4, n[V] float4 (w = valid), rec[V] float4 (x,y,z, next-in-bucket bits),
+//                acc[V] Acc4 (sum of p_k - v_i in 2^-30 m, count), vispix[V] int, nbr[V] int4, rg[V] float4
+//   per face   : tris[F] int4 (a,b,c,pad), fn[F] float4 face normals
+//   per pixel  : depth[W*H] float, zbuf[W*H] u64, head[W*H] int, corr[W*H] int
+//   solver     : partials[nblk][NP*NP] float, A[NP*NP] double, per-candidate theta / DQ tables
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace trk {
+
+constexpr int kMaxLinks = 79;       // NP = P + 1 <= 80
+constexpr int kMaxNP = 80;
+constexpr int kCandidates = 6;      // damping values tried per LM iteration: lambda * 10^c, c = 0..5
+constexpr float kFix = 1073741824.0f;  // 2^30: fixed-point scale of the per-vertex sums
+
+struct DQ {
+  float4 r, d;  // (w, x, y, z) real and dual parts
+};
+
+// Per-vertex association sums: sum of (p_k - v_i) in units of 2^-30 m, and the pixel count.
+struct __align__(32) Acc4 {
+  long long x, y, z, w;
+};
+
+// All positions on the device live in a session-local frame: the camera frame shifted by the template's
+// bind-pose centroid c (so coordinates stay within ~1 m and FP32 keeps ~1e-7 m of absolute precision).
+// FK starts from pre = T(-c); the bind pose is stored in the same frame.
+struct LinkTable {
+  int L;
+  int parent[kMaxLinks];
+  int type[kMaxLinks];
+  float axis[kMaxLinks][3];
+  DQ pre;               // T(-c)
+  DQ off[kMaxLinks];
+  DQ bindc[kMaxLinks];  // conjugate of the bind-pose DQ T(-c) H^0_{0,j}
+};
+
+// Per-session constants passed by value to the kernels.
+struct Cam {
+  int W, H;
+  float fx, fy, cx, cy;
+  float z_near, eps_vis, tau, kappa;  // kappa: ring-bound factor of the association search
+  int R;                               // window half-size
+  float ox, oy, oz;                    // origin c of the session-local frame (camera coordinates)
+  double inv_fx, inv_fy;
+};
+
+// ---------------------------------------------------------------------------------------------
+// quaternion / dual quaternion arithmetic (FP32)
+// ---------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ float4 qmul(float4 a, float4 b) {
+  return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
+                     a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                     a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y,
+                     a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+}
+__host__ __device__ __forceinline__ float4 qconj(float4 a) { return make_float4(a.x, -a.y, -a.z, -a.w); }
+__host__ __device__ __forceinline__ float4 qadd(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__host__ __device__ __forceinline__ float4 qscale(float4 a, float s) {
+  return make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
+}
+__host__ __device__ __forceinline__ float qdot(float4 a, float4 b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+__host__ __device__ __forceinline__ DQ dqmul(const DQ& a, const DQ& b) {
+  DQ h;
+  h.r = qmul(a.r, b.r);
+  h.d = qadd(qmul(a.r, b.d), qmul(a.d, b.r));
+  return h;
+}
+__host__ __device__ __forceinline__ DQ dqconj(const DQ& a) {
+  DQ h;
+  h.r = qconj(a.r);
+  h.d = qconj(a.d);
+  return h;
+}
+
+// joint transform of link j at value th (hinge: rotation about z; prismatic: translation along z)
+__device__ __forceinline__ DQ joint_dq(int type, const float* z, float th) {
+  DQ h;
+  if (type == 0) {
+    float s, c;
+    sincosf(0.5f * th, &s, &c);
+    h.r = make_float4(c, z[0] * s, z[1] * s, z[2] * s);
+    h.d = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    h.r = make_float4(1.f, 0.f, 0.f, 0.f);
+    h.d = make_float4(0.f, 0.5f * th * z[0], 0.5f * th * z[1], 0.5f * th * z[2]);
+  }
+  return h;
+}
+
+// Forward kinematics of link j by walking its chain from the root: H_{0,j} = prod (off_m J_m(theta_m)).
+// Writes H_{j,Delta} = H_{0,j} conj(H^0_{0,j}) and the twist Xi_j = H_{0,j} G_j conj(H_{0,j}) with
+// G_j = (0, z/2 | 0) for a hinge and (0 | 0, z/2) for a prismatic joint (the joint's generator
+// H_j^{-1} dH_j/dtheta_j): dH_{k,Delta}/dtheta_j = Xi_j H_{k,Delta} for every k below j.
+template <typename ThetaT>
+__device__ __forceinline__ void fk_link(const LinkTable& lt, const ThetaT* theta, int j, DQ* Hd_out,
+                                        float* xi_out /*6*/) {
+  int chain[kMaxLinks];
+  int n = 0;
+  for (int k = j; k >= 0; k = lt.parent[k]) chain[n++] = k;
+  DQ H = lt.pre;
+  for (int t = n - 1; t >= 0; --t) {
+    int m = chain[t];
+    H = dqmul(dqmul(H, lt.off[m]), joint_dq(lt.type[m], lt.axis[m], (float)theta[m]));
+  }
+  *Hd_out = dqmul(H, lt.bindc[j]);
+  DQ G;
+  const float* z = lt.axis[j];
+  if (lt.type[j] == 0) {
+    G.r = make_float4(0.f, 0.5f * z[0], 0.5f * z[1], 0.5f * z[2]);
+    G.d = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    G.r = make_float4(0.f, 0.f, 0.f, 0.f);
+    G.d = make_float4(0.f, 0.5f * z[0], 0.5f * z[1], 0.5f * z[2]);
+  }
+  DQ X = dqmul(dqmul(H, G), dqconj(H));
+  xi_out[0] = X.r.y; xi_out[1] = X.r.z; xi_out[2] = X.r.w;
+  xi_out[3] = X.d.y; xi_out[4] = X.d.z; xi_out[5] = X.d.w;
+}
+
+// Blend of the <= 4 bone offsets of a vertex with the antipodal sign alignment to the heaviest bone
+// (largest weight, ties to the smaller link index).
+__device__ __forceinline__ DQ blend_bones(const DQ* Hd, uchar4 bi, float4 bw, float sg[4]) {
+  const int idx[4] = {bi.x, bi.y, bi.z, bi.w};
+  const float w[4] = {bw.x, bw.y, bw.z, bw.w};
+  int js = -1;
+  float wst = -1.f;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+    if (w[s] > 0.f && (w[s] > wst || (w[s] == wst && idx[s] < js))) { wst = w[s]; js = idx[s]; }
+  const float4 ref = Hd[js < 0 ? 0 : js].r;
+  DQ acc;
+  acc.r = make_float4(0.f, 0.f, 0.f, 0.f);
+  acc.d = acc.r;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    sg[s] = 0.f;
+    if (!(w[s] > 0.f)) continue;
+    const DQ h = Hd[idx[s]];
+    const float g = qdot(h.r, ref) >= 0.f ? 1.f : -1.f;
+    sg[s] = g;
+    acc.r = qadd(acc.r, qscale(h.r, w[s] * g));
+    acc.d = qadd(acc.d, qscale(h.d, w[s] * g));
+  }
+  return acc;
+}
+
+// Homogeneous point map of a (non-unit) blended DQ: (vec(a x a*) + 2 vec(b a*)) / |a|^2.
+__device__ __forceinline__ float3 dq_point(const DQ& H, float3 x) {
+  const float4 a = H.r, b = H.d;
+  const float N = qdot(a, a);
+  const float4 X = make_float4(0.f, x.x, x.y, x.z);
+  const float4 t1 = qmul(qmul(a, X), qconj(a));
+  const float4 t2 = qmul(b, qconj(a));
+  const float inv = 1.f / N;
+  return make_float3((t1.y + 2.f * t2.y) * inv, (t1.z + 2.f * t2.z) * inv, (t1.w + 2.f * t2.w) * inv);
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------------------------
+struct Dev;  // device pointers of one session, defined below
+void launch_fk(const Dev& d, cudaStream_t st);
+void launch_skin(const Dev& d, int phi_buf, cudaStream_t st);
+void launch_raster(const Dev& d, cudaStream_t st);
+void launch_visibility(const Dev& d, cudaStream_t st);
+void launch_associate(const Dev& d, cudaStream_t st);
+// residual + Jacobian + [J r]^T [J r]; writes E_pose to energy[slot] (slot < 0: not recorded)
+void launch_normal_equations(const Dev& d, int phi_buf, int slot, cudaStream_t st);
+void launch_lm(const Dev& d, int phi_buf, cudaStream_t st);
+// the same kernels one at a time (used by the per-kernel timing)
+void launch_resid_jtj(const Dev& d, int phi_buf, cudaStream_t st);
+void launch_reduce_jtj(const Dev& d, int slot, cudaStream_t st);
+void launch_lm_solve(const Dev& d, cudaStream_t st);
+void launch_lm_eval(const Dev& d, int phi_buf, cudaStream_t st);
+// shape step from buffer phi_src; writes E_shape to energy[slot]; returns the buffer holding Phi after it
+int launch_shape(const Dev& d, int phi_src, int slot, cudaStream_t st);
+void launch_depth_from_zbuf(const Dev& d, float* out, cudaStream_t st);
+void configure_kernels();
+
+}  // namespace trk
+
+namespace trk {
+
+// Device pointers and constants of one session (passed by value to every kernel).
+struct Dev {
+  int V, F, L, NP;  // NP = L + 1 (the residual column of [J r])
+  int pose_iters, shape_iters, shape_sweeps, knn;
+  float lambda_phi, lambda_N, lambda_w;
+  Cam cam;
+  const LinkTable* links;
+  // template and derived mesh data
+  const float4* v0;
+  const uchar4* bidx;
+  const float4* bw;
+  const int4* tris;
+  const int* csr_off;
+  const int* csr_face;
+  const int4* nbr;
+  const double* prior2;  // (lambda_s S_kk)^2
+  // tracking state
+  float4* phi[2];
+  double* theta;
+  double* lam;
+  double* energy;
+  DQ* Hd;
+  float* xi;  // [L][8], 6 used
+  // LM candidates
+  double* theta_c;  // [kCandidates][L]
+  DQ* Hd_c;         // [kCandidates][L]
+  float* xi_c;      // [kCandidates][L][8]
+  double* lm_trials;  // [8]
+  int* lm_ok;         // [kCandidates]
+  // per-iteration buffers
+  float4* v;
+  float4* n;
+  float4* fn;
+  float4* rec;
+  int* head;
+  unsigned long long* zbuf;
+  int* corr;
+  Acc4* acc;
+  int* vispix;
+  float4* rg;
+  float4* phi0;
+  const float* depth;
+  // reductions
+  float* partial;   // [nblk_jtj][NP*NP]
+  int nblk_jtj;
+  double* A;        // [NP*NP]
+  double* epart;    // [nblk_v][8]
+  int nblk_v;
+  unsigned int* counter;  // [4] last-block tickets
+  int* stats;             // [0] associated pixels, [1] associated vertices
+};
+
+}  // namespace trk

@@ -1,0 +1,224 @@
+"""ctypes binding of the C ABI in include/trk.h (argument marshalling only; every step of the tracker runs
+in the CUDA kernels of libtrk.so).  Loading fails loudly when the library has not been built or no CUDA
+device is usable: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+TRK_OK, TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA, TRK_ERR_NO_CAPACITY, TRK_ERR_TIMEOUT, TRK_ERR_NUMERIC = range(7)
+MAX_LINKS = 79
+
+FIELDS = dict(VERTS=0, NORMALS=1, ZBUF=2, VISPIX=3, CORR=4, ACC=5, NORMAL_EQ=6, THETA=7, PHI=8, LAMBDA=9, ENERGY=10,
+              LM_TRIALS=11, SHAPE_RG=12, NEIGHBOURS=13, PRIOR=14)
+
+# symbols include/trk.h declares (checked by the tests against the library's exports)
+EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_device", "trk_read_result",
+           "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
+           "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
+           "trk_read", "trk_get_info", "trk_profile_iteration"]
+
+STAGES = ["skin", "raster", "visibility", "associate", "resid_jtj", "reduce", "lm_solve", "lm_eval", "shape"]
+
+
+class TrkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"trk status {status}: {msg}")
+        self.status = status
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("verts", C.c_void_p), ("tris", C.c_void_p),
+                ("bone_idx", C.c_void_p), ("bone_w", C.c_void_p)]
+
+
+class Skeleton(C.Structure):
+    _fields_ = [("n_links", C.c_int32), ("parent", C.c_void_p), ("type", C.c_void_p), ("axis", C.c_void_p),
+                ("offset_dq", C.c_void_p), ("prior_mask", C.c_void_p)]
+
+
+class Intrinsics(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float)]
+
+
+class Params(C.Structure):
+    _fields_ = [("pose_iters", C.c_int32), ("shape_iters", C.c_int32), ("shape_sweeps", C.c_int32),
+                ("lambda_k0", C.c_float), ("lambda_s", C.c_float), ("lambda_phi", C.c_float), ("lambda_N", C.c_float),
+                ("lambda_w", C.c_float), ("cutoff_m", C.c_float), ("eps_vis_m", C.c_float), ("z_near_m", C.c_float),
+                ("window_half_px", C.c_int32), ("knn", C.c_int32), ("precision", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_links", C.c_int32), ("n_verts", C.c_int32), ("n_tris", C.c_int32), ("width", C.c_int32),
+                ("height", C.c_int32), ("kernels_per_frame", C.c_int32), ("device_bytes", C.c_size_t)]
+
+
+class Result(C.Structure):
+    _fields_ = [("theta", C.c_void_p), ("offsets", C.c_void_p), ("energy", C.c_void_p), ("n_assoc_px", C.c_int32),
+                ("n_assoc_verts", C.c_int32)]
+
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libtrk.so (building it first if it is missing or stale and nvcc is available)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1711_07999_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, sz = C.c_void_p, C.c_int32, C.c_size_t
+        sigs = {
+            "trk_create": [vp, vp, vp, vp, C.POINTER(vp)], "trk_set_pose": [vp, vp, vp],
+            "trk_track_frame": [vp, vp, vp], "trk_track_frame_device": [vp, vp, vp], "trk_read_result": [vp, vp],
+            "trk_render_depth": [vp, vp, vp, vp], "trk_set_depth": [vp, vp], "trk_step_skin": [vp],
+            "trk_step_raster": [vp], "trk_step_visibility": [vp], "trk_step_associate": [vp],
+            "trk_step_normal_equations": [vp], "trk_step_lm": [vp], "trk_step_shape": [vp],
+            "trk_read": [vp, i32, vp, sz], "trk_get_info": [vp, vp], "trk_profile_iteration": [vp, i32, sz, vp],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.trk_destroy.argtypes = [vp]
+        L.trk_destroy.restype = None
+        L.trk_last_error.argtypes = []
+        L.trk_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != TRK_OK:
+        raise TrkError(status, lib().trk_last_error().decode())
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def params_struct(p: dict) -> Params:
+    return Params(pose_iters=p["pose_iters"], shape_iters=p["shape_iters"], shape_sweeps=p["shape_sweeps"],
+                  lambda_k0=p["lambda_k0"], lambda_s=p["lambda_s"], lambda_phi=p["lambda_phi"],
+                  lambda_N=p["lambda_N"], lambda_w=p["lambda_w"], cutoff_m=p["cutoff"], eps_vis_m=p["eps_vis"],
+                  z_near_m=p["z_near"], window_half_px=p["window_half"], knn=p["knn"], precision=0)
+
+
+class Session:
+    """One tracking session (trk_create ... trk_destroy) for a model dict of ``synth.make_model`` form."""
+
+    def __init__(self, model: dict):
+        sk, me, cam, pr = model["skeleton"], model["mesh"], model["camera"], model["params"]
+        self._keep = k = dict(
+            parent=np.ascontiguousarray(sk["parent"], np.int32), type=np.ascontiguousarray(sk["type"], np.int32),
+            axis=np.ascontiguousarray(sk["axis"], np.float32), off=np.ascontiguousarray(sk["offset_dq"], np.float32),
+            mask=np.ascontiguousarray(sk["prior_mask"], np.float32),
+            verts=np.ascontiguousarray(me["verts"], np.float32), tris=np.ascontiguousarray(me["tris"], np.int32),
+            bidx=np.ascontiguousarray(me["bone_idx"], np.uint8), bw=np.ascontiguousarray(me["bone_w"], np.float32))
+        self.L, self.V, self.F = len(k["parent"]), len(k["verts"]), len(k["tris"])
+        self.W, self.H = int(cam["width"]), int(cam["height"])
+        self.params = dict(pr)
+        mesh = Mesh(self.V, self.F, _p(k["verts"]), _p(k["tris"]), _p(k["bidx"]), _p(k["bw"]))
+        skel = Skeleton(self.L, _p(k["parent"]), _p(k["type"]), _p(k["axis"]), _p(k["off"]), _p(k["mask"]))
+        intr = Intrinsics(self.W, self.H, cam["fx"], cam["fy"], cam["cx"], cam["cy"])
+        prm = params_struct(pr)
+        h = C.c_void_p()
+        _check(lib().trk_create(C.byref(mesh), C.byref(skel), C.byref(intr), C.byref(prm), C.byref(h)))
+        self.h = h
+        self.n_energy = pr["pose_iters"] + pr["shape_iters"]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().trk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- state / frames ---------------------------------------------------------------------------
+    def set_pose(self, theta, offsets=None):
+        th = np.ascontiguousarray(theta, np.float64)
+        of = None if offsets is None else np.ascontiguousarray(offsets, np.float32).reshape(self.V, 3)
+        _check(lib().trk_set_pose(self.h, _p(th), _p(of)))
+
+    def _result(self, want_offsets=True):
+        th = np.empty(self.L, np.float64)
+        of = np.empty((self.V, 3), np.float32) if want_offsets else None
+        en = np.empty(max(self.n_energy, 1), np.float64)
+        r = Result(_p(th), _p(of), _p(en), 0, 0)
+        return r, th, of, en
+
+    def track_frame(self, depth, want_offsets=True) -> dict:
+        """Host depth [H, W] float32 metres; returns theta, offsets, energy and association counts."""
+        dep = np.ascontiguousarray(depth, np.float32)
+        assert dep.size == self.W * self.H
+        r, th, of, en = self._result(want_offsets)
+        _check(lib().trk_track_frame(self.h, _p(dep), C.byref(r)))
+        return dict(theta=th, offsets=of, energy=en[:self.n_energy], n_assoc_px=r.n_assoc_px,
+                    n_assoc_verts=r.n_assoc_verts)
+
+    def track_frame_device(self, depth_ptr: int, stream_ptr: int = 0):
+        """Enqueues a frame reading depth from a device pointer (e.g. ``tensor.data_ptr()``) on a CUDA
+        stream handle (e.g. ``torch.cuda.Stream().cuda_stream``); returns without waiting."""
+        _check(lib().trk_track_frame_device(self.h, C.c_void_p(depth_ptr), C.c_void_p(stream_ptr or None)))
+
+    def read_result(self, want_offsets=True) -> dict:
+        r, th, of, en = self._result(want_offsets)
+        _check(lib().trk_read_result(self.h, C.byref(r)))
+        return dict(theta=th, offsets=of, energy=en[:self.n_energy], n_assoc_px=r.n_assoc_px,
+                    n_assoc_verts=r.n_assoc_verts)
+
+    def render_depth(self, theta, offsets=None) -> np.ndarray:
+        out = np.empty((self.H, self.W), np.float32)
+        th = np.ascontiguousarray(theta, np.float64)
+        of = None if offsets is None else np.ascontiguousarray(offsets, np.float32).reshape(self.V, 3)
+        _check(lib().trk_render_depth(self.h, _p(th), _p(of), _p(out)))
+        return out
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib().trk_get_info(self.h, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def profile_iteration(self, reps: int = 10, flush_bytes: int = 0) -> dict:
+        """Mean CUDA-event duration (ms) of each stage of an iteration, at the current state and depth."""
+        ms = np.empty(len(STAGES), np.float32)
+        _check(lib().trk_profile_iteration(self.h, reps, flush_bytes, _p(ms)))
+        return dict(zip(STAGES, ms.tolist()))
+
+    # -- step-level calls -------------------------------------------------------------------------
+    def set_depth(self, depth):
+        dep = np.ascontiguousarray(depth, np.float32)
+        _check(lib().trk_set_depth(self.h, _p(dep)))
+
+    def step(self, name: str):
+        _check(getattr(lib(), "trk_step_" + name)(self.h))
+
+    def read(self, field: str) -> np.ndarray:
+        V, npx, L, NP = self.V, self.W * self.H, self.L, self.L + 1
+        shapes = dict(VERTS=((V, 4), np.float32), NORMALS=((V, 4), np.float32), ZBUF=((npx,), np.uint64),
+                      VISPIX=((V,), np.int32), CORR=((npx,), np.int32), ACC=((V, 4), np.int64),
+                      NORMAL_EQ=((NP, NP), np.float64), THETA=((L,), np.float64), PHI=((V, 4), np.float32),
+                      LAMBDA=((1,), np.float64), ENERGY=((self.n_energy,), np.float64), LM_TRIALS=((8,), np.float64),
+                      SHAPE_RG=((V, 4), np.float32), NEIGHBOURS=((V, 4), np.int32), PRIOR=((L,), np.float64))
+        shp, dt = shapes[field]
+        out = np.empty(shp, dt)
+        _check(lib().trk_read(self.h, FIELDS[field], _p(out), out.nbytes))
+        return out
