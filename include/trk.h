@@ -195,6 +195,19 @@ typedef enum {
  * (outside the timed interval) so that every stage starts from a cold L2. */
 trk_status trk_profile_iteration(trk_session* s, int32_t reps, size_t flush_bytes, float* ms);
 
+/* ---- Standalone contraction ------------------------------------------------------------------- */
+
+/* [J r]^T [J r] of materialised rows (Eqs. JTJ, JTr): d_rows is device FP32 [n_rows][ld], each row the
+ * Jacobian entries of one residual followed by the residual itself in its first n_cols columns; d_out
+ * receives device FP64 [n_cols][n_cols], row-major and symmetric (J^T J, J^T r and r^T r as blocks).
+ * Products are formed in FP32 and summed per CTA in FP32, the CTA partials in FP64 in a fixed order.
+ * Enqueued on cuda_stream (a cudaStream_t, NULL = the legacy default stream); returns without waiting.
+ * Scratch for the per-CTA partials (at most 296 n_cols^2 floats) comes from the stream-ordered
+ * allocator of the current device and is released on the stream.  1 <= n_cols <= 80, ld >= n_cols,
+ * n_rows >= 0 (0 rows gives zeros).  Errors: TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA. */
+trk_status trk_jtj_rows(const float* d_rows, int32_t n_rows, int32_t n_cols, int32_t ld, double* d_out,
+                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

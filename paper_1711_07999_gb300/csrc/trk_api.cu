@@ -111,6 +111,11 @@ void knn_grid(int V, const float* xyz, int K, std::vector<int>& nbr) {
 
 }  // namespace
 
+int trk::set_error_code(int st, const char* msg) {
+  g_err = msg ? msg : "";
+  return st;
+}
+
 struct trk_session {
   Dev d{};
   int device = 0;

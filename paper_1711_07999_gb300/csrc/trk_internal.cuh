@@ -188,6 +188,11 @@ int launch_shape(const Dev& d, int phi_src, int slot, cudaStream_t st);
 void launch_depth_from_zbuf(const Dev& d, float* out, cudaStream_t st);
 void configure_kernels();
 
+// Records msg as this thread's last error (read by trk_last_error) and returns st.
+int set_error_code(int st, const char* msg);
+template <typename S>
+inline S set_error(S st, const char* msg) { return static_cast<S>(set_error_code(static_cast<int>(st), msg)); }
+
 }  // namespace trk
 
 namespace trk {
