@@ -208,6 +208,20 @@ trk_status trk_profile_iteration(trk_session* s, int32_t reps, size_t flush_byte
 trk_status trk_jtj_rows(const float* d_rows, int32_t n_rows, int32_t n_cols, int32_t ld, double* d_out,
                         void* cuda_stream);
 
+/* The same contraction for callers that must not allocate device memory: a real-time frame loop that
+ * may not call the CUDA allocator once running (cudaMalloc and cudaFree can synchronise the device and
+ * take unbounded time), or a host whose device memory is owned by another allocator or a fixed budget
+ * that forbids side allocations.  The paper has no counterpart; this is an interface for such callers.
+ * Arguments and results are those of trk_jtj_rows; the caller passes the rows and the output buffer.
+ * Scratch: a fixed array of 152 x 80 x 80 floats (3.9 MB) that every device loading this library holds
+ * until the process exits, shared by all calls.  Each call overwrites the part it uses, so no clearing
+ * is needed, but calls that overlap on the GPU (concurrent streams, threads) race on it: serialise them.
+ * No allocation of any kind is made.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before any stream capture.
+ * Errors: TRK_ERR_INVALID_ARG (n_cols outside [1, 80], bad pointers or sizes), TRK_ERR_CUDA. */
+trk_status trk_jtj_rows_noalloc(const float* d_rows, int32_t n_rows, int32_t n_cols, int32_t ld, double* d_out,
+                                void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 // then added in CTA order in FP64 (deterministic for a given grid).
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "../../include/trk.h"
@@ -96,6 +97,36 @@ cudaError_t jtj_rows_launch(const float* rows, int n, int nc, int ld, double* ou
 
 int jtj_rows_blocks(int n) { return std::max(1, std::min(kJMaxBlocks, (n + kJBlock - 1) / kJBlock)); }
 
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant: the per-CTA partials live in a fixed file-scope device array (at most
+// kNoAllocBlocks CTAs x 80 x 80 floats, 3.9 MB held by every device that loads the library).  Each CTA
+// overwrites its whole partial on every call, so nothing has to be cleared between calls.
+// ---------------------------------------------------------------------------------------------
+constexpr int kNoAllocBlocks = 152;
+static __device__ __align__(256) float g_noalloc_partial[kNoAllocBlocks * kMaxNP * kMaxNP];
+
+constexpr int kMaxDevices = 64;
+static float* g_noalloc_ptr[kMaxDevices];
+static std::mutex g_noalloc_mutex;
+
+// Device address of g_noalloc_partial on the current device (looked up once per device).  In host code
+// the symbol itself is only a host-side stand-in, never a device address.
+static cudaError_t noalloc_scratch(float** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    float* p = nullptr;
+    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_partial);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
 }  // namespace trk
 
 extern "C" {
@@ -114,6 +145,21 @@ trk_status trk_jtj_rows(const float* d_rows, int32_t n_rows, int32_t n_cols, int
   const cudaError_t f = cudaFreeAsync(partial, st);
   if (e != cudaSuccess) return trk::set_error(TRK_ERR_CUDA, cudaGetErrorString(e));
   if (f != cudaSuccess) return trk::set_error(TRK_ERR_CUDA, cudaGetErrorString(f));
+  return TRK_OK;
+}
+
+trk_status trk_jtj_rows_noalloc(const float* d_rows, int32_t n_rows, int32_t n_cols, int32_t ld, double* d_out,
+                                void* cuda_stream) {
+  if (!d_rows || !d_out || n_rows < 0 || ld < n_cols)
+    return trk::set_error(TRK_ERR_INVALID_ARG, "trk_jtj_rows_noalloc: bad arguments");
+  if (n_cols <= 0 || n_cols > trk::kMaxNP)
+    return trk::set_error(TRK_ERR_INVALID_ARG, "trk_jtj_rows_noalloc: n_cols must be in [1, 80] (fixed scratch size)");
+  float* partial = nullptr;
+  cudaError_t e = trk::noalloc_scratch(&partial);
+  if (e != cudaSuccess) return trk::set_error(TRK_ERR_CUDA, cudaGetErrorString(e));
+  const int nblk = std::min(trk::kNoAllocBlocks, trk::jtj_rows_blocks(n_rows));
+  e = trk::jtj_rows_launch(d_rows, n_rows, n_cols, ld, d_out, nblk, partial, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return trk::set_error(TRK_ERR_CUDA, cudaGetErrorString(e));
   return TRK_OK;
 }
 

@@ -23,7 +23,7 @@ FIELDS = dict(VERTS=0, NORMALS=1, ZBUF=2, VISPIX=3, CORR=4, ACC=5, NORMAL_EQ=6, 
 EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_device", "trk_read_result",
            "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
-           "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows"]
+           "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc"]
 
 STAGES = ["skin", "raster", "visibility", "associate", "resid_jtj", "reduce", "lm_solve", "lm_eval", "shape"]
 
@@ -86,7 +86,7 @@ def lib(build_if_missing: bool = True):
             "trk_step_raster": [vp], "trk_step_visibility": [vp], "trk_step_associate": [vp],
             "trk_step_normal_equations": [vp], "trk_step_lm": [vp], "trk_step_shape": [vp],
             "trk_read": [vp, i32, vp, sz], "trk_get_info": [vp, vp], "trk_profile_iteration": [vp, i32, sz, vp],
-            "trk_jtj_rows": [vp, i32, i32, i32, vp, vp],
+            "trk_jtj_rows": [vp, i32, i32, i32, vp, vp], "trk_jtj_rows_noalloc": [vp, i32, i32, i32, vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -114,6 +114,12 @@ def jtj_rows(rows_ptr: int, n_rows: int, n_cols: int, ld: int, out_ptr: int, str
     given CUDA stream handle; device pointers e.g. from ``tensor.data_ptr()``)."""
     _check(lib().trk_jtj_rows(C.c_void_p(rows_ptr), n_rows, n_cols, ld, C.c_void_p(out_ptr),
                               C.c_void_p(stream_ptr or None)))
+
+
+def jtj_rows_noalloc(rows_ptr: int, n_rows: int, n_cols: int, ld: int, out_ptr: int, stream_ptr: int = 0):
+    """trk_jtj_rows without any allocation (fixed scratch, n_cols <= 80; overlapping calls race)."""
+    _check(lib().trk_jtj_rows_noalloc(C.c_void_p(rows_ptr), n_rows, n_cols, ld, C.c_void_p(out_ptr),
+                                      C.c_void_p(stream_ptr or None)))
 
 
 def params_struct(p: dict) -> Params:
