@@ -168,7 +168,9 @@ typedef enum {
   TRK_FIELD_SHAPE_RG = 12,/* float[n_verts][4]: g_i = dr_i/dphi_i and r_i of the last shape step */
   TRK_FIELD_NEIGHBOURS = 13,/* int32[n_verts][4]: N(i), -1 pads                              */
   TRK_FIELD_PRIOR = 14,   /* double[n_links]: (lambda_s S_kk)^2                              */
-  TRK_FIELD_COUNT = 15
+  TRK_FIELD_LM_SOLVER = 15,/* int32[6]: per damping candidate of the last LM step, refinement iterations
+                              of the mixed-precision solve, -1 = FP64 fallback, -2 = not positive definite */
+  TRK_FIELD_COUNT = 16
 } trk_field;
 
 /* Copies a session buffer to host memory; bytes must equal the field's size exactly. */

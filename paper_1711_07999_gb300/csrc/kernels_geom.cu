@@ -19,18 +19,11 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 // ---------------------------------------------------------------------------------------------
 __global__ void k_fk(Dev d) {
   __shared__ LinkTable lt;
+  __shared__ DQ H0[kMaxLinks];
   for (int t = threadIdx.x; t < (int)(sizeof(LinkTable) / 4); t += blockDim.x)
     reinterpret_cast<int*>(&lt)[t] = reinterpret_cast<const int*>(d.links)[t];
   __syncthreads();
-  for (int j = threadIdx.x; j < d.L; j += blockDim.x) {
-    DQ H;
-    float xi[6];
-    fk_link(lt, d.theta, j, &H, xi);
-    d.Hd[j] = H;
-    for (int c = 0; c < 6; ++c) d.xi[8 * j + c] = xi[c];
-    d.xi[8 * j + 6] = 0.f;
-    d.xi[8 * j + 7] = 0.f;
-  }
+  fk_all(lt, d.theta, H0, d.Hd, d.xi, 8);
 }
 
 void launch_fk(const Dev& d, cudaStream_t st) { k_fk<<<1, 128, 0, st>>>(d); }
@@ -54,6 +47,8 @@ __global__ void __launch_bounds__(kBlock) k_skin(Dev d, int phi_buf) {
   if (tid == 0) {
     d.stats[0] = 0;
     d.stats[1] = 0;
+    d.qctl[0] = 0;
+    d.qctl[1] = 0;
   }
   const float4* phi = d.phi[phi_buf];
   for (int i = tid; i < d.V; i += stride) {
@@ -160,6 +155,9 @@ __global__ void __launch_bounds__(kBlock) k_visibility(Dev d) {
         vp = k;
         const int old = atomicExch(&d.head[k], i);
         d.rec[i] = make_float4(pl.x, pl.y, pl.z, __int_as_float(old));
+        // the first vertex of a bucket is also stored with the pixel, so that a bucket holding one vertex
+        // is read with two independent loads (head, pixrec) instead of a dependent chain
+        if (old < 0) d.pixrec[k] = make_float4(pl.x, pl.y, pl.z, __int_as_float(i));
       }
     }
   }
@@ -179,26 +177,31 @@ void launch_visibility(const Dev& d, cudaStream_t st) {
 // that angle into a distance from p), so the search stops once that bound exceeds the best distance
 // or tau: the result is the same argmin as the exhaustive window search.
 //
-// Rings 0..kRingsPerThread are searched by the pixel's own thread; the few pixels that need more rings
-// (no vertex within ~1-2 cm: silhouettes, holes) are finished cooperatively by their warp, one pixel at
-// a time, the lanes splitting each ring's 8r buckets and combining (d^2, index) keys with a warp-min.
+// k_associate: rings 0..kRingsPerThread by the pixel's own thread, each ring's bucket heads and first
+// records loaded together.  Pixels still open after that (no vertex within ~1-2 cm: the first iterations
+// of a frame, silhouettes) go to a queue that k_associate_tail drains with one warp per pixel, the lanes
+// splitting each ring's 8r buckets and combining (d^2, index) keys with a warp-min.
 // The pixel's offset p - v_i is added to the vertex's fixed-point sums (integer atomics: the sums do
 // not depend on the order of the additions).
 // ---------------------------------------------------------------------------------------------
 constexpr int kRingsPerThread = 2;
 
-__device__ __forceinline__ void scan_bucket(const Dev& d, int q, float3 p, float tau2, int& best, float& bd2) {
-  int i = __ldg(&d.head[q]);
+__device__ __forceinline__ void consider(int i, float3 p, float4 r, float tau2, int& best, float& bd2) {
+  const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
+  const float d2 = dx * dx + dy * dy + dz * dz;
+  if (d2 <= tau2 && (best < 0 || d2 < bd2 || (d2 == bd2 && i < best))) {
+    best = i;
+    bd2 = d2;
+  }
+}
+
+// the rest of a bucket after its first record: walk from the head until the first record is reached
+__device__ __forceinline__ void scan_rest(const Dev& d, int h, int first, float3 p, float tau2, int& best, float& bd2) {
   // a bucket list never holds more than |V| entries; the hop bound only guards against misuse
-  for (int hops = 0; i >= 0 && hops < d.V; ++hops) {
-    const float4 r = d.rec[i];
-    const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
-    const float d2 = dx * dx + dy * dy + dz * dz;
-    if (d2 <= tau2 && (best < 0 || d2 < bd2 || (d2 == bd2 && i < best))) {
-      best = i;
-      bd2 = d2;
-    }
-    i = __float_as_int(r.w);
+  for (int hops = 0; h >= 0 && h != first && hops < d.V; ++hops) {
+    const float4 r = d.rec[h];
+    consider(h, p, r, tau2, best, bd2);
+    h = __float_as_int(r.w);
   }
 }
 
@@ -213,8 +216,43 @@ __device__ __forceinline__ int ring_bucket(int px, int py, int r, int t, int W, 
   return (x >= 0 && y >= 0 && x < W && y < H) ? y * W + x : -1;
 }
 
+// Scans up to N buckets whose pixel indices are in q[0..N) (-1 = none) with all first loads in flight.
+template <int N>
+__device__ __forceinline__ void scan_group(const Dev& d, const int* q, float3 p, float tau2, int& best, float& bd2) {
+  int h[N];
+  float4 f[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    h[u] = q[u] >= 0 ? __ldg(&d.head[q[u]]) : -1;
+    f[u] = q[u] >= 0 ? d.pixrec[q[u]] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+  }
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    if (h[u] < 0) continue;
+    const int first = __float_as_int(f[u].w);
+    consider(first, p, f[u], tau2, best, bd2);
+    if (h[u] != first) scan_rest(d, h[u], first, p, tau2, best, bd2);
+  }
+}
+
 __device__ __forceinline__ unsigned long long key_of(int best, float bd2) {
   return best < 0 ? ~0ull : (((unsigned long long)__float_as_uint(bd2) << 32) | (unsigned)best);
+}
+
+__device__ __forceinline__ void commit_pixel(const Dev& d, int best, float3 p) {
+  const float4 vb = d.v[best];
+  unsigned long long* a = reinterpret_cast<unsigned long long*>(&d.acc[best]);
+  atomicAdd(a + 0, (unsigned long long)__float2ll_rn((p.x - vb.x) * kFix));
+  atomicAdd(a + 1, (unsigned long long)__float2ll_rn((p.y - vb.y) * kFix));
+  atomicAdd(a + 2, (unsigned long long)__float2ll_rn((p.z - vb.z) * kFix));
+  atomicAdd(a + 3, 1ull);
+}
+
+__device__ __forceinline__ float3 back_project(const Cam& c, int px, int py, float dep) {
+  // in FP64, then moved into the session-local frame (exact up to one FP32 rounding)
+  return make_float3((float)(((double)px - (double)c.cx) * (double)dep * c.inv_fx - (double)c.ox),
+                     (float)(((double)py - (double)c.cy) * (double)dep * c.inv_fy - (double)c.oy),
+                     (float)((double)dep - (double)c.oz));
 }
 
 __global__ void __launch_bounds__(kBlock) k_associate(Dev d) {
@@ -229,43 +267,63 @@ __global__ void __launch_bounds__(kBlock) k_associate(Dev d) {
   int best = -1;
   float bd2 = 0.f;
   float3 p = make_float3(0.f, 0.f, 0.f);
-  bool open = false;  // still searching after the thread-owned rings
+  bool open = false;
   if (dep > 0.f) {
-    // back-projection in FP64, then moved into the session-local frame (exact up to one FP32 rounding)
-    p = make_float3((float)(((double)px - (double)c.cx) * (double)dep * c.inv_fx - (double)c.ox),
-                    (float)(((double)py - (double)c.cy) * (double)dep * c.inv_fy - (double)c.oy),
-                    (float)((double)dep - (double)c.oz));
+    p = back_project(c, px, py, dep);
     open = true;
-    const int rmax = min(c.R, kRingsPerThread);
-    for (int r = 0; r <= rmax; ++r) {
+    for (int r = 0; r <= min(c.R, kRingsPerThread); ++r) {
       if (r == 0) {
-        scan_bucket(d, k, p, tau2, best, bd2);
+        const int q0[1] = {k};
+        scan_group<1>(d, q0, p, tau2, best, bd2);
       } else {
-        for (int t = 0; t < 8 * r; ++t) {
-          const int q = ring_bucket(px, py, r, t, c.W, c.H);
-          if (q >= 0) scan_bucket(d, q, p, tau2, best, bd2);
+        for (int t0 = 0; t0 < 8 * r; t0 += 8) {
+          int q[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) q[u] = ring_bucket(px, py, r, t0 + u, c.W, c.H);
+          scan_group<8>(d, q, p, tau2, best, bd2);
         }
       }
       const float lb = dep * ((float)r + 0.499f) * c.kappa;
       if (lb > c.tau || (best >= 0 && lb * lb > bd2) || r == c.R) { open = false; break; }
     }
   }
-  // warp-cooperative completion of the open pixels, one at a time
-  unsigned pending = __ballot_sync(0xffffffffu, open);
-  while (pending) {
-    const int src = __ffs(pending) - 1;
-    pending &= pending - 1;
-    const int sx = __shfl_sync(0xffffffffu, px, src), sy = __shfl_sync(0xffffffffu, py, src);
-    const float sdep = __shfl_sync(0xffffffffu, dep, src);
-    const float3 sp = make_float3(__shfl_sync(0xffffffffu, p.x, src), __shfl_sync(0xffffffffu, p.y, src),
-                                  __shfl_sync(0xffffffffu, p.z, src));
+  // queue the open pixels (one atomic per warp)
+  const unsigned om = __ballot_sync(0xffffffffu, open);
+  unsigned base = 0;
+  if (lane == 0 && om) base = atomicAdd(&d.qctl[0], __popc(om));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (open) d.queue[base + __popc(om & ((1u << lane) - 1u))] = make_int4(k, best, __float_as_int(bd2), 0);
+  if (inimg && !open) d.corr[k] = best;
+  const bool done = !open && best >= 0;
+  if (done) commit_pixel(d, best, p);
+  const unsigned m = __ballot_sync(0xffffffffu, done);
+  if (lane == 0 && m) atomicAdd(&d.stats[0], __popc(m));
+}
+
+constexpr int kTailWarps = 8;
+
+__global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
+  const Cam c = d.cam;
+  const int lane = threadIdx.x & 31;
+  const float tau2 = c.tau * c.tau;
+  const unsigned n = *(volatile unsigned*)&d.qctl[0];
+  int done = 0;
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&d.qctl[1], 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n) break;
+    const int4 e = d.queue[item];
+    const int k = e.x, px = k % c.W, py = k / c.W;
+    const float dep = d.depth[k];
+    const float3 p = back_project(c, px, py, dep);
+    unsigned long long key = key_of(e.y, __int_as_float(e.z));
     int wb = -1;
     float wd2 = 0.f;
-    unsigned long long key = key_of(__shfl_sync(0xffffffffu, best, src), __shfl_sync(0xffffffffu, bd2, src));
     for (int r = kRingsPerThread + 1; r <= c.R; ++r) {
-      for (int t = lane; t < 8 * r; t += 32) {
-        const int q = ring_bucket(sx, sy, r, t, c.W, c.H);
-        if (q >= 0) scan_bucket(d, q, sp, tau2, wb, wd2);
+      for (int t0 = 0; t0 < 8 * r; t0 += 32) {
+        const int q[1] = {t0 + lane < 8 * r ? ring_bucket(px, py, r, t0 + lane, c.W, c.H) : -1};
+        scan_group<1>(d, q, p, tau2, wb, wd2);
       }
       unsigned long long kk = key_of(wb, wd2);
       kk = kk < key ? kk : key;
@@ -275,31 +333,25 @@ __global__ void __launch_bounds__(kBlock) k_associate(Dev d) {
         kk = other < kk ? other : kk;
       }
       key = kk;
-      const float lb = sdep * ((float)r + 0.499f) * c.kappa;
-      const float kd2 = key == ~0ull ? 0.f : __uint_as_float((unsigned)(key >> 32));
-      if (lb > c.tau || (key != ~0ull && lb * lb > kd2)) break;
+      const float lb = dep * ((float)r + 0.499f) * c.kappa;
+      if (lb > c.tau || (key != ~0ull && lb * lb > __uint_as_float((unsigned)(key >> 32)))) break;
     }
-    if (lane == src && key != ~0ull) {
-      best = (int)(unsigned)(key & 0xffffffffu);
-      bd2 = __uint_as_float((unsigned)(key >> 32));
+    const int best = key == ~0ull ? -1 : (int)(unsigned)(key & 0xffffffffu);
+    if (lane == 0) {
+      d.corr[k] = best;
+      if (best >= 0) {
+        commit_pixel(d, best, p);
+        ++done;
+      }
     }
   }
-  if (inimg) d.corr[k] = best;
-  if (best >= 0) {
-    const float4 vb = d.v[best];
-    unsigned long long* a = reinterpret_cast<unsigned long long*>(&d.acc[best]);
-    atomicAdd(a + 0, (unsigned long long)__float2ll_rn((p.x - vb.x) * kFix));
-    atomicAdd(a + 1, (unsigned long long)__float2ll_rn((p.y - vb.y) * kFix));
-    atomicAdd(a + 2, (unsigned long long)__float2ll_rn((p.z - vb.z) * kFix));
-    atomicAdd(a + 3, 1ull);
-  }
-  const unsigned m = __ballot_sync(0xffffffffu, best >= 0);
-  if (lane == 0 && m) atomicAdd(&d.stats[0], __popc(m));
+  if (lane == 0 && done) atomicAdd(&d.stats[0], done);
 }
 
 void launch_associate(const Dev& d, cudaStream_t st) {
   dim3 g((d.cam.W + 15) / 16, (d.cam.H + 15) / 16);
   k_associate<<<g, kBlock, 0, st>>>(d);
+  k_associate_tail<<<2 * 152, 32 * kTailWarps, 0, st>>>(d);
 }
 
 __global__ void k_depth_from_zbuf(Dev d, float* out) {

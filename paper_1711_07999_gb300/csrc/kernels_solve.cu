@@ -195,101 +195,287 @@ void launch_normal_equations(const Dev& d, int phi_buf, int slot, cudaStream_t s
 // b = J^T r + (lambda_s S)^2 Theta and lambda_c = min(lambda 10^c, 1e7); a parameter whose diagonal is
 // zero is frozen (x_k = 0).  Theta_c = Theta - x and its FK tables follow.
 //
-// FP64 Cholesky, right-looking, two block barriers per column: (1) scale column k by 1/L_kk (computed
-// with one rsqrt by the thread that finished the pivot in the previous update) into a contiguous copy,
-// (2) rank-1 update of the trailing triangle, one warp per row, lanes across the columns.  No FP64
-// division is issued.  The two triangular solves run on one warp (warp-synchronous).
+// On this GPU a dependent FP64 FMA costs ~70 cycles and an FP64 rsqrt ~440 (FP32: ~4 and ~20), so the
+// P sequential pivot steps of an FP64 Cholesky are latency-bound (~80 us at P = 55).  The solve therefore
+// factors the Jacobi-scaled matrix D M D (unit diagonal) in FP32 and reaches FP64 accuracy by iterative
+// refinement: x += D (D M D)^-1 D (b - M x) with the residual in FP64, until the scaled residual is below
+// 1e-10 of the scaled right-hand side.  If the FP32 factorisation breaks down or the refinement stalls,
+// the FP64 Cholesky factorisation of M is used instead.
 // ---------------------------------------------------------------------------------------------
 constexpr int kSolveThreads = 256;
+constexpr int kMaxRefine = 8;
 
-__device__ __forceinline__ bool pivot_inv(double p, double& l, double& inv) {
-  if (!(p > 0.0)) return false;
-  inv = rsqrt(p);
-  l = p * inv;
+__device__ void chol_solve_fp64(double* M, double* b, int P, int& fail_out) {
+  __shared__ int fail;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int k = 0; k < P; ++k) {
+    if (tid == 0) {
+      const double piv = M[k * P + k];
+      if (!(piv > 0.0)) fail = 1;
+      M[k * P + k] = sqrt(fmax(piv, 0.0));
+    }
+    __syncthreads();
+    if (fail) break;
+    const double ik = 1.0 / M[k * P + k];
+    for (int r = k + 1 + tid; r < P; r += nt) M[r * P + k] *= ik;
+    __syncthreads();
+    const int n = P - k - 1;
+    for (int e = tid; e < n * n; e += nt) {
+      const int r = k + 1 + e / n, q = k + 1 + e % n;
+      if (q <= r) M[r * P + q] -= M[r * P + k] * M[q * P + k];
+    }
+    __syncthreads();
+  }
+  if (!fail) {
+    for (int k = 0; k < P; ++k) {
+      if (tid == 0) b[k] /= M[k * P + k];
+      __syncthreads();
+      for (int r = k + 1 + tid; r < P; r += nt) b[r] -= M[r * P + k] * b[k];
+      __syncthreads();
+    }
+    for (int k = P - 1; k >= 0; --k) {
+      if (tid == 0) b[k] /= M[k * P + k];
+      __syncthreads();
+      for (int r = tid; r < k; r += nt) b[r] -= M[k * P + r] * b[k];
+      __syncthreads();
+    }
+  }
+  fail_out = fail;
+  __syncthreads();
+}
+
+// (r, q) of the e-th lower-triangle element in row-major order (e = r (r + 1) / 2 + q, q <= r)
+__device__ __forceinline__ void tri_rc(int e, int& r, int& q) {
+  int rr = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+  while (rr * (rr + 1) / 2 > e) --rr;
+  r = rr;
+  q = e - rr * (rr + 1) / 2;
+}
+
+constexpr int kBlk = 8;         // block size of the factorisation
+constexpr int kMaxPad = 80;     // P padded to a multiple of kBlk
+
+// Blocked FP32 Cholesky of the padded matrix F (lower triangle, in place), 1/L_kk into ivd.  Per block
+// column: (1) warp 0 factors the 8x8 diagonal block in registers (lane = row, shuffles for the column),
+// (2) one thread per row below solves its 8 entries against that block, (3) one warp per 8x8 block of the
+// trailing triangle subtracts the rank-8 product.  Returns false if a pivot is not positive.
+__device__ bool chol_blocked(float (*F)[kMaxPad + 1], float* ivd, int Pp) {
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nw = nt >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < Pp; j += kBlk) {
+    if (warp == 0) {
+      const int i = lane & 7, r = j + i;
+      float a[kBlk];
+#pragma unroll
+      for (int q = 0; q < kBlk; ++q) a[q] = F[r][j + q];
+#pragma unroll
+      for (int c = 0; c < kBlk; ++c) {
+        const float dc = __shfl_sync(0xffffffffu, a[c], c);
+        if (!(dc > 0.f)) { if (lane == 0) bad = 1; }
+        const float iv = rsqrtf(fmaxf(dc, 1e-30f));
+        a[c] = i > c ? a[c] * iv : (i == c ? dc * iv : a[c]);
+        if (lane == 0) ivd[j + c] = iv;
+#pragma unroll
+        for (int q = c + 1; q < kBlk; ++q) {
+          const float lqc = __shfl_sync(0xffffffffu, a[c], q);
+          if (i >= q) a[q] = fmaf(-a[c], lqc, a[q]);
+        }
+      }
+      if (lane < kBlk) {
+#pragma unroll
+        for (int q = 0; q < kBlk; ++q)
+          if (q <= i) F[r][j + q] = a[q];
+      }
+    }
+    __syncthreads();
+    if (bad) return false;
+    for (int r = j + kBlk + tid; r < Pp; r += nt) {  // panel
+      float a[kBlk];
+#pragma unroll
+      for (int c = 0; c < kBlk; ++c) a[c] = F[r][j + c];
+#pragma unroll
+      for (int c = 0; c < kBlk; ++c) {
+        float sacc = a[c];
+#pragma unroll
+        for (int q = 0; q < c; ++q) sacc = fmaf(-a[q], F[j + c][j + q], sacc);
+        a[c] = sacc * ivd[j + c];
+      }
+#pragma unroll
+      for (int c = 0; c < kBlk; ++c) F[r][j + c] = a[c];
+    }
+    __syncthreads();
+    const int nb = (Pp - j - kBlk) / kBlk, nblocks = nb * (nb + 1) / 2;
+    for (int blk = warp; blk < nblocks; blk += nw) {  // trailing update, one warp per 8x8 block
+      int bi, bq;
+      tri_rc(blk, bi, bq);
+      const int r0 = j + kBlk + kBlk * bi, c0 = j + kBlk + kBlk * bq;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = lane + 32 * h, r = r0 + (e >> 3), q = c0 + (e & 7);
+        float lr[kBlk], lq[kBlk];
+#pragma unroll
+        for (int c = 0; c < kBlk; ++c) { lr[c] = F[r][j + c]; lq[c] = F[q][j + c]; }
+        float dot = 0.f;
+#pragma unroll
+        for (int c = 0; c < kBlk; ++c) dot = fmaf(lr[c], lq[c], dot);
+        if (bi != bq || q <= r) F[r][q] -= dot;
+      }
+    }
+    __syncthreads();
+  }
   return true;
+}
+
+// Blocked forward and backward substitution with the factor of chol_blocked: y <- (L L^T)^-1 y.
+__device__ void solve_blocked(float (*F)[kMaxPad + 1], const float* ivd, float* y, int Pp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  for (int j = 0; j < Pp; j += kBlk) {  // L z = y
+    if (warp == 0) {
+      const int i = lane & 7;
+      float v = y[j + i];
+#pragma unroll
+      for (int c = 0; c < kBlk; ++c) {
+        const float zc = __shfl_sync(0xffffffffu, v, c) * ivd[j + c];
+        v = i == c ? zc : (i > c ? fmaf(-F[j + i][j + c], zc, v) : v);
+      }
+      if (lane < kBlk) y[j + lane] = v;
+    }
+    __syncthreads();
+    for (int r = j + kBlk + tid; r < Pp; r += nt) {
+      float sacc = y[r];
+#pragma unroll
+      for (int c = 0; c < kBlk; ++c) sacc = fmaf(-F[r][j + c], y[j + c], sacc);
+      y[r] = sacc;
+    }
+    __syncthreads();
+  }
+  for (int j = Pp - kBlk; j >= 0; j -= kBlk) {  // L^T x = z
+    if (warp == 0) {
+      const int i = lane & 7;
+      float v = y[j + i];
+#pragma unroll
+      for (int c = kBlk - 1; c >= 0; --c) {
+        const float xc = __shfl_sync(0xffffffffu, v, c) * ivd[j + c];
+        v = i == c ? xc : (i < c ? fmaf(-F[j + c][j + i], xc, v) : v);
+      }
+      if (lane < kBlk) y[j + lane] = v;
+    }
+    __syncthreads();
+    for (int r = tid; r < j; r += nt) {
+      float sacc = y[r];
+#pragma unroll
+      for (int c = 0; c < kBlk; ++c) sacc = fmaf(-F[j + c][r], y[j + c], sacc);
+      y[r] = sacc;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_lm_solve(Dev d) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float F[kMaxPad][kMaxPad + 1];  // FP32 scaled system -> its Cholesky factor
+  __shared__ float ivd[kMaxPad], ys[kMaxPad], sc[kMaxPad];
   const int P = d.L, NP = d.NP, c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
-  const int ld = P + 1;
-  double* M = reinterpret_cast<double*>(smem_raw);  // [P][P+1]
-  double* b = M + (size_t)P * ld;
+  const int Pp = (P + kBlk - 1) / kBlk * kBlk;
+  double* M = reinterpret_cast<double*>(smem_raw);  // [P][P] FP64 system for the residuals
+  double* x = M + P * P;
+  double* res = x + P;
+  double* b = res + P;
   double* dg = b + P;
-  double* inv = dg + P;
-  double* colk = inv + P;
-  LinkTable* lt = reinterpret_cast<LinkTable*>(smem_raw + ((((size_t)P * ld + 4 * P) * 8 + 15) & ~(size_t)15));
-  __shared__ int bad;
+  LinkTable* lt = reinterpret_cast<LinkTable*>(smem_raw + ((((size_t)P * P + 4 * P) * 8 + 15) & ~(size_t)15));
+  DQ* H0 = reinterpret_cast<DQ*>(reinterpret_cast<unsigned char*>(lt) + ((sizeof(LinkTable) + 15) & ~(size_t)15));
+  __shared__ unsigned rmax_bits, bmax_bits;
   for (int t = tid; t < (int)(sizeof(LinkTable) / 4); t += nt)
     reinterpret_cast<int*>(lt)[t] = reinterpret_cast<const int*>(d.links)[t];
   double lam = *d.lam;
   for (int t = 0; t < c; ++t) lam = fmin(lam * 10.0, 1e7);
   for (int r = tid; r < P; r += nt) dg[r] = d.A[r * NP + r] + d.prior2[r];
+  if (tid == 0) bmax_bits = 0u;
   __syncthreads();
-  for (int r = tid; r < P; r += nt) b[r] = dg[r] == 0.0 ? 0.0 : d.A[r * NP + P] + d.prior2[r] * d.theta[r];
-  for (int e = tid; e < P * P; e += nt) {
-    const int r = e / P, q = e % P;
-    const bool frozen = dg[r] == 0.0 || dg[q] == 0.0;
-    M[r * ld + q] = frozen ? (r == q ? 1.0 : 0.0) : d.A[r * NP + q] + (r == q ? d.prior2[r] + lam * dg[r] : 0.0);
+  // ---- setup: M = A + diag(prior + lambda dg) (FP64), frozen rows/columns -> identity; scale D in FP32
+  for (int r = tid; r < Pp; r += nt) {
+    if (r >= P) { sc[r] = 1.f; continue; }
+    const bool fr = dg[r] == 0.0;
+    sc[r] = fr ? 1.f : rsqrtf((float)(dg[r] * (1.0 + lam)));
+    b[r] = fr ? 0.0 : d.A[r * NP + P] + d.prior2[r] * d.theta[r];
+    x[r] = 0.0;
+    res[r] = b[r];
+    atomicMax(&bmax_bits, __float_as_uint(fabsf((float)b[r] * sc[r])));
   }
-  __syncthreads();
-  if (tid == 0) {
-    double l, iv;
-    bad = !pivot_inv(M[0], l, iv);
-    if (!bad) { M[0] = l; inv[0] = iv; }
-  }
-  __syncthreads();
-  for (int k = 0; k < P && !bad; ++k) {
-    const double ik = inv[k];
-    for (int r = k + 1 + tid; r < P; r += nt) {
-      const double v = M[r * ld + k] * ik;
-      M[r * ld + k] = v;
-      colk[r] = v;
+  for (int e0 = tid; e0 < P * P; e0 += 4 * nt) {
+    double a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * nt;
+      a[u] = e < P * P ? d.A[(e / P) * NP + e % P] : 0.0;
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * nt;
+      if (e >= P * P) continue;
+      const int r = e / P, q = e % P;
+      const bool frozen = dg[r] == 0.0 || dg[q] == 0.0;
+      M[e] = frozen ? (r == q ? 1.0 : 0.0) : a[u] + (r == q ? d.prior2[r] + lam * dg[r] : 0.0);
+    }
+  }
+  __syncthreads();
+  // ---- FP32 factor of D M D, padded with identity rows to a multiple of the block size
+  for (int e = tid; e < Pp * Pp; e += nt) {
+    const int r = e / Pp, q = e % Pp;
+    if (q > r) continue;
+    F[r][q] = (r < P && q < P) ? (float)M[r * P + q] * sc[r] * sc[q] : (r == q ? 1.f : 0.f);
+  }
+  __syncthreads();
+  const bool ok32 = chol_blocked(F, ivd, Pp);
+  // ---- iterative refinement: x += D (D M D)^-1 D (b - M x), residual in FP64
+  int iters = 0;
+  bool converged = false;
+  const float bmax = __uint_as_float(bmax_bits);
+  for (int it = 0; it < kMaxRefine && ok32; ++it) {
+    for (int r = tid; r < Pp; r += nt) ys[r] = r < P ? (float)res[r] * sc[r] : 0.f;
     __syncthreads();
-    for (int r = k + 1 + warp; r < P; r += nwarp) {
-      const double lrk = colk[r];
-      double* row = M + (size_t)r * ld;
-      for (int q = k + 1 + lane; q <= r; q += 32) row[q] = fma(-lrk, colk[q], row[q]);
-      if (r == k + 1 && lane == 0) {  // the next pivot is final: factor it now
-        double l, iv;
-        if (pivot_inv(row[r], l, iv)) { row[r] = l; inv[r] = iv; } else { bad = 1; }
+    solve_blocked(F, ivd, ys, Pp);
+    for (int r = tid; r < P; r += nt) x[r] += (double)sc[r] * (double)ys[r];
+    if (tid == 0) rmax_bits = 0u;
+    __syncthreads();
+    for (int r = tid; r < P; r += nt) {  // res = b - M x, four independent FP64 accumulators
+      const double* mr = M + (size_t)r * P;
+      double s0 = b[r], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int q = 0;
+      for (; q + 3 < P; q += 4) {
+        s0 = fma(-mr[q], x[q], s0);
+        s1 = fma(-mr[q + 1], x[q + 1], s1);
+        s2 = fma(-mr[q + 2], x[q + 2], s2);
+        s3 = fma(-mr[q + 3], x[q + 3], s3);
       }
+      for (; q < P; ++q) s0 = fma(-mr[q], x[q], s0);
+      const double rres = (s0 + s1) + (s2 + s3);
+      res[r] = rres;
+      atomicMax(&rmax_bits, __float_as_uint(fabsf((float)rres * sc[r])));
     }
     __syncthreads();
+    iters = it + 1;
+    if (__uint_as_float(rmax_bits) <= 1e-10f * bmax) { converged = true; break; }
   }
-  const int fail = bad;
-  if (!fail && warp == 0) {
-    for (int k = 0; k < P; ++k) {  // L y = b
-      __syncwarp();
-      const double yk = b[k] * inv[k];
-      __syncwarp();
-      if (lane == 0) b[k] = yk;
-      for (int r = k + 1 + lane; r < P; r += 32) b[r] = fma(-M[r * ld + k], yk, b[r]);
-    }
-    for (int k = P - 1; k >= 0; --k) {  // L^T x = y
-      __syncwarp();
-      const double xk = b[k] * inv[k];
-      __syncwarp();
-      if (lane == 0) b[k] = xk;
-      for (int r = lane; r < k; r += 32) b[r] = fma(-M[k * ld + r], xk, b[r]);
-    }
+  int fail = 0;
+  if (!converged) {  // FP64 Cholesky of the unscaled system
+    for (int r = tid; r < P; r += nt) x[r] = b[r];
+    __syncthreads();
+    chol_solve_fp64(M, x, P, fail);
   }
-  __syncthreads();
   double* thc = d.theta_c + (size_t)c * P;
-  for (int j = tid; j < P; j += nt) thc[j] = fail ? d.theta[j] : d.theta[j] - b[j];
-  if (tid == 0) d.lm_ok[c] = !fail;
-  __syncthreads();
-  for (int j = tid; j < P; j += nt) {
-    DQ H;
-    float xi[6];
-    fk_link(*lt, thc, j, &H, xi);
-    d.Hd_c[(size_t)c * P + j] = H;
-    float* xo = d.xi_c + ((size_t)c * P + j) * 8;
-    for (int q = 0; q < 6; ++q) xo[q] = xi[q];
-    xo[6] = xo[7] = 0.f;
+  for (int j = tid; j < P; j += nt) thc[j] = fail ? d.theta[j] : d.theta[j] - x[j];
+  if (tid == 0) {
+    d.lm_ok[c] = !fail;
+    d.lm_ok[kCandidates + c] = converged ? iters : (fail ? -2 : -1);
   }
+  __syncthreads();
+  fk_all(*lt, thc, H0, d.Hd_c + (size_t)c * P, d.xi_c + (size_t)c * P * 8, 8);
 }
 
 // Energy of each candidate at the fixed association (normals and p~ held), then the accept step:
@@ -400,7 +586,8 @@ __global__ void __launch_bounds__(kBlock) k_lm_eval(Dev d, int phi_buf) {
 }
 
 static int lm_solve_smem(int L) {
-  return (int)(((((size_t)L * (L + 1) + 4 * L) * 8 + 15) & ~(size_t)15) + sizeof(LinkTable));
+  return (int)(((((size_t)L * L + 4 * L) * 8 + 15) & ~(size_t)15) + ((sizeof(LinkTable) + 15) & ~(size_t)15) +
+               (size_t)L * sizeof(DQ));
 }
 
 void launch_lm_solve(const Dev& d, cudaStream_t st) {

@@ -332,6 +332,11 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   // ---- link table: normalised axes, offsets, conj(bind) from FK at Theta = 0 in FP64 ----------------
   LinkTable lt{};
   lt.L = L;
+  lt.max_depth = 0;
+  for (int j = 0; j < L; ++j) {
+    lt.depth[j] = sk->parent[j] < 0 ? 0 : lt.depth[sk->parent[j]] + 1;
+    lt.max_depth = std::max(lt.max_depth, lt.depth[j]);
+  }
   lt.pre.r = make_float4(1.f, 0.f, 0.f, 0.f);
   lt.pre.d = make_float4(0.f, (float)pre.d.x, (float)pre.d.y, (float)pre.d.z);
   std::vector<HDQ> bind(L);
@@ -411,9 +416,10 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   TRY(dalloc(s, &d.Hd, L)); TRY(dalloc(s, &d.xi, (size_t)8 * L));
   TRY(dalloc(s, &d.theta_c, (size_t)kCandidates * L)); TRY(dalloc(s, &d.Hd_c, (size_t)kCandidates * L));
   TRY(dalloc(s, &d.xi_c, (size_t)kCandidates * L * 8)); TRY(dalloc(s, &d.lm_trials, 8));
-  TRY(dalloc(s, &d.lm_ok, kCandidates));
+  TRY(dalloc(s, &d.lm_ok, 2 * kCandidates));
   TRY(dalloc(s, &d.v, V)); TRY(dalloc(s, &d.n, V)); TRY(dalloc(s, &d.fn, F)); TRY(dalloc(s, &d.rec, V));
   TRY(dalloc(s, &d.head, npx)); TRY(dalloc(s, &d.zbuf, npx)); TRY(dalloc(s, &d.corr, npx));
+  TRY(dalloc(s, &d.pixrec, npx)); TRY(dalloc(s, &d.queue, npx)); TRY(dalloc(s, &d.qctl, 4));
   TRY(dalloc(s, &d.acc, V)); TRY(dalloc(s, &d.vispix, V)); TRY(dalloc(s, &d.rg, V)); TRY(dalloc(s, &d.phi0, V));
   float* ddepth;
   TRY(dalloc(s, &ddepth, npx));
@@ -438,6 +444,7 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   if (F) CK(cudaMemcpyAsync(dcsr_face, csr_face.data(), sizeof(int) * 3 * F, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dprior, prior2.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(d.counter, 0, sizeof(unsigned) * 4, st));
+  CK(cudaMemsetAsync(d.qctl, 0, sizeof(unsigned) * 4, st));
   CK(cudaMemsetAsync(d.stats, 0, sizeof(int) * 4, st));
   CK(cudaMemsetAsync(d.energy, 0, sizeof(double) * std::max(1, prm->pose_iters + prm->shape_iters), st));
   CK(cudaMemsetAsync(d.lm_trials, 0, sizeof(double) * 8, st));
@@ -550,6 +557,7 @@ trk_status trk_step_visibility(trk_session* s) {
 }
 trk_status trk_step_associate(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  CK(cudaMemsetAsync(s->d.qctl, 0, sizeof(unsigned) * 2, s->stream));
   launch_associate(s->d, s->stream);
   return sync_check(s);
 }
@@ -593,6 +601,7 @@ trk_status trk_read(trk_session* s, trk_field field, void* dst, size_t bytes) {
     case TRK_FIELD_SHAPE_RG: src = d.rg; need = V * 16; break;
     case TRK_FIELD_NEIGHBOURS: src = d.nbr; need = V * 16; break;
     case TRK_FIELD_PRIOR: src = d.prior2; need = L * 8; break;
+    case TRK_FIELD_LM_SOLVER: src = d.lm_ok + kCandidates; need = kCandidates * 4; break;
     default: return fail(TRK_ERR_INVALID_ARG, "unknown field %d", (int)field);
   }
   if (bytes != need) return fail(TRK_ERR_INVALID_ARG, "field %d needs %zu bytes, got %zu", (int)field, need, bytes);
@@ -617,7 +626,7 @@ trk_status trk_get_info(trk_session* s, trk_info* out) {
   out->n_tris = d.F;
   out->width = d.cam.W;
   out->height = d.cam.H;
-  const int per_assoc = (d.F > 0 ? 4 : 3);  // skin, raster, visibility, associate
+  const int per_assoc = (d.F > 0 ? 5 : 4);  // skin, raster, visibility, associate (2 kernels)
   out->kernels_per_frame = s->prm.pose_iters * (per_assoc + 4) + s->prm.shape_iters * (per_assoc + s->prm.shape_sweeps);
   out->device_bytes = s->device_bytes;
   return TRK_OK;

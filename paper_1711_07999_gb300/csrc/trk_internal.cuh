@@ -33,6 +33,8 @@ struct __align__(32) Acc4 {
 // FK starts from pre = T(-c); the bind pose is stored in the same frame.
 struct LinkTable {
   int L;
+  int max_depth;           // links are grouped by depth (root links: 0) for level-synchronous FK
+  int depth[kMaxLinks];
   int parent[kMaxLinks];
   int type[kMaxLinks];
   float axis[kMaxLinks][3];
@@ -128,6 +130,43 @@ __device__ __forceinline__ void fk_link(const LinkTable& lt, const ThetaT* theta
   xi_out[3] = X.d.y; xi_out[4] = X.d.z; xi_out[5] = X.d.w;
 }
 
+// Block-level FK of all links, level by level (every link of one depth in parallel, a barrier between
+// levels), with the joint transforms' sines and cosines computed up front in parallel.  Same products
+// in the same order as fk_link.  H0 (shared, [L]) is scratch; all threads of the block must call it.
+template <typename ThetaT>
+__device__ __forceinline__ void fk_all(const LinkTable& lt, const ThetaT* theta, DQ* H0, DQ* Hd_out, float* xi_out,
+                                       int xi_stride) {
+  const int L = lt.L;
+  for (int j = threadIdx.x; j < L; j += blockDim.x) H0[j] = joint_dq(lt.type[j], lt.axis[j], (float)theta[j]);
+  __syncthreads();
+  for (int lev = 0; lev <= lt.max_depth; ++lev) {
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+      if (lt.depth[j] != lev) continue;
+      const DQ par = lt.parent[j] < 0 ? lt.pre : H0[lt.parent[j]];
+      H0[j] = dqmul(dqmul(par, lt.off[j]), H0[j]);
+    }
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    const DQ H = H0[j];
+    Hd_out[j] = dqmul(H, lt.bindc[j]);
+    DQ G;
+    const float* z = lt.axis[j];
+    if (lt.type[j] == 0) {
+      G.r = make_float4(0.f, 0.5f * z[0], 0.5f * z[1], 0.5f * z[2]);
+      G.d = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      G.r = make_float4(0.f, 0.f, 0.f, 0.f);
+      G.d = make_float4(0.f, 0.5f * z[0], 0.5f * z[1], 0.5f * z[2]);
+    }
+    const DQ X = dqmul(dqmul(H, G), dqconj(H));
+    float* xo = xi_out + (size_t)j * xi_stride;
+    xo[0] = X.r.y; xo[1] = X.r.z; xo[2] = X.r.w;
+    xo[3] = X.d.y; xo[4] = X.d.z; xo[5] = X.d.w;
+    if (xi_stride > 6) { xo[6] = 0.f; xo[7] = 0.f; }
+  }
+}
+
 // Blend of the <= 4 bone offsets of a vertex with the antipodal sign alignment to the heaviest bone
 // (largest weight, ties to the smaller link index).
 __device__ __forceinline__ DQ blend_bones(const DQ* Hd, uchar4 bi, float4 bw, float sg[4]) {
@@ -174,7 +213,7 @@ void launch_fk(const Dev& d, cudaStream_t st);
 void launch_skin(const Dev& d, int phi_buf, cudaStream_t st);
 void launch_raster(const Dev& d, cudaStream_t st);
 void launch_visibility(const Dev& d, cudaStream_t st);
-void launch_associate(const Dev& d, cudaStream_t st);
+void launch_associate(const Dev& d, cudaStream_t st);  // two kernels: thread-owned rings, then the queue
 // residual + Jacobian + [J r]^T [J r]; writes E_pose to energy[slot] (slot < 0: not recorded)
 void launch_normal_equations(const Dev& d, int phi_buf, int slot, cudaStream_t st);
 void launch_lm(const Dev& d, int phi_buf, cudaStream_t st);
@@ -225,13 +264,16 @@ struct Dev {
   DQ* Hd_c;         // [kCandidates][L]
   float* xi_c;      // [kCandidates][L][8]
   double* lm_trials;  // [8]
-  int* lm_ok;         // [kCandidates]
+  int* lm_ok;         // [kCandidates] ok flags, then [kCandidates] solver diagnostics
   // per-iteration buffers
   float4* v;
   float4* n;
   float4* fn;
   float4* rec;
+  float4* pixrec;  // [W*H] first vertex inserted into each pixel's bucket: x, y, z, index bits
   int* head;
+  int4* queue;     // [W*H] pixels whose association search continues past the thread-owned rings
+  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take
   unsigned long long* zbuf;
   int* corr;
   Acc4* acc;

@@ -17,7 +17,7 @@ TRK_OK, TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA, TRK_ERR_NO_CAPACITY, TRK
 MAX_LINKS = 79
 
 FIELDS = dict(VERTS=0, NORMALS=1, ZBUF=2, VISPIX=3, CORR=4, ACC=5, NORMAL_EQ=6, THETA=7, PHI=8, LAMBDA=9, ENERGY=10,
-              LM_TRIALS=11, SHAPE_RG=12, NEIGHBOURS=13, PRIOR=14)
+              LM_TRIALS=11, SHAPE_RG=12, NEIGHBOURS=13, PRIOR=14, LM_SOLVER=15)
 
 # symbols include/trk.h declares (checked by the tests against the library's exports)
 EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_device", "trk_read_result",
@@ -231,7 +231,8 @@ class Session:
                       VISPIX=((V,), np.int32), CORR=((npx,), np.int32), ACC=((V, 4), np.int64),
                       NORMAL_EQ=((NP, NP), np.float64), THETA=((L,), np.float64), PHI=((V, 4), np.float32),
                       LAMBDA=((1,), np.float64), ENERGY=((self.n_energy,), np.float64), LM_TRIALS=((8,), np.float64),
-                      SHAPE_RG=((V, 4), np.float32), NEIGHBOURS=((V, 4), np.int32), PRIOR=((L,), np.float64))
+                      SHAPE_RG=((V, 4), np.float32), NEIGHBOURS=((V, 4), np.int32), PRIOR=((L,), np.float64),
+                      LM_SOLVER=((6,), np.int32))
         shp, dt = shapes[field]
         out = np.empty(shp, dt)
         _check(lib().trk_read(self.h, FIELDS[field], _p(out), out.nbytes))
