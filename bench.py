@@ -10,6 +10,8 @@ Prints one JSON line (rank 0):
              before every step, outside the timed intervals.  "plain" holds the same figures for one
              session alone (--sessions 1 makes it the headline)
   latency    p50 / p99 per-frame latency (from the step's start to the session's completion)
+  serving    (in "batched") --serve-streams streams with Poisson arrivals at 30 fps each through the frame
+             server (trk_server_*): achieved frames/s and submit -> completion p50 / p99 latency
   e2e        frames/s through trk_track_frame with host (pinned) depth: H2D of the frame and D2H of
              Theta, Phi and the energies inside the timed region
   roofline   the dominant kernel's achieved rate against the measured peak of MEASURED_PEAKS.json
@@ -292,6 +294,78 @@ def run_batched_e2e(sessions, host_frames, n_seq, steps, flush):
     return wall, [x for l in lat for x in l]
 
 
+def run_serving(sessions, host_frames, n_seq, duration_s, fps, seed):
+    """Poisson arrivals (rate fps per stream, random phase) submitted through the frame server at their
+    arrival times; one collector thread per stream.  Returns frames/s and submit -> completion latency."""
+    import threading
+    from paper_1711_07999_gb300 import trk
+    rng = np.random.default_rng(seed)
+    N = len(sessions)
+    arrivals = []
+    for b in range(N):
+        t = rng.uniform(0, 1.0 / fps)
+        while t < duration_s:
+            arrivals.append((t, b))
+            t += rng.exponential(1.0 / fps)
+    arrivals.sort()
+    budget = sum(x.info()["device_bytes"] for x in sessions)
+    tickets = [[] for _ in range(N)]
+    done = [0] * N
+    with trk.Server(budget, max_inflight=N) as sv:
+        for x in sessions:
+            sv.attach(x)
+        cond = threading.Condition()
+
+        def collector(b):
+            k = 0
+            while True:
+                with cond:
+                    while k >= len(tickets[b]) and not finished[0]:
+                        cond.wait(0.01)
+                    if k >= len(tickets[b]):
+                        return
+                    t = tickets[b][k]
+                sv.wait(sessions[b], t, timeout_us=30_000_000, want_offsets=True)
+                done[b] += 1
+                k += 1
+
+        finished = [False]
+        th = [threading.Thread(target=collector, args=(b,)) for b in range(N)]
+        for t in th:
+            t.start()
+        nxt = [0] * N
+        lag = []
+        t0 = time.perf_counter()
+        for ta, b in arrivals:
+            dt = t0 + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            lag.append(time.perf_counter() - t0 - ta)
+            tk = sv.submit(sessions[b], host_frames[(nxt[b] + 7 * b) % n_seq])
+            nxt[b] += 1
+            with cond:
+                tickets[b].append(tk)
+                cond.notify_all()
+        with cond:
+            finished[0] = True
+            cond.notify_all()
+        t_sub = time.perf_counter() - t0
+        for t in th:
+            t.join()
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+        for x in sessions:
+            sv.detach(x)
+    n = sum(done)
+    # served frames over the span from the first arrival to the last completion (the drain included)
+    return {"streams": N, "offered_fps": N * fps, "arrivals": "poisson", "frames": n, "seconds": round(wall, 3),
+            "achieved_fps": n / wall, "drain_ms": (wall - t_sub) * 1e3,
+            "submit_lag_ms": {"p50": float(np.percentile(lag, 50)) * 1e3, "max": float(np.max(lag)) * 1e3},
+            "latency_ms": {"p50": st["latency_p50_us"] / 1000,
+                                                      "p99": st["latency_p99_us"] / 1000,
+                                                      "max": st["latency_max_us"] / 1000}}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -408,6 +482,18 @@ def run_ours(args, rank, world, local_rank):
                    "latency_ms": {"p50": float(np.percentile(lat_b, 50)), "p99": float(np.percentile(lat_b, 99))},
                    "e2e": {"value": world * B * args.steps / float(twb.item()),
                            "p50_ms": float(np.percentile(lat_be, 50)), "p99_ms": float(np.percentile(lat_be, 99))}}
+        serving = None
+        if args.serve_streams > 0:
+            more = [trk.Session(synth.make_model(2, session=rank * 1000 + 100 + b))
+                    for b in range(max(0, args.serve_streams - len(group)))]
+            streams = (group + more)[:args.serve_streams]
+            for b, x in enumerate(streams):
+                x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
+            serving = run_serving(streams, [host[i].numpy() for i in range(n_seq)], n_seq, args.serve_seconds, 30.0,
+                                  synth.seed_for(5, rank))
+            for x in more:
+                x.close()
+        batched["serving"] = serving
         for x in extra:
             x.close()
     line = None
@@ -455,6 +541,8 @@ def main():
     ap.add_argument("--cpu-frames", type=int, default=4, help="oracle frames of the CPU baseline sample")
     ap.add_argument("--profile-reps", type=int, default=20)
     ap.add_argument("--sessions", type=int, default=16, help="concurrent sessions of the batched measurement")
+    ap.add_argument("--serve-streams", type=int, default=32, help="Poisson streams (30 fps each) of the serving run")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)

@@ -197,6 +197,39 @@ typedef enum {
  * (outside the timed interval) so that every stage starts from a cold L2. */
 trk_status trk_profile_iteration(trk_session* s, int32_t reps, size_t flush_bytes, float* ms);
 
+/* ---- Serving: continuous batching of frames from many sessions on one device -------------------- */
+
+typedef struct trk_server trk_server;
+
+typedef struct {
+  uint64_t frames_done;     /* frames completed since the server was created            */
+  int32_t in_flight;        /* frames on the GPU now                                     */
+  int32_t sessions;         /* attached sessions                                         */
+  size_t hbm_used_bytes;    /* device bytes of the attached sessions                     */
+  double latency_p50_us, latency_p99_us, latency_max_us;  /* submit -> completion, wall time */
+} trk_server_stats;
+
+/* Creates a frame server on the current device.  Sessions are admitted while the sum of their device
+ * memory stays within hbm_budget_bytes; at most max_inflight frames run on the GPU at a time (0 admits
+ * frames but never launches them).  A dispatcher thread launches a session's next frame on the
+ * session's own stream as soon as its previous frame is done and a slot is free, so frames of different
+ * sessions overlap on the device and one session's frames run in submission order. */
+trk_status trk_server_create(size_t hbm_budget_bytes, int32_t max_inflight, trk_server** out);
+/* Admits a session (same device).  TRK_ERR_NO_CAPACITY if it does not fit the remaining budget.  While
+ * attached, the session must be driven only through the server. */
+trk_status trk_server_attach(trk_server* sv, trk_session* s);
+/* Releases a session's budget; TRK_ERR_INVALID_ARG while it still has frames queued or running. */
+trk_status trk_server_detach(trk_server* sv, trk_session* s);
+/* Queues one frame (host depth [height][width], copied at the call) and returns its ticket. */
+trk_status trk_server_submit(trk_server* sv, trk_session* s, const float* depth_m, uint64_t* ticket);
+/* Waits up to timeout_us for the frame and fills *out (host buffers, as trk_track_frame; out may be
+ * NULL).  TRK_ERR_TIMEOUT if the frame is not done by then (the ticket stays valid); TRK_ERR_INVALID_ARG
+ * for an unknown or already collected ticket.  Each ticket is collected once. */
+trk_status trk_server_wait(trk_server* sv, uint64_t ticket, int64_t timeout_us, trk_result* out);
+trk_status trk_server_get_stats(trk_server* sv, trk_server_stats* out);
+/* Stops the dispatcher, waits for frames on the GPU and frees every uncollected frame. */
+void trk_server_destroy(trk_server* sv);
+
 /* ---- Standalone contraction ------------------------------------------------------------------- */
 
 /* [J r]^T [J r] of materialised rows (Eqs. JTJ, JTr): d_rows is device FP32 [n_rows][ld], each row the

@@ -269,6 +269,37 @@ trk_status sync_check(trk_session* s) {
 
 }  // namespace
 
+// ---- helpers of the frame server (server.cu) --------------------------------------------------
+namespace trk {
+size_t session_device_bytes(const trk_session* s) { return s->device_bytes; }
+int session_device(const trk_session* s) { return s->device; }
+void session_result_sizes(const trk_session* s, int* n_links, int* n_verts, int* n_energy) {
+  *n_links = s->d.L;
+  *n_verts = s->d.V;
+  *n_energy = s->prm.pose_iters + s->prm.shape_iters;
+}
+// H2D of the frame's depth and the frame graph, on the session's stream
+trk_status session_enqueue_frame(trk_session* s, const float* host_depth, cudaStream_t* stream_out) {
+  TRY(ensure_graph(s));
+  CK(cudaMemcpyAsync(const_cast<float*>(s->d.depth), host_depth, sizeof(float) * s->d.cam.W * s->d.cam.H,
+                     cudaMemcpyHostToDevice, s->stream));
+  CK(cudaGraphLaunch(s->graph, s->stream));
+  s->last_stream = s->stream;
+  *stream_out = s->stream;
+  return TRK_OK;
+}
+// D2H of the frame's results into (pinned) host buffers, on the session's stream
+trk_status session_enqueue_results(trk_session* s, double* theta, float* phi4, double* energy, int* stats) {
+  const Dev& d = s->d;
+  const int ne = s->prm.pose_iters + s->prm.shape_iters;
+  CK(cudaMemcpyAsync(theta, d.theta, sizeof(double) * d.L, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(phi4, d.phi[0], sizeof(float4) * d.V, cudaMemcpyDeviceToHost, s->stream));
+  if (ne > 0) CK(cudaMemcpyAsync(energy, d.energy, sizeof(double) * ne, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(stats, d.stats, sizeof(int) * 2, cudaMemcpyDeviceToHost, s->stream));
+  return TRK_OK;
+}
+}  // namespace trk
+
 extern "C" {
 
 const char* trk_last_error(void) { return g_err.c_str(); }

@@ -23,7 +23,9 @@ FIELDS = dict(VERTS=0, NORMALS=1, ZBUF=2, VISPIX=3, CORR=4, ACC=5, NORMAL_EQ=6, 
 EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_device", "trk_read_result",
            "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
-           "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc"]
+           "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc",
+           "trk_server_create", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
+           "trk_server_get_stats", "trk_server_destroy"]
 
 STAGES = ["skin", "raster", "visibility", "associate", "resid_jtj", "reduce", "lm_solve", "lm_eval", "shape"]
 
@@ -61,6 +63,12 @@ class Info(C.Structure):
                 ("height", C.c_int32), ("kernels_per_frame", C.c_int32), ("device_bytes", C.c_size_t)]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [("frames_done", C.c_uint64), ("in_flight", C.c_int32), ("sessions", C.c_int32),
+                ("hbm_used_bytes", C.c_size_t), ("latency_p50_us", C.c_double), ("latency_p99_us", C.c_double),
+                ("latency_max_us", C.c_double)]
+
+
 class Result(C.Structure):
     _fields_ = [("theta", C.c_void_p), ("offsets", C.c_void_p), ("energy", C.c_void_p), ("n_assoc_px", C.c_int32),
                 ("n_assoc_verts", C.c_int32)]
@@ -87,6 +95,9 @@ def lib(build_if_missing: bool = True):
             "trk_step_normal_equations": [vp], "trk_step_lm": [vp], "trk_step_shape": [vp],
             "trk_read": [vp, i32, vp, sz], "trk_get_info": [vp, vp], "trk_profile_iteration": [vp, i32, sz, vp],
             "trk_jtj_rows": [vp, i32, i32, i32, vp, vp], "trk_jtj_rows_noalloc": [vp, i32, i32, i32, vp, vp],
+            "trk_server_create": [sz, i32, C.POINTER(vp)], "trk_server_attach": [vp, vp], "trk_server_detach": [vp, vp],
+            "trk_server_submit": [vp, vp, vp, C.POINTER(C.c_uint64)], "trk_server_wait": [vp, C.c_uint64, C.c_int64, vp],
+            "trk_server_get_stats": [vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -94,6 +105,8 @@ def lib(build_if_missing: bool = True):
             f.restype = C.c_int
         L.trk_destroy.argtypes = [vp]
         L.trk_destroy.restype = None
+        L.trk_server_destroy.argtypes = [vp]
+        L.trk_server_destroy.restype = None
         L.trk_last_error.argtypes = []
         L.trk_last_error.restype = C.c_char_p
         _lib = L
@@ -237,3 +250,53 @@ class Session:
         out = np.empty(shp, dt)
         _check(lib().trk_read(self.h, FIELDS[field], _p(out), out.nbytes))
         return out
+
+
+class Server:
+    """Continuous-batching frame server (trk_server_*) over attached sessions."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 32):
+        h = C.c_void_p()
+        _check(lib().trk_server_create(hbm_budget_bytes, max_inflight, C.byref(h)))
+        self.h = h
+        self._sessions = {}
+
+    def attach(self, session: Session):
+        _check(lib().trk_server_attach(self.h, session.h))
+        self._sessions[session.h.value] = session
+
+    def detach(self, session: Session):
+        _check(lib().trk_server_detach(self.h, session.h))
+        self._sessions.pop(session.h.value, None)
+
+    def submit(self, session: Session, depth) -> int:
+        dep = np.ascontiguousarray(depth, np.float32)
+        t = C.c_uint64()
+        _check(lib().trk_server_submit(self.h, session.h, _p(dep), C.byref(t)))
+        return t.value
+
+    def wait(self, session: Session, ticket: int, timeout_us: int = 10_000_000, want_offsets=True) -> dict:
+        r, th, of, en = session._result(want_offsets)
+        _check(lib().trk_server_wait(self.h, ticket, timeout_us, C.byref(r)))
+        return dict(theta=th, offsets=of, energy=en[:session.n_energy], n_assoc_px=r.n_assoc_px,
+                    n_assoc_verts=r.n_assoc_verts)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().trk_server_get_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().trk_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
