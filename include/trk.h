@@ -81,8 +81,18 @@ typedef struct {
   float lambda_k0, lambda_s, lambda_phi, lambda_N, lambda_w;
   float cutoff_m, eps_vis_m, z_near_m;
   int32_t window_half_px, knn;
-  int32_t precision; /* 0 = FP32 (the only value accepted) */
+  int32_t precision; /* TRK_PRECISION_*: how [J r]^T [J r] is formed in each pose iteration      */
 } trk_params;
+
+/* Arithmetic of the contraction [J r]^T [J r] (Eqs. JTJ, JTr).  FP32: products and per-CTA sums on the
+ * FP32 cores.  BF16X3 / TF32X3: every value of [J r] split as hi + lo (BF16 or TF32), the products
+ * hi hi + hi lo + lo hi formed on the tensor cores (tcgen05) with FP32 accumulation; relative error of a
+ * product about 2^-16 (BF16X3) or 2^-21 (TF32X3) against about 2^-24 for FP32.  In every mode the
+ * per-CTA partials are added in FP64, the energy E is summed on the FP32 cores, and the LM system is
+ * solved and the step accepted in FP64 (Sec. 4.2). */
+#define TRK_PRECISION_FP32 0
+#define TRK_PRECISION_BF16X3 1
+#define TRK_PRECISION_TF32X3 2
 
 /* Per-frame outputs, written into caller (host) buffers; any pointer may be NULL. */
 typedef struct {
@@ -256,6 +266,18 @@ trk_status trk_jtj_rows(const float* d_rows, int32_t n_rows, int32_t n_cols, int
  * Errors: TRK_ERR_INVALID_ARG (n_cols outside [1, 80], bad pointers or sizes), TRK_ERR_CUDA. */
 trk_status trk_jtj_rows_noalloc(const float* d_rows, int32_t n_rows, int32_t n_cols, int32_t ld, double* d_out,
                                 void* cuda_stream);
+
+/* The same contraction on the tensor cores (Eqs. JTJ, JTr): out = R^T R for the FP32 rows R as in
+ * trk_jtj_rows, with precision TRK_PRECISION_BF16X3 or TRK_PRECISION_TF32X3.  Each CTA accumulates
+ * 64-row chunks in tensor memory (FP32) and drains them every 512 rows into Kahan-compensated FP32 sums;
+ * the CTA sums (value and compensation) are added in FP64 in a fixed order, so the result is
+ * deterministic for given arguments.  Entry error against the exact R^T R: about 2^-16 (BF16X3) or 2^-21
+ * (TF32X3) times sum_k |R_ka R_kb|.  Scratch (at most 2 x 296 n_cols^2 floats) comes from the
+ * stream-ordered allocator and is released on the stream.  1 <= n_cols <= 80, ld >= n_cols, n_rows >= 0.
+ * Errors: TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA.  Entries are NaN if a tensor-core completion
+ * wait ran out (about one second; a failure of the device, not of the data). */
+trk_status trk_jtj_rows_tc(const float* d_rows, int32_t n_rows, int32_t n_cols, int32_t ld, int32_t precision,
+                           double* d_out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

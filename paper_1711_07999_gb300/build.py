@@ -15,8 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libtrk.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["kernels_geom.cu", "kernels_solve.cu", "kernels_jtj.cu", "trk_api.cu", "server.cu"]
-DEPS = ["trk_internal.cuh", os.path.join(ROOT, "include", "trk.h")]
+SOURCES = ["kernels_geom.cu", "kernels_solve.cu", "kernels_jtj.cu", "kernels_tc.cu", "trk_api.cu", "server.cu"]
+DEPS = ["trk_internal.cuh", "tcgen05.cuh", os.path.join(ROOT, "include", "trk.h")]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
               "-Xcompiler", "-fPIC,-ffp-contract=off", "-diag-suppress", "177"]
 

@@ -95,6 +95,12 @@ cudaError_t jtj_rows_launch(const float* rows, int n, int nc, int ld, double* ou
   return cudaGetLastError();
 }
 
+// Fixed-order FP64 sum of nslots partials of nc x nc floats into out.
+cudaError_t jtj_reduce_launch(const float* partial, int nslots, int nc, double* out, cudaStream_t st) {
+  k_jtj_reduce<<<(nc * nc + 31) / 32, 1024, 0, st>>>(partial, nslots, nc, out);
+  return cudaGetLastError();
+}
+
 int jtj_rows_blocks(int n) { return std::max(1, std::min(kJMaxBlocks, (n + kJBlock - 1) / kJBlock)); }
 
 // ---------------------------------------------------------------------------------------------

@@ -7,6 +7,8 @@
 // 10 lambda, ..., 10^5 lambda) are solved side by side, one CTA each, and their energies evaluated in
 // one pass over the vertices; the first candidate that does not raise the energy is taken on the device,
 // which gives the same result as trying them one after the other without any host round trip.
+#include <mutex>
+
 #include "trk_internal.cuh"
 
 namespace trk {
@@ -745,13 +747,29 @@ int launch_shape(const Dev& d, int phi_src, int slot, cudaStream_t st) {
   return cur;
 }
 
+void configure_tc_kernels();
+
 void configure_kernels() {
+  configure_tc_kernels();
   cudaFuncSetAttribute(k_resid_jtj<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(1, kMaxLinks));
   cudaFuncSetAttribute(k_resid_jtj<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(2, kMaxLinks));
   cudaFuncSetAttribute(k_resid_jtj<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(3, kMaxLinks));
   cudaFuncSetAttribute(k_resid_jtj<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(4, kMaxLinks));
   cudaFuncSetAttribute(k_resid_jtj<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(5, kMaxLinks));
   cudaFuncSetAttribute(k_lm_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, lm_solve_smem(kMaxLinks));
+}
+
+// Sets the kernels' shared-memory limits once per device (the attributes are per device).
+void ensure_configured() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done[dev]) {
+    configure_kernels();
+    done[dev] = true;
+  }
 }
 
 }  // namespace trk

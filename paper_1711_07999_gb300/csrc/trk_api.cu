@@ -329,11 +329,7 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
     ~Guard() { if (s) trk_destroy(s); }
   } guard{s};
   CK(cudaGetDevice(&s->device));
-  static bool configured[64] = {false};
-  if (s->device < 64 && !configured[s->device]) {
-    configure_kernels();
-    configured[s->device] = true;
-  }
+  ensure_configured();
   CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
   s->prm = *prm;
   const int L = sk->n_links, V = mesh->n_verts, F = mesh->n_tris, W = cam->width, H = cam->height;

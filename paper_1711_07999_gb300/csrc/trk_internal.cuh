@@ -226,6 +226,7 @@ void launch_lm_eval(const Dev& d, int phi_buf, cudaStream_t st);
 int launch_shape(const Dev& d, int phi_src, int slot, cudaStream_t st);
 void launch_depth_from_zbuf(const Dev& d, float* out, cudaStream_t st);
 void configure_kernels();
+void ensure_configured();  // configure_kernels once per device (thread-safe)
 
 // Records msg as this thread's last error (read by trk_last_error) and returns st.
 int set_error_code(int st, const char* msg);

@@ -15,6 +15,7 @@ LIB_PATH = _build.LIB
 
 TRK_OK, TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA, TRK_ERR_NO_CAPACITY, TRK_ERR_TIMEOUT, TRK_ERR_NUMERIC = range(7)
 MAX_LINKS = 79
+PRECISION_FP32, PRECISION_BF16X3, PRECISION_TF32X3 = 0, 1, 2
 
 FIELDS = dict(VERTS=0, NORMALS=1, ZBUF=2, VISPIX=3, CORR=4, ACC=5, NORMAL_EQ=6, THETA=7, PHI=8, LAMBDA=9, ENERGY=10,
               LM_TRIALS=11, SHAPE_RG=12, NEIGHBOURS=13, PRIOR=14, LM_SOLVER=15)
@@ -24,7 +25,7 @@ EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_dev
            "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
            "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc",
-           "trk_server_create", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
+           "trk_jtj_rows_tc", "trk_server_create", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
            "trk_server_get_stats", "trk_server_destroy"]
 
 STAGES = ["skin", "raster", "visibility", "associate", "resid_jtj", "reduce", "lm_solve", "lm_eval", "shape"]
@@ -95,6 +96,7 @@ def lib(build_if_missing: bool = True):
             "trk_step_normal_equations": [vp], "trk_step_lm": [vp], "trk_step_shape": [vp],
             "trk_read": [vp, i32, vp, sz], "trk_get_info": [vp, vp], "trk_profile_iteration": [vp, i32, sz, vp],
             "trk_jtj_rows": [vp, i32, i32, i32, vp, vp], "trk_jtj_rows_noalloc": [vp, i32, i32, i32, vp, vp],
+            "trk_jtj_rows_tc": [vp, i32, i32, i32, i32, vp, vp],
             "trk_server_create": [sz, i32, C.POINTER(vp)], "trk_server_attach": [vp, vp], "trk_server_detach": [vp, vp],
             "trk_server_submit": [vp, vp, vp, C.POINTER(C.c_uint64)], "trk_server_wait": [vp, C.c_uint64, C.c_int64, vp],
             "trk_server_get_stats": [vp, vp],
@@ -135,11 +137,19 @@ def jtj_rows_noalloc(rows_ptr: int, n_rows: int, n_cols: int, ld: int, out_ptr: 
                                       C.c_void_p(stream_ptr or None)))
 
 
+def jtj_rows_tc(rows_ptr: int, n_rows: int, n_cols: int, ld: int, precision: int, out_ptr: int,
+                stream_ptr: int = 0):
+    """trk_jtj_rows on the tensor cores: split-BF16x3 (PRECISION_BF16X3) or 3xTF32 (PRECISION_TF32X3)."""
+    _check(lib().trk_jtj_rows_tc(C.c_void_p(rows_ptr), n_rows, n_cols, ld, precision, C.c_void_p(out_ptr),
+                                 C.c_void_p(stream_ptr or None)))
+
+
 def params_struct(p: dict) -> Params:
     return Params(pose_iters=p["pose_iters"], shape_iters=p["shape_iters"], shape_sweeps=p["shape_sweeps"],
                   lambda_k0=p["lambda_k0"], lambda_s=p["lambda_s"], lambda_phi=p["lambda_phi"],
                   lambda_N=p["lambda_N"], lambda_w=p["lambda_w"], cutoff_m=p["cutoff"], eps_vis_m=p["eps_vis"],
-                  z_near_m=p["z_near"], window_half_px=p["window_half"], knn=p["knn"], precision=0)
+                  z_near_m=p["z_near"], window_half_px=p["window_half"], knn=p["knn"],
+                  precision=p.get("precision", PRECISION_FP32))
 
 
 class Session:
