@@ -14,6 +14,9 @@ Prints one JSON line (rank 0):
              server (trk_server_*): achieved frames/s and submit -> completion p50 / p99 latency
   e2e        frames/s through trk_track_frame with host (pinned) depth: H2D of the frame and D2H of
              Theta, Phi and the energies inside the timed region
+  precision  per [J r]^T [J r] arithmetic (fp32, bf16x3, tf32x3; the last two on the tensor cores): batched
+             frames/s, the contraction stage's time and each result's error against the oracle on the
+             CPU-baseline frames
   roofline   the dominant kernel's achieved rate against the measured peak of MEASURED_PEAKS.json
   cpu_baseline  the FP64 oracle on the host, one core, a bounded sample of the same sequence
 --impl reference times the oracle itself (on host cores) on the same workload and metric.
@@ -187,17 +190,86 @@ def oracle_frames(model, n_frames, seed):
 
 
 def cpu_baseline(model, n_frames):
-    """The oracle as it stands, single-threaded FP64, on the first n_frames of the sequence."""
+    """The oracle as it stands, single-threaded FP64, on the first n_frames of the sequence.  Also returns
+    the frames and the oracle's state after each (for the per-result error of the precision modes)."""
     from paper_1711_07999_gb300 import synth
     o, frames = oracle_frames(model, n_frames, seed=synth.seed_for(2, 900))
     o.set_state(synth.gt_theta(model, 0.0), None)
-    t0 = time.perf_counter()
+    states = []
+    dt = 0.0
     for d in frames:
-        o.track_frame(d)
-    dt = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        e, _, _ = o.track_frame(d)
+        dt += time.perf_counter() - t0
+        th, phi, _ = o.get_state()
+        states.append((th, phi, e, determined_dofs(o, model, th, phi, d)))
     return dict(value=n_frames / dt, unit="frames/s", cores=1, kind="oracle",
                 sample=f"first {n_frames} frames of the sequence, 10 pose + 2 shape iterations each, FP64, 1 thread",
-                seconds=round(dt, 2))
+                seconds=round(dt, 2)), frames, states
+
+
+def determined_dofs(o, model, th, phi, depth, tol=1e-3):
+    """DoFs the energy fixes to within tol at the oracle's state: moving DoF k by tol (the others
+    re-optimised) raises E by more than 1e-5 relative, sqrt(1e-5 E [H^-1]_kk) < tol, H = J^T J + prior."""
+    import oracle
+    P = o.pass_at(th, phi, depth)
+    J = o.jacobian(th, phi, P["n"], P["inA"])
+    JTJ, _ = oracle.normal_eq(J, P["r"], P["inA"])
+    _, S, _ = o.derived()
+    H = JTJ + np.diag((model["params"]["lambda_s"] * S) ** 2)
+    return np.sqrt(1e-5 * P["E"] * np.diag(np.linalg.inv(H))) < tol
+
+
+def errors_vs_oracle(model, prec, frames, states):
+    """Per-result error of one precision mode against the oracle on the same frames (free-running from
+    the same start): joint values, offsets (99th percentile and max over vertices), energies."""
+    from paper_1711_07999_gb300 import synth, trk
+    dth, dthd, ndet, dphi99, dphimax, de = [], [], [], [], [], []
+    with trk.Session(synth.make_model(2, precision=prec)) as s:
+        s.set_pose(synth.gt_theta(model, 0.0))
+        for d, (th, phi, e, det) in zip(frames, states):
+            g = s.track_frame(d)
+            dth.append(float(np.abs(g["theta"] - th).max()))
+            dthd.append(float(np.abs(g["theta"] - th)[det].max()))
+            ndet.append(int(det.sum()))
+            dd = np.abs(g["offsets"] - phi).max(axis=1)
+            dphi99.append(float(np.percentile(dd, 99)))
+            dphimax.append(float(dd.max()))
+            de.append(float(np.max(np.abs(g["energy"] - e) / e)))
+    return {"frames": len(frames), "theta_rad_max_determined": max(dthd), "determined_dofs": min(ndet),
+            "theta_rad_max": max(dth), "offsets_mm_p99": 1e3 * max(dphi99),
+            "offsets_mm_max": 1e3 * max(dphimax), "energy_rel_max": max(de)}
+
+
+def run_precision_modes(args, model, rank, dev, n_seq, flush, nA, NP, sample):
+    """Each [J r]^T [J r] arithmetic (FP32 cores, split-BF16x3 and 3xTF32 on the tensor cores): batched
+    frames/s with the same sessions and frames as the FP32 batched run, the contraction stage's time, and
+    (rank 0, one GPU) the error of every result against the oracle on the CPU-baseline frames."""
+    from paper_1711_07999_gb300 import synth, trk
+    out = {}
+    for name, prec in (("fp32", trk.PRECISION_FP32), ("bf16x3", trk.PRECISION_BF16X3),
+                       ("tf32x3", trk.PRECISION_TF32X3)):
+        group = [trk.Session(synth.make_model(2, session=rank * 1000 + b, precision=prec)) for b in range(args.sessions)]
+        for b, x in enumerate(group):
+            x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
+        steps = max(3, args.steps // 2)
+        tb, lat = run_batched(group, dev, n_seq, steps, args.warmup, flush)
+        group[0].set_depth(dev[0].cpu().numpy())
+        prof = group[0].profile_iteration(reps=args.profile_reps, flush_bytes=L2_FLUSH_BYTES)
+        ms = prof["resid_jtj"]
+        r = {"batched_fps": len(group) * steps / (tb / 1000.0), "latency_ms_p99": float(np.percentile(lat, 99)),
+             "resid_jtj_ms": ms}
+        if prec != trk.PRECISION_FP32:
+            # the contraction's tensor work: 3 products of 2 * 128 * N per associated row (M padded to 128)
+            N = 16 * ((NP + 15) // 16)
+            tflops = 3 * 2 * 128 * N * nA / (ms / 1000.0) / 1e12
+            r["tensor_tflops_in_stage"] = tflops
+        if sample is not None:
+            r["error_vs_oracle"] = errors_vs_oracle(model, prec, *sample)
+        for x in group:
+            x.close()
+        out[name] = r
+    return out
 
 
 def run_reference(args, rank, world):
@@ -497,8 +569,14 @@ def run_ours(args, rank, world, local_rank):
         for x in extra:
             x.close()
     line = None
+    cpu, sample = None, None
+    if rank == 0 and world == 1 and args.cpu_frames > 0:
+        cpu, frames_o, states_o = cpu_baseline(model, args.cpu_frames)
+        sample = (frames_o, states_o)
+    precision = None
+    if args.precision_modes and B > 1:
+        precision = run_precision_modes(args, model, rank, dev, n_seq, flush, nA, NP, sample)
     if rank == 0:
-        cpu = cpu_baseline(model, args.cpu_frames) if (world == 1 and args.cpu_frames > 0) else None
         plain = {"value": value, "ms_per_step": max_ms / args.steps,
                  "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
                  "e2e": {"value": e2e_value, "p50_ms": 1000 * float(np.percentile(e2e_t, 50)),
@@ -519,6 +597,7 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": d2h * B, "p50_ms": head["e2e"]["p50_ms"], "p99_ms": head["e2e"]["p99_ms"]},
             "plain": plain,
             "batched": batched,
+            "precision": precision,
             "gpu_launches": info["kernels_per_frame"] * args.steps * (B if batched is not None else 1),
             "roofline": roof,
             "stage_ms": {k: round(v, 5) for k, v in prof.items()},
@@ -543,6 +622,8 @@ def main():
     ap.add_argument("--sessions", type=int, default=16, help="concurrent sessions of the batched measurement")
     ap.add_argument("--serve-streams", type=int, default=32, help="Poisson streams (30 fps each) of the serving run")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--precision-modes", type=int, default=1,
+                    help="also time the tensor-core [J r]^T [J r] modes and their error against the oracle")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)

@@ -9,6 +9,7 @@
 // which gives the same result as trying them one after the other without any host round trip.
 #include <mutex>
 
+#include "tcgen05.cuh"
 #include "trk_internal.cuh"
 
 namespace trk {
@@ -39,21 +40,23 @@ __device__ __forceinline__ float3 Lfun(float4 c, float4 h) {
 // The block's rows (compacted to A) are staged in shared memory; 16 x 16 threads each own a TxT tile
 // of the (16T) x (16T) product and sweep the rows.
 // ---------------------------------------------------------------------------------------------
-template <int T>
-__global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
-  constexpr int ROW = 16 * T + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* Js = reinterpret_cast<float*>(smem_raw);
-  DQ* sHd = reinterpret_cast<DQ*>(Js + kBlock * ROW);
-  float* sXi = reinterpret_cast<float*>(sHd + d.L);
-  int* sPar = reinterpret_cast<int*>(sXi + 6 * d.L);
-  __shared__ int s_warp[kBlock / 32];
-  const int tid = threadIdx.x;
-  for (int j = tid; j < d.L; j += kBlock) {
+// Copies the link tables this block needs (H_Delta, Xi, parents) to shared memory.
+__device__ __forceinline__ void load_link_tables(const Dev& d, DQ* sHd, float* sXi, int* sPar) {
+  for (int j = threadIdx.x; j < d.L; j += kBlock) {
     sHd[j] = d.Hd[j];
     for (int c = 0; c < 6; ++c) sXi[6 * j + c] = d.xi[8 * j + c];
     sPar[j] = d.links->parent[j];
   }
+}
+
+// Writes the [J r] rows of this block's vertices of A, compacted in vertex order, to Js (row stride ROW,
+// columns [0, width) with width >= NP, zero beyond NP) and returns their number.  Sets r2 to this
+// thread's r_i^2 (0 outside A).  Contains a __syncthreads that also publishes the link tables; the
+// caller synchronises again before reading Js.
+__device__ __forceinline__ int jacobian_rows(const Dev& d, int phi_buf, float* Js, int ROW, int width,
+                                             const DQ* sHd, const float* sXi, const int* sPar, int* s_warp,
+                                             float& r2) {
+  const int tid = threadIdx.x;
   const int i = blockIdx.x * kBlock + tid;
   bool inA = false;
   Acc4 a4 = Acc4{0, 0, 0, 0};
@@ -72,13 +75,16 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
     off += k < w ? s_warp[k] : 0;
     total += s_warp[k];
   }
+  r2 = 0.f;
   if (inA) {
     float* row = Js + (off + __popc(m & ((1u << lane) - 1u))) * ROW;
-    for (int k = 0; k < 16 * T; ++k) row[k] = 0.f;
+    for (int k = 0; k < width; ++k) row[k] = 0.f;
     const float inv = 1.f / ((float)a4.w * kFix);
     const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
     const float3 n = f3(nn);
-    row[d.L] = dot3(n, pm);
+    const float r = dot3(n, pm);
+    row[d.L] = r;
+    r2 = r * r;
     float sg[4];
     const uchar4 bi = d.bidx[i];
     const float4 bw = d.bw[i];
@@ -105,6 +111,22 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
       }
     }
   }
+  return total;
+}
+
+template <int T>
+__global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
+  constexpr int ROW = 16 * T + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Js = reinterpret_cast<float*>(smem_raw);
+  DQ* sHd = reinterpret_cast<DQ*>(Js + kBlock * ROW);
+  float* sXi = reinterpret_cast<float*>(sHd + d.L);
+  int* sPar = reinterpret_cast<int*>(sXi + 6 * d.L);
+  __shared__ int s_warp[kBlock / 32];
+  const int tid = threadIdx.x;
+  load_link_tables(d, sHd, sXi, sPar);
+  float r2;
+  const int total = jacobian_rows(d, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, s_warp, r2);
   __syncthreads();
   const int ty = tid >> 4, tx = tid & 15;
   float acc[T][T];
@@ -134,6 +156,104 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
       const int r = ty * T + a, c = tx * T + b;
       if (r < NP && c < NP) out[r * NP + c] = acc[a][b];
     }
+  if (tid == 0 && total) atomicAdd(&d.stats[1], total);
+}
+
+// ---------------------------------------------------------------------------------------------
+// The same rows contracted on the tensor cores (split-BF16x3 or 3xTF32, PREC 1 / 2): the block's rows
+// are taken in chunks of TL::K (64 BF16 / 32 TF32 rows), split into hi + lo K-major tiles and multiplied
+// by one issuing thread into an FP32 accumulator in tensor memory (128 lanes x N columns; lane = parameter
+// a, column = parameter b).  The energy entry [r]^T [r] is summed on the FP32 cores instead, so that the
+// LM acceptance test compares energies formed the same way in every precision mode.  One stage of tiles
+// (the next chunk waits for the previous chunk's MMAs) keeps the block at ~105 KB of shared memory, two
+// blocks per SM; their 2 x 128 TMEM columns fit the 512 of an SM, so tcgen05.alloc never waits.
+// ---------------------------------------------------------------------------------------------
+template <int PREC, int NB>
+__global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(Dev d, int phi_buf) {
+  using TL = tc::Tile<PREC, 8>;
+  constexpr int N = 16 * NB, ROW = N + 1, T = TL::T;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* tiles = smem_raw;  // hi tile, lo tile
+  float* Js = reinterpret_cast<float*>(smem_raw + TL::STAGE);
+  DQ* sHd = reinterpret_cast<DQ*>(Js + kBlock * ROW);
+  float* sXi = reinterpret_cast<float*>(sHd + d.L);
+  int* sPar = reinterpret_cast<int*>(sXi + 6 * d.L);
+  __shared__ int s_warp[kBlock / 32];
+  __shared__ float s_e[kBlock / 32];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int NP = d.NP;
+
+  tc::zero_padding<PREC, TL::CH, kBlock>(tiles, 2, NP);
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (w == 0) tc::tmem_alloc(&tslot, tc::kTmemCols);
+  load_link_tables(d, sHd, sXi, sPar);
+  float r2;
+  const int total = jacobian_rows(d, phi_buf, Js, ROW, NP, sHd, sXi, sPar, s_warp, r2);
+  for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  if (lane == 0) s_e[w] = r2;
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const uint32_t idesc = tc::instr_desc(tc::Split<PREC>::fmt, tc::kRows, N);
+  const uint32_t hi = tc::smem_u32(tiles);
+  const int nchunks = (total + TL::K - 1) / TL::K;
+  bool ok = true;
+  for (int q = 0; q < nchunks; ++q) {
+    if (q > 0) {  // the previous chunk's MMAs read the tiles
+      ok &= tc::mbar_wait(&bar, (q - 1) & 1);
+      tc::fence_proxy_async();
+    }
+    const int base = q * TL::K, cnt = min(TL::K, total - base);
+    const int kq = (cnt + 2 * T - 1) / (2 * T) * (2 * T);
+    const float* blk = Js + base * ROW;
+    tc::stage_chunk<PREC, TL::CH, kBlock>([&](int k, int m) { return k < cnt ? blk[k * ROW + m] : 0.f; }, kq, NP,
+                                          tiles);
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      tc::issue_chunk<PREC, TL::CH>(tmem, hi, hi + TL::BYTES, kq / (2 * T), idesc, q == 0);
+      tc::commit(&bar);
+    }
+  }
+  if (nchunks > 0) {
+    ok &= tc::mbar_wait(&bar, (nchunks - 1) & 1);
+    tc::fence_after_sync();
+  }
+  float E = 0.f;
+  for (int k = 0; k < kBlock / 32; ++k) E += s_e[k];
+  // warps w and w + 4 read the same 32 TMEM lanes (parameters a), alternate 8-column groups (b)
+  float* out = d.partial + (size_t)blockIdx.x * NP * NP;
+  const int a = 32 * (w & 3) + lane;
+  const float bad = __int_as_float(0x7fc00000);
+  for (int g = w >> 2; g < N / 8; g += 2) {
+    uint32_t r[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    if (nchunks > 0) {
+      tc::ld_x8(tmem + ((uint32_t)(32 * (w & 3)) << 16) + 8 * g, r);
+      tc::ld_wait(r);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int b = 8 * g + t;
+      if (a < NP && b < NP) out[b * NP + a] = (a == NP - 1 && b == NP - 1) ? E : (ok ? __uint_as_float(r[t]) : bad);
+    }
+  }
+  if (!ok && tid == 0) {
+    atomicExch(&d.stats[3], 1);
+    tc::mbar_wait(&bar, (nchunks - 1) & 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (w == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, tc::kTmemCols);
+  }
   if (tid == 0 && total) atomicAdd(&d.stats[1], total);
 }
 
@@ -169,7 +289,37 @@ static int jtj_smem_bytes(int T, int L) {
   return kBlock * (16 * T + 1) * 4 + L * (int)sizeof(DQ) + 6 * L * 4 + L * 4;
 }
 
+template <int PREC>
+static int jtj_tc_smem_bytes(int NB, int L) {
+  return tc::Tile<PREC, 8>::STAGE + kBlock * (16 * NB + 1) * 4 + L * (int)sizeof(DQ) + 6 * L * 4 + L * 4;
+}
+
+template <int PREC>
+static void launch_resid_jtj_tc(const Dev& d, int phi_buf, cudaStream_t st) {
+  const int NB = (d.NP + 15) / 16;
+  const int g = d.nblk_jtj;
+  const int sm = jtj_tc_smem_bytes<PREC>(NB, d.L);
+  switch (NB) {
+    case 1: k_resid_jtj_tc<PREC, 1><<<g, kBlock, sm, st>>>(d, phi_buf); break;
+    case 2: k_resid_jtj_tc<PREC, 2><<<g, kBlock, sm, st>>>(d, phi_buf); break;
+    case 3: k_resid_jtj_tc<PREC, 3><<<g, kBlock, sm, st>>>(d, phi_buf); break;
+    case 4: k_resid_jtj_tc<PREC, 4><<<g, kBlock, sm, st>>>(d, phi_buf); break;
+    default: k_resid_jtj_tc<PREC, 5><<<g, kBlock, sm, st>>>(d, phi_buf); break;
+  }
+}
+
+template <int PREC>
+static void configure_resid_jtj_tc() {
+  cudaFuncSetAttribute(k_resid_jtj_tc<PREC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_tc_smem_bytes<PREC>(1, kMaxLinks));
+  cudaFuncSetAttribute(k_resid_jtj_tc<PREC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_tc_smem_bytes<PREC>(2, kMaxLinks));
+  cudaFuncSetAttribute(k_resid_jtj_tc<PREC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_tc_smem_bytes<PREC>(3, kMaxLinks));
+  cudaFuncSetAttribute(k_resid_jtj_tc<PREC, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_tc_smem_bytes<PREC>(4, kMaxLinks));
+  cudaFuncSetAttribute(k_resid_jtj_tc<PREC, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_tc_smem_bytes<PREC>(5, kMaxLinks));
+}
+
 void launch_resid_jtj(const Dev& d, int phi_buf, cudaStream_t st) {
+  if (d.precision == 1) return launch_resid_jtj_tc<1>(d, phi_buf, st);
+  if (d.precision == 2) return launch_resid_jtj_tc<2>(d, phi_buf, st);
   const int T = (d.NP + 15) / 16;
   const int g = d.nblk_jtj;
   const int sm = jtj_smem_bytes(T, d.L);
@@ -751,6 +901,8 @@ void configure_tc_kernels();
 
 void configure_kernels() {
   configure_tc_kernels();
+  configure_resid_jtj_tc<1>();
+  configure_resid_jtj_tc<2>();
   cudaFuncSetAttribute(k_resid_jtj<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(1, kMaxLinks));
   cudaFuncSetAttribute(k_resid_jtj<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(2, kMaxLinks));
   cudaFuncSetAttribute(k_resid_jtj<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(3, kMaxLinks));

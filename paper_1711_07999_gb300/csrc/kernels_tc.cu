@@ -24,7 +24,7 @@ template <int PREC, int NB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_jtj_rows_tc(const float* __restrict__ rows, int n, int nc, int ld, int rows_per_block,
                   float* __restrict__ partial) {
-  using TL = tc::Tile<PREC>;
+  using TL = tc::Tile<PREC, tc::kChunkRows / tc::Split<PREC>::T>;
   constexpr int N = 16 * NB, T = TL::T;
   extern __shared__ __align__(1024) unsigned char smem[];  // two stages of (hi tile, lo tile)
   __shared__ uint64_t bars[2];
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nrows = max(0, r1 - r0);
   const int nchunks = (nrows + tc::kChunkRows - 1) / tc::kChunkRows;
 
-  tc::zero_padding<PREC, kTcThreads>(smem, 4, nc);
+  tc::zero_padding<PREC, TL::CH, kTcThreads>(smem, 4, nc);
   if (tid == 0) {
     tc::mbar_init(&bars[0], 1);
     tc::mbar_init(&bars[1], 1);
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int cnt = min(tc::kChunkRows, r1 - base);
     const int kq = (cnt + 2 * T - 1) / (2 * T) * (2 * T);
     const float* blk = rows + (size_t)base * ld;
-    tc::stage_chunk<PREC, kTcThreads>(
+    tc::stage_chunk<PREC, TL::CH, kTcThreads>(
         [&](int k, int m) { return k < cnt ? __ldg(blk + (size_t)k * ld + m) : 0.f; }, kq, nc,
         smem + st * TL::STAGE);
     tc::fence_proxy_async();
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (tid == 0) {
       tc::fence_after_sync();
       const uint32_t hi = sbase + st * TL::STAGE;
-      tc::issue_chunk<PREC>(tmem, hi, hi + TL::BYTES, kq / (2 * T), idesc, pending == 0);
+      tc::issue_chunk<PREC, TL::CH>(tmem, hi, hi + TL::BYTES, kq / (2 * T), idesc, pending == 0);
       tc::commit(&bars[st]);
     }
     ++pending;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 template <int PREC>
 static constexpr int tc_rows_smem() {
-  return 2 * tc::Tile<PREC>::STAGE;
+  return 2 * tc::Tile<PREC, tc::kChunkRows / tc::Split<PREC>::T>::STAGE;
 }
 
 template <int PREC>

@@ -1,7 +1,7 @@
 // server.cu -- continuous-batching frame server over tracking sessions (the serving calls of trk.h).
 //
 // A dispatcher thread keeps every attached session's frames flowing: a submitted frame is copied into a
-// pinned staging buffer at once; as soon as its session has no frame on the GPU and one of the
+// pinned staging buffer at once (buffers are pooled per session and reused once a frame is collected); as soon as its session has no frame on the GPU and one of the
 // max_inflight slots is free, the frame is launched on the session's own stream (H2D of the depth, the
 // session's frame graph, D2H of the results, an event).  Frames of different sessions therefore overlap
 // on the device, new requests are admitted whenever a slot frees up, and one session's frames run in
@@ -33,15 +33,20 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
-struct Request {
-  uint64_t ticket = 0;
-  trk_session* s = nullptr;
+// Pinned staging of one frame of one session (reused: pinning host memory takes milliseconds).
+struct Staging {
   float* depth = nullptr;     // pinned [H*W]
   double* theta = nullptr;    // pinned [L]
   float* phi4 = nullptr;      // pinned [V][4]
   double* energy = nullptr;   // pinned [pose + shape iters]
-  int* stats = nullptr;       // pinned [2]
+  int* stats = nullptr;       // pinned [4]
   cudaEvent_t done_ev = nullptr;
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  trk_session* s = nullptr;
+  Staging* b = nullptr;
   clk::time_point t_submit, t_done;
   int state = 0;              // 0 queued, 1 on the GPU, 2 done
   trk_status status = TRK_OK;
@@ -50,6 +55,7 @@ struct Request {
 struct SessionSlot {
   std::deque<Request*> pending;
   Request* inflight = nullptr;
+  std::vector<Staging*> spare;  // staging buffers of collected frames, ready for reuse
 };
 
 }  // namespace
@@ -71,14 +77,35 @@ struct trk_server {
 
 namespace {
 
+void free_staging(Staging* b) {
+  if (!b) return;
+  if (b->done_ev) cudaEventDestroy(b->done_ev);
+  cudaFreeHost(b->depth);
+  cudaFreeHost(b->theta);
+  cudaFreeHost(b->phi4);
+  cudaFreeHost(b->energy);
+  cudaFreeHost(b->stats);
+  delete b;
+}
+
+Staging* new_staging(size_t npx, int L, int V, int ne) {
+  Staging* b = new Staging();
+  const bool ok = cudaMallocHost(&b->depth, sizeof(float) * npx) == cudaSuccess &&
+                  cudaMallocHost(&b->theta, sizeof(double) * L) == cudaSuccess &&
+                  cudaMallocHost(&b->phi4, sizeof(float) * 4 * V) == cudaSuccess &&
+                  cudaMallocHost(&b->energy, sizeof(double) * std::max(ne, 1)) == cudaSuccess &&
+                  cudaMallocHost(&b->stats, sizeof(int) * 4) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&b->done_ev, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    free_staging(b);
+    return nullptr;
+  }
+  return b;
+}
+
 void free_request(Request* r) {
   if (!r) return;
-  if (r->done_ev) cudaEventDestroy(r->done_ev);
-  cudaFreeHost(r->depth);
-  cudaFreeHost(r->theta);
-  cudaFreeHost(r->phi4);
-  cudaFreeHost(r->energy);
-  cudaFreeHost(r->stats);
+  free_staging(r->b);
   delete r;
 }
 
@@ -91,9 +118,9 @@ void launch_ready(trk_server* sv) {
     Request* r = sl.pending.front();
     sl.pending.pop_front();
     cudaStream_t st = nullptr;
-    trk_status e = trk::session_enqueue_frame(r->s, r->depth, &st);
-    if (e == TRK_OK) e = trk::session_enqueue_results(r->s, r->theta, r->phi4, r->energy, r->stats);
-    if (e == TRK_OK && cudaEventRecord(r->done_ev, st) != cudaSuccess) e = TRK_ERR_CUDA;
+    trk_status e = trk::session_enqueue_frame(r->s, r->b->depth, &st);
+    if (e == TRK_OK) e = trk::session_enqueue_results(r->s, r->b->theta, r->b->phi4, r->b->energy, r->b->stats);
+    if (e == TRK_OK && cudaEventRecord(r->b->done_ev, st) != cudaSuccess) e = TRK_ERR_CUDA;
     if (e != TRK_OK) {
       r->status = e;
       r->state = 2;
@@ -117,7 +144,7 @@ void worker_loop(trk_server* sv) {
       Request* r = kv.second.inflight;
       if (!r) continue;
       any = true;
-      const cudaError_t q = cudaEventQuery(r->done_ev);
+      const cudaError_t q = cudaEventQuery(r->b->done_ev);
       if (q == cudaErrorNotReady) continue;
       r->status = q == cudaSuccess ? TRK_OK : TRK_ERR_CUDA;
       r->state = 2;
@@ -175,6 +202,7 @@ trk_status trk_server_detach(trk_server* sv, trk_session* s) {
   if (!it->second.pending.empty() || it->second.inflight)
     return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_detach: the session still has frames");
   sv->used -= trk::session_device_bytes(s);
+  for (Staging* b : it->second.spare) free_staging(b);
   sv->sessions.erase(it);
   return TRK_OK;
 }
@@ -187,23 +215,29 @@ trk_status trk_server_submit(trk_server* sv, trk_session* s, const float* depth_
   trk_get_info(s, &inf);
   const size_t npx = (size_t)inf.width * inf.height;
   Request* r = new Request();
-  bool ok = cudaMallocHost(&r->depth, sizeof(float) * npx) == cudaSuccess &&
-            cudaMallocHost(&r->theta, sizeof(double) * L) == cudaSuccess &&
-            cudaMallocHost(&r->phi4, sizeof(float) * 4 * V) == cudaSuccess &&
-            cudaMallocHost(&r->energy, sizeof(double) * std::max(ne, 1)) == cudaSuccess &&
-            cudaMallocHost(&r->stats, sizeof(int) * 2) == cudaSuccess &&
-            cudaEventCreateWithFlags(&r->done_ev, cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    free_request(r);
-    return trk::set_error(TRK_ERR_OOM, "trk_server_submit: pinned staging allocation failed");
-  }
-  std::memcpy(r->depth, depth_m, sizeof(float) * npx);
   r->s = s;
   r->t_submit = clk::now();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     auto it = sv->sessions.find(s);
     if (it == sv->sessions.end()) {
+      delete r;
+      return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_submit: session not attached");
+    }
+    if (!it->second.spare.empty()) {
+      r->b = it->second.spare.back();
+      it->second.spare.pop_back();
+    }
+  }
+  if (!r->b && !(r->b = new_staging(npx, L, V, ne))) {
+    delete r;
+    return trk::set_error(TRK_ERR_OOM, "trk_server_submit: pinned staging allocation failed");
+  }
+  std::memcpy(r->b->depth, depth_m, sizeof(float) * npx);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->sessions.find(s);
+    if (it == sv->sessions.end()) {  // detached meanwhile
       free_request(r);
       return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_submit: session not attached");
     }
@@ -236,18 +270,27 @@ trk_status trk_server_wait(trk_server* sv, uint64_t ticket, int64_t timeout_us, 
     }
   }
   lk.unlock();
-  const trk_status st = r->status;
+  const Staging* b = r->b;
+  trk_status st = r->status;
+  if (st == TRK_OK && b->stats[3]) st = trk::set_error(TRK_ERR_TIMEOUT, "trk_server_wait: a tensor-core wait ran out");
   if (st == TRK_OK && out) {
     int L = 0, V = 0, ne = 0;
     trk::session_result_sizes(r->s, &L, &V, &ne);
-    if (out->theta) std::memcpy(out->theta, r->theta, sizeof(double) * L);
-    if (out->energy) std::memcpy(out->energy, r->energy, sizeof(double) * ne);
+    if (out->theta) std::memcpy(out->theta, b->theta, sizeof(double) * L);
+    if (out->energy) std::memcpy(out->energy, b->energy, sizeof(double) * ne);
     if (out->offsets)
       for (int i = 0; i < V; ++i)
-        for (int c = 0; c < 3; ++c) out->offsets[3 * i + c] = r->phi4[4 * i + c];
-    out->n_assoc_px = r->stats[0];
-    out->n_assoc_verts = r->stats[1];
+        for (int c = 0; c < 3; ++c) out->offsets[3 * i + c] = b->phi4[4 * i + c];
+    out->n_assoc_px = b->stats[0];
+    out->n_assoc_verts = b->stats[1];
   }
+  lk.lock();  // the staging goes back to its session (or is freed if the session left meanwhile)
+  auto it = sv->sessions.find(r->s);
+  if (it != sv->sessions.end()) {
+    it->second.spare.push_back(r->b);
+    r->b = nullptr;
+  }
+  lk.unlock();
   free_request(r);
   if (st != TRK_OK) return trk::set_error(st, "trk_server_wait: the frame failed on the device");
   return TRK_OK;
@@ -280,8 +323,10 @@ void trk_server_destroy(trk_server* sv) {
   }
   sv->cv_work.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
-  for (auto& kv : sv->sessions)
-    if (kv.second.inflight) cudaEventSynchronize(kv.second.inflight->done_ev);
+  for (auto& kv : sv->sessions) {
+    if (kv.second.inflight) cudaEventSynchronize(kv.second.inflight->b->done_ev);
+    for (Staging* b : kv.second.spare) free_staging(b);
+  }
   for (auto& kv : sv->requests) free_request(kv.second);
   delete sv;
 }

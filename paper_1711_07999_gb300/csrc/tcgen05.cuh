@@ -202,21 +202,22 @@ struct Split<2> {
   }
 };
 
-constexpr int kChunkRows = 64;  // rows of [J r] per operand tile (K of one tile)
+constexpr int kChunkRows = 64;  // rows of [J r] per operand tile of the standalone contraction
 
-template <int PREC>
+// Operand tiles with CH core matrices along K (K = CH * T rows of [J r]), 128 rows (M).
+template <int PREC, int CH_>
 struct Tile {
   static constexpr int T = Split<PREC>::T;
-  static constexpr int CH = kChunkRows / T;          // core matrices along K
+  static constexpr int CH = CH_;
+  static constexpr int K = CH * T;                       // rows of [J r] per tile
   static constexpr int BYTES = (kRows / 8) * CH * 128;  // one operand tile (hi or lo)
   static constexpr int STAGE = 2 * BYTES;               // hi tile, then lo tile
 };
 
 // Issues the MMAs of one staged chunk: nsteps steps of 2T rows, three products each.
-template <int PREC>
+template <int PREC, int CH>
 __device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t hi, uint32_t lo, int nsteps, uint32_t idesc,
                                             bool overwrite) {
-  constexpr int CH = Tile<PREC>::CH;
   for (int j = 0; j < nsteps; ++j) {
     const uint64_t ah = tile_desc(hi, j, CH), al = tile_desc(lo, j, CH);
     Split<PREC>::mma(tmem, ah, ah, idesc, (overwrite && j == 0) ? 0u : 1u);
@@ -226,22 +227,21 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t hi, uint32_t
 }
 
 // Zeroes rows [nc, 128) of n_tiles consecutive operand tiles (the M padding; never written again).
-template <int PREC, int NT>
+template <int PREC, int CH, int NT>
 __device__ __forceinline__ void zero_padding(unsigned char* tiles, int n_tiles, int nc) {
-  constexpr int CH = Tile<PREC>::CH;
   const int per_tile = (kRows - nc) * CH;
   for (int e = threadIdx.x; e < n_tiles * per_tile; e += NT) {
     const int t = e / per_tile, r = e % per_tile;
-    *reinterpret_cast<uint4*>(tiles + t * Tile<PREC>::BYTES + tile_offset(nc + r / CH, r % CH, CH)) =
+    *reinterpret_cast<uint4*>(tiles + t * Tile<PREC, CH>::BYTES + tile_offset(nc + r / CH, r % CH, CH)) =
         make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
 // Splits rows [0, kq) of a chunk (kq a multiple of 2T; src(k, m) = 0 for rows past the data) for the
 // columns m < nc into the hi and lo tiles at stage.
-template <int PREC, int NT, class Src>
+template <int PREC, int CH, int NT, class Src>
 __device__ __forceinline__ void stage_chunk(const Src& src, int kq, int nc, unsigned char* stage) {
-  constexpr int T = Tile<PREC>::T, CH = Tile<PREC>::CH;
+  constexpr int T = Split<PREC>::T;
   const int items = nc * (kq / T);
   for (int q = threadIdx.x; q < items; q += NT) {
     const int m = q % nc, c = q / nc;
@@ -252,7 +252,7 @@ __device__ __forceinline__ void stage_chunk(const Src& src, int kq, int nc, unsi
     Split<PREC>::pack(x, hi, lo);
     const int off = tile_offset(m, c, CH);
     *reinterpret_cast<uint4*>(stage + off) = hi;
-    *reinterpret_cast<uint4*>(stage + Tile<PREC>::BYTES + off) = lo;
+    *reinterpret_cast<uint4*>(stage + Tile<PREC, CH>::BYTES + off) = lo;
   }
 }
 

@@ -163,7 +163,9 @@ trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsi
   if (c->width <= 0 || c->height <= 0 || !(c->fx > 0) || !(c->fy > 0) || !std::isfinite(c->cx) || !std::isfinite(c->cy))
     return fail(TRK_ERR_INVALID_ARG, "bad intrinsics");
   if ((long long)c->width * c->height > (1ll << 28)) return fail(TRK_ERR_NO_CAPACITY, "image too large");
-  if (p->precision != 0) return fail(TRK_ERR_INVALID_ARG, "precision %d not supported", p->precision);
+  if (p->precision != TRK_PRECISION_FP32 && p->precision != TRK_PRECISION_BF16X3 &&
+      p->precision != TRK_PRECISION_TF32X3)
+    return fail(TRK_ERR_INVALID_ARG, "precision %d not supported", p->precision);
   if (p->pose_iters < 0 || p->shape_iters < 0 || p->shape_sweeps < 1 || p->knn < 0 || p->knn > 4 ||
       p->window_half_px < 0 || !(p->cutoff_m > 0) || !(p->lambda_k0 > 0) || p->lambda_s < 0 || p->lambda_phi < 0 ||
       p->lambda_N < 0 || p->lambda_w < 0 || !(p->z_near_m > 0) || !(p->eps_vis_m >= 0))
@@ -239,7 +241,7 @@ trk_status fetch_result(trk_session* s, cudaStream_t st, trk_result* out) {
   double* h = s->h_pinned;  // [L] theta, [ne] energy, [1] stats
   CK(cudaMemcpyAsync(h, d.theta, sizeof(double) * d.L, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h + d.L, d.energy, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h + d.L + ne, d.stats, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h + d.L + ne, d.stats, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   std::vector<float4> phi;
   if (out->offsets) {
     phi.resize(d.V);
@@ -248,10 +250,11 @@ trk_status fetch_result(trk_session* s, cudaStream_t st, trk_result* out) {
   CK(cudaStreamSynchronize(st));
   if (out->theta) std::memcpy(out->theta, h, sizeof(double) * d.L);
   if (out->energy) std::memcpy(out->energy, h + d.L, sizeof(double) * ne);
-  int stats[2];
+  int stats[4];
   std::memcpy(stats, h + d.L + ne, sizeof(stats));
   out->n_assoc_px = stats[0];
   out->n_assoc_verts = stats[1];
+  if (stats[3]) return fail(TRK_ERR_TIMEOUT, "a tensor-core completion wait ran out; results are not valid");
   if (out->offsets)
     for (int i = 0; i < d.V; ++i) {
       out->offsets[3 * i] = phi[i].x;
@@ -295,7 +298,7 @@ trk_status session_enqueue_results(trk_session* s, double* theta, float* phi4, d
   CK(cudaMemcpyAsync(theta, d.theta, sizeof(double) * d.L, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(phi4, d.phi[0], sizeof(float4) * d.V, cudaMemcpyDeviceToHost, s->stream));
   if (ne > 0) CK(cudaMemcpyAsync(energy, d.energy, sizeof(double) * ne, cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaMemcpyAsync(stats, d.stats, sizeof(int) * 2, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(stats, d.stats, sizeof(int) * 4, cudaMemcpyDeviceToHost, s->stream));
   return TRK_OK;
 }
 }  // namespace trk
@@ -337,6 +340,7 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   d.V = V; d.F = F; d.L = L; d.NP = L + 1;
   d.pose_iters = prm->pose_iters; d.shape_iters = prm->shape_iters; d.shape_sweeps = prm->shape_sweeps;
   d.knn = prm->knn;
+  d.precision = prm->precision;
   d.lambda_phi = prm->lambda_phi; d.lambda_N = prm->lambda_N; d.lambda_w = prm->lambda_w;
   d.cam.W = W; d.cam.H = H; d.cam.fx = cam->fx; d.cam.fy = cam->fy; d.cam.cx = cam->cx; d.cam.cy = cam->cy;
   d.cam.z_near = prm->z_near_m; d.cam.eps_vis = prm->eps_vis_m; d.cam.tau = prm->cutoff_m; d.cam.R = prm->window_half_px;

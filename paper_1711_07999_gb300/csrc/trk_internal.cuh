@@ -289,7 +289,8 @@ struct Dev {
   double* epart;    // [nblk_v][8]
   int nblk_v;
   unsigned int* counter;  // [4] last-block tickets
-  int* stats;             // [0] associated pixels, [1] associated vertices
+  int* stats;             // [0] associated pixels, [1] associated vertices, [3] tensor-core wait ran out
+  int precision;          // TRK_PRECISION_*: arithmetic of [J r]^T [J r]
 };
 
 }  // namespace trk

@@ -1,0 +1,232 @@
+"""The tensor-core precision modes of a frame (split-BF16x3 and 3xTF32 [J r]^T [J r], Eqs. JTJ and JTr)
+against the FP64 oracle.
+
+Tolerances, from the arithmetic:
+  normal equations  the FP32 path's tolerance (1e-5 of the largest entry, for the FP32 Jacobian rows)
+                    plus the split bound (3 u^2 + 770 * 2^-24) sum_k |x_ka x_kb| (u = 2^-8 BF16,
+                    2^-11 TF32; hi + lo leaves u^2 |x| out, lo_a lo_b is dropped, and a block's at most
+                    256 rows are summed in FP32 by 3 MMAs each before the FP64 sum across blocks);
+  energy            1e-5 relative, as in FP32 mode (E is summed on the FP32 cores in every mode);
+  frames            joint values 1e-3 rad and offsets 0.05 mm, as in FP32 mode.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_07999_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1711_07999_gb300 import trk  # noqa: E402
+
+PRECS = [trk.PRECISION_BF16X3, trk.PRECISION_TF32X3]
+U = {trk.PRECISION_BF16X3: 2.0 ** -8, trk.PRECISION_TF32X3: 2.0 ** -11}
+
+
+def _scene(cfg, prec, seed=0, pert=2.0, V=None, width=None):
+    m = synth.make_model(cfg, V=V, width=width, precision=prec)
+    o = oracle.Oracle(m)
+    depth = synth.add_noise(o.render(synth.gt_theta(m, 0.0), synth.gt_offsets(m, 0.0)), cfg,
+                            np.random.default_rng(seed))
+    rng = np.random.default_rng(seed + 7)
+    th = synth.gt_theta(m, 0.0) + np.radians(pert) * rng.normal(size=o.L) * (m["skeleton"]["type"] == 0)
+    phi = (synth.gt_offsets(m, 0.0) * 0.5).astype(np.float32).astype(np.float64)
+    return m, o, depth, th, phi
+
+
+def _oracle_rows(o, s, th, phi, depth):
+    v, _ = o.skin(th, phi)
+    n, ok = o.normals(v)
+    acc, cnt = o.accumulate(v, depth, s.read("CORR"))
+    r, inA, E = o.residuals(th, n, ok, acc, cnt)
+    J = o.jacobian(th, phi, n, inA)
+    JTJ, JTr = oracle.normal_eq(J, r, inA)
+    return J, r, inA, JTJ, JTr, E
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_normal_equations_within_the_split_bound(prec):
+    m, o, depth, th, phi = _scene(1, prec)
+    with trk.Session(m) as s:
+        s.set_pose(th, phi)
+        s.set_depth(depth)
+        for st in ("skin", "raster", "visibility", "associate", "normal_equations"):
+            s.step(st)
+        A = s.read("NORMAL_EQ")
+        E = s.read("ENERGY")[0]
+        J, r, inA, JTJ, JTr, E_ref = _oracle_rows(o, s, th, phi, depth)
+    L = o.L
+    R = np.column_stack([J, r])[inA.astype(bool)]
+    mag = np.abs(R).T @ np.abs(R)
+    ref = np.zeros((L + 1, L + 1))
+    ref[:L, :L], ref[:L, L], ref[L, :L] = JTJ, JTr, JTr
+    tol = 1e-5 * np.abs(JTJ).max() + (3 * U[prec] ** 2 + 770 * 2.0 ** -24) * mag
+    err = np.abs(A - ref)
+    err[L, L] = 0.0
+    assert (err <= tol).all(), (err / tol).max()
+    assert E == pytest.approx(E_ref, rel=1e-5)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_energy_per_iteration_at_matched_state(prec):
+    m, o, depth, th, phi = _scene(1, prec, seed=4)
+    with trk.Session(m) as s:
+        s.set_pose(synth.start_theta(m))
+        s.set_depth(depth)
+        for it in range(m["params"]["pose_iters"]):
+            th_g = s.read("THETA")
+            for st in ("skin", "raster", "visibility", "associate", "normal_equations"):
+                s.step(st)
+            E_g = s.read("ENERGY")[0]
+            *_, E_ref = _oracle_rows(o, s, th_g, np.zeros((o.V, 3)), depth)
+            assert E_g == pytest.approx(E_ref, rel=1e-5), it
+            s.step("lm")
+
+
+def _assert_offsets_close(phi, phi_ref):
+    d = np.abs(phi - phi_ref).max(axis=1)
+    assert np.percentile(d, 99) < 5e-5, np.percentile(d, 99)
+    assert (d > 5e-5).mean() <= 1e-2, (d > 5e-5).sum()
+    assert d.max() < 0.05, d.max()
+
+
+def _track_both(m, o, frames, th0):
+    out = []
+    with trk.Session(m) as s:
+        s.set_pose(th0)
+        o.set_state(th0, None)
+        for d in frames:
+            g = s.track_frame(d)
+            e_ref, _, na_ref = o.track_frame(d)
+            th_ref, phi_ref, _ = o.get_state()
+            out.append((g, e_ref, th_ref, phi_ref, na_ref))
+    return out
+
+
+def _report(tag, outs):
+    for f, (g, e_ref, th_ref, phi_ref, _) in enumerate(outs):
+        d = np.abs(g["offsets"] - phi_ref).max(axis=1)
+        print(f"{tag} frame {f}: |dtheta| max {np.abs(g['theta'] - th_ref).max():.2e} rad, "
+              f"|dphi| p99 {np.percentile(d, 99) * 1e3:.2e} mm max {d.max() * 1e3:.2e} mm, "
+              f"|dE|/E max {np.max(np.abs(g['energy'] - e_ref) / e_ref):.2e}")
+
+
+def test_frame_config1_end_to_end_tf32x3():
+    m, o, depth, th, phi = _scene(1, trk.PRECISION_TF32X3, seed=3)
+    outs = _track_both(m, o, [depth] * 3, synth.start_theta(m))
+    _report("cfg1 TF32X3", outs)
+    g, e_ref, th_ref, phi_ref, na_ref = outs[-1]
+    assert np.abs(g["theta"] - th_ref).max() < 1e-3
+    _assert_offsets_close(g["offsets"], phi_ref)
+    assert abs(g["n_assoc_px"] - na_ref) <= max(5, 0.01 * na_ref)
+
+
+def test_frame_config1_bf16x3_reaches_the_same_fit():
+    """Split-BF16x3 keeps ~16 bits of each product; on this unconverged start (10 degrees off) its steps
+    differ from the FP64 steps by ~1e-4 relative, a later association differs, and the trajectory ends
+    elsewhere in the flat valley of the energy (about 1e-2 rad in the joint values after three frames).
+    Checked: the fit it reaches is as good (final pose energy within 1 %)."""
+    m, o, depth, th, phi = _scene(1, trk.PRECISION_BF16X3, seed=3)
+    outs = _track_both(m, o, [depth] * 3, synth.start_theta(m))
+    _report("cfg1 BF16X3", outs)
+    g, e_ref = outs[-1][0], outs[-1][1]
+    P = m["params"]["pose_iters"]
+    assert abs(g["energy"][P - 1] - e_ref[P - 1]) <= 1e-2 * e_ref[P - 1]
+    assert np.isfinite(g["theta"]).all() and np.isfinite(g["offsets"]).all()
+
+
+@pytest.fixture(scope="module")
+def cfg3():
+    m = synth.make_model(3)
+    o = oracle.Oracle(m)
+    depth = synth.add_noise(o.render(synth.gt_theta(m, 0.0), synth.gt_offsets(m, 0.0)), 3, np.random.default_rng(13))
+    return m, o, depth
+
+
+@pytest.mark.parametrize("prec", [trk.PRECISION_FP32] + PRECS)
+def test_config3_iterations_at_matched_state(cfg3, prec):
+    """The 200k-vertex / 1280x720 workload, four pose iterations: at each, the oracle at the GPU's own
+    state and association gives the same energy (1e-5), normal equations within the mode's bound, and
+    the FP64 LM step of the GPU's system gives the GPU's decision and step (1e-6 rad)."""
+    m0, o, depth = cfg3
+    m = synth.make_model(3, precision=prec)
+    L = o.L
+    with trk.Session(m) as s:
+        s.set_pose(synth.start_theta(m))
+        s.set_depth(depth)
+        for it in range(4):
+            th_g = s.read("THETA")
+            lam = s.read("LAMBDA")[0]
+            for st in ("skin", "raster", "visibility", "associate", "normal_equations"):
+                s.step(st)
+            E_g = s.read("ENERGY")[0]
+            A = s.read("NORMAL_EQ")
+            zero = np.zeros((o.V, 3))
+            v, _ = o.skin(th_g, zero)
+            n, ok = o.normals(v)
+            acc, cnt = o.accumulate(v, depth, s.read("CORR"))
+            r, inA, E_ref = o.residuals(th_g, n, ok, acc, cnt)
+            J = o.jacobian(th_g, zero, n, inA)
+            JTJ, JTr = oracle.normal_eq(J, r, inA)
+            assert E_g == pytest.approx(E_ref, rel=1e-5), it
+            R = np.column_stack([J, r])[inA.astype(bool)]
+            mag = np.abs(R).T @ np.abs(R)
+            u2 = 0.0 if prec == trk.PRECISION_FP32 else 3 * U[prec] ** 2 + 770 * 2.0 ** -24
+            ref = np.zeros((L + 1, L + 1))
+            ref[:L, :L], ref[:L, L], ref[L, :L] = JTJ, JTr, JTr
+            err = np.abs(A - ref)
+            err[L, L] = 0.0
+            assert (err <= 1e-5 * np.abs(JTJ).max() + u2 * mag).all(), it
+            s.step("lm")
+            trials = s.read("LM_TRIALS")
+            o.set_state(th_g, None)
+            a_ref, th_ref, lam_ref, _ = o.lm_step(A[:L, :L], A[:L, L], trials[6], v, n, acc, cnt, inA, th_g, lam)
+            assert int(trials[7]) == a_ref, it
+            assert np.abs(s.read("THETA") - th_ref).max() < 1e-6, it
+
+
+def _determined(o, th, phi, depth, tol=1e-3):
+    """DoFs the energy fixes to within tol: moving DoF k (the others re-optimised) by tol raises the
+    energy by more than the per-iteration energy tolerance (1e-5 relative), i.e.
+    sqrt(1e-5 E [H^-1]_kk) < tol with H = J^T J + prior at the oracle's final state."""
+    P = o.pass_at(th, phi, depth)
+    J = o.jacobian(th, phi, P["n"], P["inA"])
+    JTJ, _ = oracle.normal_eq(J, P["r"], P["inA"])
+    _, S, _ = o.derived()
+    H = JTJ + np.diag((o.params["lambda_s"] * S) ** 2)
+    spread = np.sqrt(1e-5 * P["E"] * np.diag(np.linalg.inv(H)))
+    return spread < tol
+
+
+@pytest.mark.parametrize("prec", [trk.PRECISION_FP32] + PRECS)
+def test_config3_frame_free_running(cfg3, prec):
+    """One free-running frame of the 200k-vertex / 1280x720 workload.  Joint values are compared at
+    1e-3 rad where the energy determines them to that tolerance (the hand and head-twist DoFs of this
+    body move ~1e-2 rad for a 1e-5 change of E, so two correct runs differ there); the final pose energy
+    within 1e-3 and the offsets as in FP32 mode (BF16X3: energy only, its ~16-bit products steer the
+    weak directions further)."""
+    m0, o, depth = cfg3
+    m = synth.make_model(3, precision=prec)
+    outs = _track_both(m, o, [depth], synth.start_theta(m))
+    _report(f"cfg3 prec {prec}", outs)
+    g, e_ref, th_ref, phi_ref, _ = outs[0]
+    P = m["params"]["pose_iters"]
+    assert abs(g["energy"][P - 1] - e_ref[P - 1]) <= 1e-3 * e_ref[P - 1]
+    if prec == trk.PRECISION_BF16X3:
+        return
+    det = _determined(o, th_ref, phi_ref, depth)
+    print(f"  {det.sum()} of {det.size} DoFs determined to 1e-3 rad; "
+          f"max error there {np.abs(g['theta'] - th_ref)[det].max():.2e}")
+    assert det.sum() >= det.size // 2
+    assert np.abs(g["theta"] - th_ref)[det].max() < 1e-3
+    _assert_offsets_close(g["offsets"], phi_ref)
+
+
+def test_invalid_precision_is_rejected():
+    m = synth.make_model(1, V=500, width=64, precision=7)
+    with pytest.raises(trk.TrkError) as e:
+        trk.Session(m)
+    assert e.value.status == trk.TRK_ERR_INVALID_ARG
