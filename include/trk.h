@@ -267,6 +267,29 @@ trk_status trk_jtj_rows(const float* d_rows, int32_t n_rows, int32_t n_cols, int
 trk_status trk_jtj_rows_noalloc(const float* d_rows, int32_t n_rows, int32_t n_cols, int32_t ld, double* d_out,
                                 void* cuda_stream);
 
+/* ---- batches: many sessions stepped by the same launches ------------------------------------------
+ * A batch runs one frame of every member session per call, each stage of the frame (Secs. 4.1-4.3) as
+ * ONE kernel launch over the blocks of all members (a block table maps each block to its session), the
+ * whole frame as one CUDA graph.  Members may differ in mesh, skeleton and image size; they must share
+ * the device (the current one), the iteration schedule (pose_iters, shape_iters, shape_sweeps) and the
+ * precision.  Each member's results are bitwise those it computes alone.  A session may belong to
+ * several batches but must not be stepped by two calls at the same time (same rule as for sessions). */
+typedef struct trk_batch trk_batch;
+
+/* Builds the block tables and captures the frame graph.  The session pointers are borrowed: destroy the
+ * batch before any of its sessions.  Errors: TRK_ERR_INVALID_ARG (NULL or repeated session, members that
+ * differ in device, schedule or precision), TRK_ERR_OOM, TRK_ERR_CUDA. */
+trk_status trk_batch_create(trk_session* const* sessions, int32_t n_sessions, trk_batch** out);
+
+/* One frame of every member: member k reads its depth image from the device buffer d_depths[k] (host
+ * array of n_sessions device pointers, row-major float32 metres, 0 = invalid).  Enqueued on cuda_stream
+ * (NULL = legacy default stream); results stay in each session's device state: trk_read_result(member)
+ * reads them in stream order.  The depth buffers must stay valid until the stream reaches the frame. */
+trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, void* cuda_stream);
+
+/* Waits for the batch's outstanding work and releases its device tables and graph. */
+void trk_batch_destroy(trk_batch* b);
+
 /* The same contraction on the tensor cores (Eqs. JTJ, JTr): out = R^T R for the FP32 rows R as in
  * trk_jtj_rows, with precision TRK_PRECISION_BF16X3 or TRK_PRECISION_TF32X3.  Each CTA accumulates
  * 64-row chunks in tensor memory (FP32) and drains them every 512 rows into Kahan-compensated FP32 sums;

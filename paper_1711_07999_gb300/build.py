@@ -2,7 +2,8 @@
 
 Translation units compile in parallel; the shared library links the CUDA runtime statically.  Host code
 is compiled without floating-point contraction so that the neighbourhood search gives the same ties on
-every host architecture.
+every host architecture; device code without implicit multiply-add contraction, so that a session
+computes bit for bit the same through its own launches and through a batch's.
 """
 from __future__ import annotations
 
@@ -15,9 +16,11 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libtrk.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["kernels_geom.cu", "kernels_solve.cu", "kernels_jtj.cu", "kernels_tc.cu", "trk_api.cu", "server.cu"]
+SOURCES = ["kernels_geom.cu", "kernels_solve.cu", "kernels_jtj.cu", "kernels_tc.cu", "trk_api.cu", "server.cu", "batch.cu"]
 DEPS = ["trk_internal.cuh", "tcgen05.cuh", os.path.join(ROOT, "include", "trk.h")]
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
+# -fmad=false: no implicit multiply-add contraction in device code (the FMAs the kernels want are written
+# as fmaf), so a stage body inlined into different kernels rounds identically everywhere.
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo", "-fmad=false",
               "-Xcompiler", "-fPIC,-ffp-contract=off", "-diag-suppress", "177"]
 
 

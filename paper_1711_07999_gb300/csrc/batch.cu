@@ -1,0 +1,249 @@
+// batch.cu -- many tracking sessions stepped together (the batch calls of trk.h).
+//
+// Every stage of a frame (skinning, z-buffer, visibility, association, [J r]^T [J r], the LM solve and
+// acceptance, the shape step) runs as ONE kernel launch over the blocks of all sessions: a per-stage
+// table maps each block to (session, block position in that session's grid), and the block reads its
+// session's descriptor from a device array.  A frame of the whole batch is one CUDA graph of the same
+// ~90 launches a single session needs, however many sessions there are, and the sessions' blocks share
+// each launch's waves (small sessions fill the gaps of large ones).  Each session computes exactly what
+// it computes alone: blocks of different sessions touch disjoint buffers, and every per-session
+// reduction keeps its fixed order.
+#include <algorithm>
+#include <vector>
+
+#include "../../include/trk.h"
+#include "trk_internal.cuh"
+
+namespace trk {
+const Dev& session_dev(const trk_session* s);
+const trk_params& session_params(const trk_session* s);
+int session_device(const trk_session* s);
+void session_set_last_stream(trk_session* s, cudaStream_t st);
+}  // namespace trk
+
+using namespace trk;
+
+namespace {
+
+// kJtj1..kJtj5: the [J r] blocks of the sessions with tile width class ceil(NP / 16) = 1..5
+enum Kind { kSkin, kTris, kVerts, kAssoc, kJtj1, kJtj2, kJtj3, kJtj4, kJtj5, kReduce, kLm, kKinds };
+constexpr int kSrcSlots = 4;
+constexpr int kMaxBatch = 4096;  // the tail's prefix kernel scans up to 1024 x 4 sessions
+
+struct Table {
+  int4* d_map = nullptr;
+  int n = 0;
+};
+
+}  // namespace
+
+struct trk_batch {
+  std::vector<trk_session*> sessions;
+  int device = 0;
+  int pose_iters = 0, shape_iters = 0, shape_sweeps = 0, precision = 0;
+  int max_links = 0, max_np = 0;
+  int assoc_blocks = 608;     // persistent association blocks
+  int tail_blocks = 304;      // association-tail blocks (shared by all sessions' queues)
+  Dev* d_devs = nullptr;
+  unsigned* d_ctl = nullptr;  // [0] occupied tiles of the frame, [1] association tile counter, [2] tail counter
+  unsigned* d_prefix = nullptr;  // [n + 1] queued pixels before each session
+  int4* d_tiles = nullptr;    // occupied 16 x 16 tiles of the frame (session, x, y, tiles per row)
+  Table tables[kKinds];
+  const float** d_srcs = nullptr;  // device copy of the per-session depth pointers of the current frame
+  const float** h_srcs = nullptr;  // pinned, kSrcSlots slots of one pointer per session
+  cudaEvent_t src_ev[4] = {};      // the copy out of each slot has been done
+  int src_slot = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+BatchGrid grid_of(const trk_batch* b, Kind k) { return BatchGrid{b->d_devs, b->tables[k].d_map}; }
+
+// Blocks of session s in the launches of kind k.
+void blocks_of(const Dev& d, Kind k, int& gx, int& gy) {
+  const int npx = d.cam.W * d.cam.H;
+  gy = 1;
+  switch (k) {
+    case kSkin: gx = std::max((d.V + 255) / 256, (npx + 2047) / 2048); break;  // also clears the pixel buffers
+    case kTris: gx = (d.F + 255) / 256; break;
+    case kVerts: gx = d.nblk_v; break;
+    case kAssoc: gx = (d.cam.W + 15) / 16; gy = (d.cam.H + 15) / 16; break;
+    case kJtj1: case kJtj2: case kJtj3: case kJtj4: case kJtj5:
+      gx = (d.NP + 15) / 16 == k - kJtj1 + 1 ? d.nblk_jtj : 0;
+      break;
+    case kReduce: gx = (d.NP * d.NP + 31) / 32; break;
+    default: gx = kCandidates; break;  // kLm
+  }
+}
+
+void enqueue_batch_frame(trk_batch* b, cudaStream_t st) {
+  const int B = (int)b->sessions.size();
+  const int P = b->pose_iters, S = b->shape_iters;
+  const int L = b->max_links;
+  cudaMemsetAsync(b->d_ctl, 0, sizeof(unsigned) * 3, st);
+  launch_gather_depth_b(grid_of(b, kAssoc), b->tables[kAssoc].n, b->d_srcs, b->d_tiles, b->d_ctl, st);
+  int cur = 0;
+  auto geometry = [&]() {
+    launch_skin_b(grid_of(b, kSkin), b->tables[kSkin].n, L, cur, b->d_ctl, st);
+    launch_raster_b(grid_of(b, kTris), b->tables[kTris].n, st);
+    launch_visibility_b(grid_of(b, kVerts), b->tables[kVerts].n, st);
+    launch_associate_b(b->d_devs, B, b->d_tiles, b->d_ctl, b->d_prefix, b->assoc_blocks, b->tail_blocks, st);
+  };
+  for (int it = 0; it < P; ++it) {
+    geometry();
+    BatchGrid gj[5];
+    int nj[5];
+    for (int t = 0; t < 5; ++t) {
+      gj[t] = grid_of(b, (Kind)(kJtj1 + t));
+      nj[t] = b->tables[kJtj1 + t].n;
+    }
+    launch_normal_equations_b(gj, nj, grid_of(b, kReduce), b->tables[kReduce].n, L, b->precision, cur, it, st);
+    launch_lm_b(grid_of(b, kLm), b->tables[kLm].n, grid_of(b, kVerts), b->tables[kVerts].n, L, cur, st);
+  }
+  for (int it = 0; it < S; ++it) {
+    geometry();
+    cur = launch_shape_b(grid_of(b, kVerts), b->tables[kVerts].n, L, b->shape_sweeps, cur, P + it, st);
+  }
+  if (cur != 0)
+    for (trk_session* s : b->sessions) {
+      const Dev& d = session_dev(s);
+      cudaMemcpyAsync(d.phi[0], d.phi[cur], sizeof(float4) * d.V, cudaMemcpyDeviceToDevice, st);
+    }
+}
+
+void free_batch(trk_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (Table& t : b->tables) cudaFree(t.d_map);
+  cudaFree(b->d_devs);
+  cudaFree(b->d_ctl);
+  cudaFree(b->d_prefix);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_srcs);
+  for (cudaEvent_t e : b->src_ev)
+    if (e) {
+      cudaEventSynchronize(e);
+      cudaEventDestroy(e);
+    }
+  cudaFreeHost(b->h_srcs);
+  delete b;
+}
+
+#define BCK(call)                                                                 \
+  do {                                                                            \
+    const cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                      \
+      free_batch(b);                                                              \
+      return set_error(e_ == cudaErrorMemoryAllocation ? TRK_ERR_OOM : TRK_ERR_CUDA, \
+                       cudaGetErrorString(e_));                                   \
+    }                                                                             \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+trk_status trk_batch_create(trk_session* const* sessions, int32_t n_sessions, trk_batch** out) {
+  if (!sessions || n_sessions < 1 || n_sessions > kMaxBatch || !out)
+    return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: bad arguments (1 <= n_sessions <= 4096)");
+  trk_batch* b = new trk_batch();
+  const trk_params& p0 = session_params(sessions[0]);
+  b->device = session_device(sessions[0]);
+  b->pose_iters = p0.pose_iters;
+  b->shape_iters = p0.shape_iters;
+  b->shape_sweeps = p0.shape_sweeps;
+  b->precision = p0.precision;
+  for (int k = 0; k < n_sessions; ++k) {
+    trk_session* s = sessions[k];
+    if (!s) {
+      free_batch(b);
+      return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: NULL session");
+    }
+    for (int j = 0; j < k; ++j)
+      if (sessions[j] == s) {
+        free_batch(b);
+        return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: a session appears twice");
+      }
+    const trk_params& p = session_params(s);
+    if (session_device(s) != b->device || p.pose_iters != b->pose_iters || p.shape_iters != b->shape_iters ||
+        p.shape_sweeps != b->shape_sweeps || p.precision != b->precision) {
+      free_batch(b);
+      return set_error(TRK_ERR_INVALID_ARG,
+                       "trk_batch_create: sessions differ in device, iteration schedule or precision");
+    }
+    const Dev& d = session_dev(s);
+    b->max_links = std::max(b->max_links, d.L);
+    b->max_np = std::max(b->max_np, d.NP);
+    b->sessions.push_back(s);
+  }
+  int cur_dev = 0;
+  cudaGetDevice(&cur_dev);
+  if (cur_dev != b->device) {
+    free_batch(b);
+    return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: the sessions' device is not the current device");
+  }
+  ensure_configured();
+  std::vector<Dev> devs;
+  for (trk_session* s : b->sessions) devs.push_back(session_dev(s));
+  BCK(cudaMalloc(&b->d_devs, sizeof(Dev) * devs.size()));
+  BCK(cudaMemcpy(b->d_devs, devs.data(), sizeof(Dev) * devs.size(), cudaMemcpyHostToDevice));
+  for (int k = 0; k < kKinds; ++k) {
+    std::vector<int4> map;
+    for (int s = 0; s < (int)devs.size(); ++s) {
+      int gx = 0, gy = 0;
+      blocks_of(devs[s], (Kind)k, gx, gy);
+      for (int y = 0; y < gy; ++y)
+        for (int x = 0; x < gx; ++x) map.push_back(make_int4(s, x, y, gx));
+    }
+    b->tables[k].n = (int)map.size();
+    if (!map.empty()) {
+      BCK(cudaMalloc(&b->tables[k].d_map, sizeof(int4) * map.size()));
+      BCK(cudaMemcpy(b->tables[k].d_map, map.data(), sizeof(int4) * map.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  BCK(cudaMalloc(&b->d_ctl, sizeof(unsigned) * 3));
+  BCK(cudaMalloc(&b->d_prefix, sizeof(unsigned) * (n_sessions + 1)));
+  BCK(cudaMalloc(&b->d_tiles, sizeof(int4) * std::max(b->tables[kAssoc].n, 1)));
+  BCK(cudaMalloc(&b->d_srcs, sizeof(float*) * devs.size()));
+  BCK(cudaMallocHost(&b->h_srcs, sizeof(float*) * devs.size() * kSrcSlots));
+  for (cudaEvent_t& e : b->src_ev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  BCK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  enqueue_batch_frame(b, b->cap);
+  BCK(cudaStreamEndCapture(b->cap, &g));
+  const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  BCK(e);
+  *out = b;
+  return TRK_OK;
+}
+
+trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, void* cuda_stream) {
+  if (!b || !d_depths) return set_error(TRK_ERR_INVALID_ARG, "trk_batch_track_device: NULL argument");
+  const int B = (int)b->sessions.size();
+  for (int k = 0; k < B; ++k)
+    if (!d_depths[k]) return set_error(TRK_ERR_INVALID_ARG, "trk_batch_track_device: NULL depth pointer");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // a ring of pinned pointer slots: a slot is rewritten only after the copy out of it has run
+  const int slot = b->src_slot;
+  b->src_slot = (slot + 1) % kSrcSlots;
+  const float** h = b->h_srcs + (size_t)slot * B;
+  cudaError_t e = cudaEventSynchronize(b->src_ev[slot]);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < B; ++k) h[k] = d_depths[k];
+    e = cudaMemcpyAsync(b->d_srcs, h, sizeof(float*) * B, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->src_ev[slot], st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, st);
+  if (e != cudaSuccess) return set_error(TRK_ERR_CUDA, cudaGetErrorString(e));
+  for (trk_session* s : b->sessions) session_set_last_stream(s, st);
+  return TRK_OK;
+}
+
+void trk_batch_destroy(trk_batch* b) { free_batch(b); }
+
+}  // extern "C"

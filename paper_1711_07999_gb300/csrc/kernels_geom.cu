@@ -32,16 +32,17 @@ void launch_fk(const Dev& d, cudaStream_t st) { k_fk<<<1, 128, 0, st>>>(d); }
 // Eqs. H_Sigma, deformation: v_i = H_iSigma (v0_i + phi_i).  Also clears the per-pixel and
 // per-vertex accumulators of this iteration (z-buffer, bucket heads, association sums).
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_skin(Dev d, int phi_buf) {
+__device__ __forceinline__ void skin_impl(const Dev& d, BlockPos bp, int phi_buf) {
   extern __shared__ DQ sHd[];
   for (int j = threadIdx.x; j < d.L; j += blockDim.x) sHd[j] = d.Hd[j];
   __syncthreads();
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int stride = gridDim.x * blockDim.x;
+  const int tid = bp.x * blockDim.x + threadIdx.x;
+  const int stride = bp.gx * blockDim.x;
   const int npx = d.cam.W * d.cam.H;
   for (int k = tid; k < npx; k += stride) {
     d.zbuf[k] = ~0ull;
     d.head[k] = -1;
+    d.corr[k] = -1;
   }
   for (int k = tid; k < d.V; k += stride) d.acc[k] = Acc4{0, 0, 0, 0};
   if (tid == 0) {
@@ -60,11 +61,22 @@ __global__ void __launch_bounds__(kBlock) k_skin(Dev d, int phi_buf) {
   }
 }
 
+// ctl (batches only): the first block resets the association's tile and tail counters of this iteration.
+__global__ void __launch_bounds__(kBlock) k_skin(BatchGrid g, Dev d0, int phi_buf, unsigned* ctl) {
+  if (g.map == nullptr) {
+    skin_impl(d0, grid_pos(), phi_buf);
+    return;
+  }
+  __shared__ Dev sd;
+  if (ctl && blockIdx.x == 0 && threadIdx.x < 2) ctl[1 + threadIdx.x] = 0;  // tile and tail counters
+  skin_impl(sd, batch_block(g, sd), phi_buf);
+}
+
 static int grid_for(int n, int block) { return (n + block - 1) / block; }
 
 void launch_skin(const Dev& d, int phi_buf, cudaStream_t st) {
   const int g = max(grid_for(d.V, kBlock), 152);
-  k_skin<<<g, kBlock, d.L * sizeof(DQ), st>>>(d, phi_buf);
+  k_skin<<<g, kBlock, d.L * sizeof(DQ), st>>>(kSingle, d, phi_buf, nullptr);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -72,8 +84,8 @@ void launch_skin(const Dev& d, int phi_buf, cudaStream_t st) {
 // both windings, depth from the ray-plane intersection, min-reduced as (float bits << 32) | id.
 // Also writes the unnormalised face normal (b - a) x (c - a) used by the vertex normals.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_raster(Dev d) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void raster_impl(const Dev& d, BlockPos bp) {
+  const int f = bp.x * blockDim.x + threadIdx.x;
   if (f >= d.F) return;
   const int4 t = d.tris[f];
   const Cam c = d.cam;
@@ -116,8 +128,17 @@ __global__ void __launch_bounds__(kBlock) k_raster(Dev d) {
   }
 }
 
+__global__ void __launch_bounds__(kBlock) k_raster(BatchGrid g, Dev d0) {
+  if (g.map == nullptr) {
+    raster_impl(d0, grid_pos());
+    return;
+  }
+  __shared__ Dev sd;
+  raster_impl(sd, batch_block(g, sd));
+}
+
 void launch_raster(const Dev& d, cudaStream_t st) {
-  if (d.F > 0) k_raster<<<grid_for(d.F, kBlock), kBlock, 0, st>>>(d);
+  if (d.F > 0) k_raster<<<grid_for(d.F, kBlock), kBlock, 0, st>>>(kSingle, d);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -125,8 +146,8 @@ void launch_raster(const Dev& d, cudaStream_t st) {
 // rounded pixel inside the image, not behind the z-buffer by more than eps_vis), and insertion of
 // each visible vertex into its pixel's bucket (a singly linked list: head[pixel] -> rec[i].w).
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) k_visibility(Dev d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void visibility_impl(const Dev& d, BlockPos bp) {
+  const int i = bp.x * blockDim.x + threadIdx.x;
   if (i >= d.V) return;
   float3 s = make_float3(0.f, 0.f, 0.f);
   const int e = d.csr_off[i + 1];
@@ -164,8 +185,17 @@ __global__ void __launch_bounds__(kBlock) k_visibility(Dev d) {
   d.vispix[i] = vp;
 }
 
+__global__ void __launch_bounds__(kBlock) k_visibility(BatchGrid g, Dev d0) {
+  if (g.map == nullptr) {
+    visibility_impl(d0, grid_pos());
+    return;
+  }
+  __shared__ Dev sd;
+  visibility_impl(sd, batch_block(g, sd));
+}
+
 void launch_visibility(const Dev& d, cudaStream_t st) {
-  k_visibility<<<grid_for(d.V, kBlock), kBlock, 0, st>>>(d);
+  k_visibility<<<grid_for(d.V, kBlock), kBlock, 0, st>>>(kSingle, d);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -255,11 +285,11 @@ __device__ __forceinline__ float3 back_project(const Cam& c, int px, int py, flo
                      (float)((double)dep - (double)c.oz));
 }
 
-__global__ void __launch_bounds__(kBlock) k_associate(Dev d) {
+__device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
   const Cam c = d.cam;
   const int lane = threadIdx.x & 31;
-  const int px = blockIdx.x * 16 + (threadIdx.x & 15);
-  const int py = blockIdx.y * 16 + (threadIdx.x >> 4);
+  const int px = bp.x * 16 + (threadIdx.x & 15);
+  const int py = bp.y * 16 + (threadIdx.x >> 4);
   const bool inimg = px < c.W && py < c.H;
   const int k = py * c.W + px;
   const float dep = inimg ? d.depth[k] : 0.f;
@@ -300,12 +330,81 @@ __global__ void __launch_bounds__(kBlock) k_associate(Dev d) {
   if (lane == 0 && m) atomicAdd(&d.stats[0], __popc(m));
 }
 
+
 constexpr int kTailWarps = 8;
 
-__global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
+// The rings beyond the thread-owned ones for queue entry `item` of session d, by one warp (the lanes
+// split each ring's buckets; (d^2, index) keys combined by a warp-min).  Returns, in every lane, whether
+// the pixel got a correspondence (lane 0 writes it and adds the pixel's sums).
+__device__ __forceinline__ bool tail_item(const Dev& d, unsigned item) {
   const Cam c = d.cam;
   const int lane = threadIdx.x & 31;
   const float tau2 = c.tau * c.tau;
+  const int4 e = d.queue[item];
+  const int k = e.x, px = k % c.W, py = k / c.W;
+  const float dep = d.depth[k];
+  const float3 p = back_project(c, px, py, dep);
+  unsigned long long key = key_of(e.y, __int_as_float(e.z));
+  int wb = -1;
+  float wd2 = 0.f;
+  for (int r = kRingsPerThread + 1; r <= c.R; ++r) {
+    for (int t0 = 0; t0 < 8 * r; t0 += 32) {
+      const int q[1] = {t0 + lane < 8 * r ? ring_bucket(px, py, r, t0 + lane, c.W, c.H) : -1};
+      scan_group<1>(d, q, p, tau2, wb, wd2);
+    }
+    unsigned long long kk = key_of(wb, wd2);
+    kk = kk < key ? kk : key;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, kk, o);
+      kk = other < kk ? other : kk;
+    }
+    key = kk;
+    const float lb = dep * ((float)r + 0.499f) * c.kappa;
+    if (lb > c.tau || (key != ~0ull && lb * lb > __uint_as_float((unsigned)(key >> 32)))) break;
+  }
+  const int best = key == ~0ull ? -1 : (int)(unsigned)(key & 0xffffffffu);
+  if (lane == 0) {
+    d.corr[k] = best;
+    if (best >= 0) commit_pixel(d, best, p);
+  }
+  return best >= 0;
+}
+
+// One session: one 16 x 16 tile per block.  A batch: persistent blocks take the frame's occupied tiles
+// (listed by the depth gather) from a shared counter, reloading the session descriptor when the session
+// changes; pixels of empty tiles keep the "no correspondence" the skinning pass wrote.
+__global__ void __launch_bounds__(kBlock) k_associate(const Dev* devs, const int4* tiles, unsigned* ctl, Dev d0) {
+  if (devs == nullptr) {
+    associate_impl(d0, grid_pos());
+    return;
+  }
+  __shared__ Dev sd;
+  __shared__ int4 s_t;
+  int cur = -1;
+  const unsigned n = ctl[0];
+  for (;;) {
+    __syncthreads();  // the previous tile is done (s_t, sd free)
+    if (threadIdx.x == 0) {
+      const unsigned i = atomicAdd(&ctl[1], 1u);
+      s_t = i < n ? tiles[i] : make_int4(-1, 0, 0, 0);
+    }
+    __syncthreads();
+    const int4 t = s_t;
+    if (t.x < 0) break;
+    if (t.x != cur) {
+      const int* src = reinterpret_cast<const int*>(devs + t.x);
+      for (int q = threadIdx.x; q < (int)(sizeof(Dev) / 4); q += blockDim.x) reinterpret_cast<int*>(&sd)[q] = src[q];
+      cur = t.x;
+      __syncthreads();
+    }
+    associate_impl(sd, BlockPos{t.y, t.z, t.w});
+  }
+}
+
+// One session: the warps of all blocks take its queue entries from the session's counter.
+__global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
+  const int lane = threadIdx.x & 31;
   const unsigned n = *(volatile unsigned*)&d.qctl[0];
   int done = 0;
   for (;;) {
@@ -313,45 +412,101 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
     if (lane == 0) item = atomicAdd(&d.qctl[1], 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= n) break;
-    const int4 e = d.queue[item];
-    const int k = e.x, px = k % c.W, py = k / c.W;
-    const float dep = d.depth[k];
-    const float3 p = back_project(c, px, py, dep);
-    unsigned long long key = key_of(e.y, __int_as_float(e.z));
-    int wb = -1;
-    float wd2 = 0.f;
-    for (int r = kRingsPerThread + 1; r <= c.R; ++r) {
-      for (int t0 = 0; t0 < 8 * r; t0 += 32) {
-        const int q[1] = {t0 + lane < 8 * r ? ring_bucket(px, py, r, t0 + lane, c.W, c.H) : -1};
-        scan_group<1>(d, q, p, tau2, wb, wd2);
-      }
-      unsigned long long kk = key_of(wb, wd2);
-      kk = kk < key ? kk : key;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, kk, o);
-        kk = other < kk ? other : kk;
-      }
-      key = kk;
-      const float lb = dep * ((float)r + 0.499f) * c.kappa;
-      if (lb > c.tau || (key != ~0ull && lb * lb > __uint_as_float((unsigned)(key >> 32)))) break;
-    }
-    const int best = key == ~0ull ? -1 : (int)(unsigned)(key & 0xffffffffu);
-    if (lane == 0) {
-      d.corr[k] = best;
-      if (best >= 0) {
-        commit_pixel(d, best, p);
-        ++done;
-      }
-    }
+    done += tail_item(d, item);
   }
   if (lane == 0 && done) atomicAdd(&d.stats[0], done);
 }
 
+// A batch: prefix[s] = queued pixels of the sessions before s (one block; at most 1024 x 4 sessions).
+__global__ void __launch_bounds__(1024) k_tail_prefix(const Dev* devs, int n_sessions, unsigned* prefix) {
+  __shared__ unsigned part[1024];
+  const int t = threadIdx.x;
+  unsigned v[4], sum = 0;
+  for (int u = 0; u < 4; ++u) {
+    const int s = 4 * t + u;
+    v[u] = s < n_sessions ? *(volatile unsigned*)&devs[s].qctl[0] : 0u;
+    sum += v[u];
+  }
+  part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the per-thread sums
+    const unsigned x = t >= o ? part[t - o] : 0u;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  unsigned run = part[t] - sum;
+  for (int u = 0; u < 4; ++u) {
+    const int s = 4 * t + u;
+    if (s < n_sessions) prefix[s] = run;
+    run += v[u];
+  }
+  if (t == 1023) prefix[n_sessions] = part[t];
+}
+
+// A batch: the warps take entries of the concatenated queues of all sessions from one counter; an
+// entry's session is found in the prefix and its descriptor read through the cache.
+__global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const Dev* devs, int n_sessions,
+                                                                          const unsigned* prefix, unsigned* ctl) {
+  const int lane = threadIdx.x & 31;
+  const unsigned total = prefix[n_sessions];
+  for (;;) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(&ctl[2], 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    int lo = 0, hi = n_sessions - 1;  // the last session whose prefix is <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const Dev& d = devs[lo];
+    if (tail_item(d, item - prefix[lo]) && lane == 0) atomicAdd(&d.stats[0], 1);
+  }
+}
+
 void launch_associate(const Dev& d, cudaStream_t st) {
   dim3 g((d.cam.W + 15) / 16, (d.cam.H + 15) / 16);
-  k_associate<<<g, kBlock, 0, st>>>(d);
+  k_associate<<<g, kBlock, 0, st>>>(nullptr, nullptr, nullptr, d);
   k_associate_tail<<<2 * 152, 32 * kTailWarps, 0, st>>>(d);
+}
+
+// ---- batched launches (one launch over the blocks of all sessions of a batch) ---------------------
+void launch_skin_b(const BatchGrid& g, int nblk, int max_links, int phi_buf, unsigned* ctl, cudaStream_t st) {
+  if (nblk > 0) k_skin<<<nblk, kBlock, max_links * sizeof(DQ), st>>>(g, Dev{}, phi_buf, ctl);
+}
+void launch_raster_b(const BatchGrid& g, int nblk, cudaStream_t st) {
+  if (nblk > 0) k_raster<<<nblk, kBlock, 0, st>>>(g, Dev{});
+}
+void launch_visibility_b(const BatchGrid& g, int nblk, cudaStream_t st) {
+  if (nblk > 0) k_visibility<<<nblk, kBlock, 0, st>>>(g, Dev{});
+}
+void launch_associate_b(const Dev* devs, int n_sessions, const int4* tiles, unsigned* ctl, unsigned* prefix,
+                        int assoc_blocks, int tail_blocks, cudaStream_t st) {
+  k_associate<<<assoc_blocks, kBlock, 0, st>>>(devs, tiles, ctl, Dev{});
+  k_tail_prefix<<<1, 1024, 0, st>>>(devs, n_sessions, prefix);
+  k_associate_tail_batch<<<tail_blocks, 32 * kTailWarps, 0, st>>>(devs, n_sessions, prefix, ctl);
+}
+
+// Copies each session's depth frame from srcs[session] into the session's own depth buffer, one 16 x 16
+// tile per block (the association's tiling), and lists the tiles that hold a valid depth.
+__global__ void __launch_bounds__(kBlock) k_gather_depth_b(BatchGrid g, const float* const* srcs, int4* tiles,
+                                                           unsigned* ctl) {
+  const int4 m = g.map[blockIdx.x];
+  const Dev& d = g.devs[m.x];
+  const int px = m.y * 16 + (threadIdx.x & 15), py = m.z * 16 + (threadIdx.x >> 4);
+  bool valid = false;
+  if (px < d.cam.W && py < d.cam.H) {
+    const int k = py * d.cam.W + px;
+    const float z = srcs[m.x][k];
+    const_cast<float*>(d.depth)[k] = z;
+    valid = z > 0.f;
+  }
+  if (__syncthreads_or(valid) && threadIdx.x == 0) tiles[atomicAdd(&ctl[0], 1u)] = m;
+}
+void launch_gather_depth_b(const BatchGrid& g, int nblk, const float* const* srcs, int4* tiles, unsigned* ctl,
+                           cudaStream_t st) {
+  if (nblk > 0) k_gather_depth_b<<<nblk, kBlock, 0, st>>>(g, srcs, tiles, ctl);
 }
 
 __global__ void k_depth_from_zbuf(Dev d, float* out) {

@@ -49,24 +49,26 @@ __device__ __forceinline__ void load_link_tables(const Dev& d, DQ* sHd, float* s
   }
 }
 
-// Writes the [J r] rows of this block's vertices of A, compacted in vertex order, to Js (row stride ROW,
-// columns [0, width) with width >= NP, zero beyond NP) and returns their number.  Sets r2 to this
-// thread's r_i^2 (0 outside A).  Contains a __syncthreads that also publishes the link tables; the
-// caller synchronises again before reading Js.
-__device__ __forceinline__ int jacobian_rows(const Dev& d, int phi_buf, float* Js, int ROW, int width,
-                                             const DQ* sHd, const float* sXi, const int* sPar, int* s_warp,
-                                             float& r2) {
+// This block's vertices in A (c_i >= 1 and a valid normal) and each one's row slot, compacted in vertex
+// order.  Contains a __syncthreads; returns the number of rows (the same in every thread).
+struct RowSlot {
+  int i, slot;
+  bool inA;
+  Acc4 a4;
+  float4 nn;
+};
+__device__ __forceinline__ int block_rows(const Dev& d, int blk, int* s_warp, RowSlot& rs) {
   const int tid = threadIdx.x;
-  const int i = blockIdx.x * kBlock + tid;
-  bool inA = false;
-  Acc4 a4 = Acc4{0, 0, 0, 0};
-  float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (i < d.V) {
-    a4 = d.acc[i];
-    nn = d.n[i];
-    inA = a4.w >= 1 && nn.w > 0.f;
+  rs.i = blk * kBlock + tid;
+  rs.inA = false;
+  rs.a4 = Acc4{0, 0, 0, 0};
+  rs.nn = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (rs.i < d.V) {
+    rs.a4 = d.acc[rs.i];
+    rs.nn = d.n[rs.i];
+    rs.inA = rs.a4.w >= 1 && rs.nn.w > 0.f;
   }
-  const unsigned m = __ballot_sync(0xffffffffu, inA);
+  const unsigned m = __ballot_sync(0xffffffffu, rs.inA);
   const int lane = tid & 31, w = tid >> 5;
   if (lane == 0) s_warp[w] = __popc(m);
   __syncthreads();
@@ -75,47 +77,56 @@ __device__ __forceinline__ int jacobian_rows(const Dev& d, int phi_buf, float* J
     off += k < w ? s_warp[k] : 0;
     total += s_warp[k];
   }
-  r2 = 0.f;
-  if (inA) {
-    float* row = Js + (off + __popc(m & ((1u << lane) - 1u))) * ROW;
-    for (int k = 0; k < width; ++k) row[k] = 0.f;
-    const float inv = 1.f / ((float)a4.w * kFix);
-    const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
-    const float3 n = f3(nn);
-    const float r = dot3(n, pm);
-    row[d.L] = r;
-    r2 = r * r;
-    float sg[4];
-    const uchar4 bi = d.bidx[i];
-    const float4 bw = d.bw[i];
-    const DQ H = blend_bones(sHd, bi, bw, sg);
-    const float4 x0 = d.v0[i], ph = d.phi[phi_buf][i], v = d.v[i];
-    const float4 X = make_float4(0.f, x0.x + ph.x, x0.y + ph.y, x0.z + ph.z);
-    const float4 Np = make_float4(0.f, n.x, n.y, n.z);
-    const float invN = 1.f / qdot(H.r, H.r);
-    const float4 Na = qmul(Np, H.r);
-    const float4 cr = qscale(qadd(qadd(qmul(Na, X), qmul(Np, H.d)), qscale(H.r, dot3(n, f3(v)))), -2.f * invN);
-    const float4 cd = qscale(Na, 2.f * invN);
-    const int idx[4] = {bi.x, bi.y, bi.z, bi.w};
-    const float ws[4] = {bw.x, bw.y, bw.z, bw.w};
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      if (!(ws[s] > 0.f)) continue;
-      const DQ h = sHd[idx[s]];
-      const float sc = ws[s] * sg[s];
-      const float3 e1 = Lfun(cr, h.r), e2 = Lfun(cd, h.d), e3 = Lfun(cd, h.r);
-      const float e[6] = {sc * (e1.x + e2.x), sc * (e1.y + e2.y), sc * (e1.z + e2.z), sc * e3.x, sc * e3.y, sc * e3.z};
-      for (int k = idx[s]; k >= 0; k = sPar[k]) {
-        const float* xk = sXi + 6 * k;
-        row[k] -= xk[0] * e[0] + xk[1] * e[1] + xk[2] * e[2] + xk[3] * e[3] + xk[4] * e[4] + xk[5] * e[5];
-      }
-    }
-  }
+  rs.slot = off + __popc(m & ((1u << lane) - 1u));
   return total;
 }
 
+// Writes this thread's [J r] row (if its vertex is in A) to Js row rs.slot (stride ROW, columns
+// [0, width) with width >= NP, zero beyond NP) and sets r2 = r_i^2 (0 outside A).  The link tables must
+// be in shared memory; the caller synchronises before reading Js.
+__device__ __forceinline__ void jacobian_row(const Dev& d, const RowSlot& rs, int phi_buf, float* Js, int ROW,
+                                             int width, const DQ* sHd, const float* sXi, const int* sPar, float& r2) {
+  r2 = 0.f;
+  if (!rs.inA) return;
+  const int i = rs.i;
+  const Acc4 a4 = rs.a4;
+  float* row = Js + rs.slot * ROW;
+  for (int k = 0; k < width; ++k) row[k] = 0.f;
+  const float inv = 1.f / ((float)a4.w * kFix);
+  const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
+  const float3 n = f3(rs.nn);
+  const float r = dot3(n, pm);
+  row[d.L] = r;
+  r2 = r * r;
+  float sg[4];
+  const uchar4 bi = d.bidx[i];
+  const float4 bw = d.bw[i];
+  const DQ H = blend_bones(sHd, bi, bw, sg);
+  const float4 x0 = d.v0[i], ph = d.phi[phi_buf][i], v = d.v[i];
+  const float4 X = make_float4(0.f, x0.x + ph.x, x0.y + ph.y, x0.z + ph.z);
+  const float4 Np = make_float4(0.f, n.x, n.y, n.z);
+  const float invN = 1.f / qdot(H.r, H.r);
+  const float4 Na = qmul(Np, H.r);
+  const float4 cr = qscale(qadd(qadd(qmul(Na, X), qmul(Np, H.d)), qscale(H.r, dot3(n, f3(v)))), -2.f * invN);
+  const float4 cd = qscale(Na, 2.f * invN);
+  const int idx[4] = {bi.x, bi.y, bi.z, bi.w};
+  const float ws[4] = {bw.x, bw.y, bw.z, bw.w};
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (!(ws[s] > 0.f)) continue;
+    const DQ h = sHd[idx[s]];
+    const float sc = ws[s] * sg[s];
+    const float3 e1 = Lfun(cr, h.r), e2 = Lfun(cd, h.d), e3 = Lfun(cd, h.r);
+    const float e[6] = {sc * (e1.x + e2.x), sc * (e1.y + e2.y), sc * (e1.z + e2.z), sc * e3.x, sc * e3.y, sc * e3.z};
+    for (int k = idx[s]; k >= 0; k = sPar[k]) {
+      const float* xk = sXi + 6 * k;
+      row[k] -= xk[0] * e[0] + xk[1] * e[1] + xk[2] * e[2] + xk[3] * e[3] + xk[4] * e[4] + xk[5] * e[5];
+    }
+  }
+}
+
 template <int T>
-__global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
+__device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int phi_buf) {
   constexpr int ROW = 16 * T + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Js = reinterpret_cast<float*>(smem_raw);
@@ -124,9 +135,16 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
   int* sPar = reinterpret_cast<int*>(sXi + 6 * d.L);
   __shared__ int s_warp[kBlock / 32];
   const int tid = threadIdx.x;
+  RowSlot rs;
+  const int total = block_rows(d, bp.x, s_warp, rs);
+  if (total == 0) {  // nothing to add: the reduction skips this block's (unwritten) partial
+    if (tid == 0) d.jtj_rows[bp.x] = 0;
+    return;
+  }
   load_link_tables(d, sHd, sXi, sPar);
+  __syncthreads();
   float r2;
-  const int total = jacobian_rows(d, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, s_warp, r2);
+  jacobian_row(d, rs, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, r2);
   __syncthreads();
   const int ty = tid >> 4, tx = tid & 15;
   float acc[T][T];
@@ -148,7 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
       for (int b = 0; b < T; ++b) acc[a][b] = fmaf(ra[a], rb[b], acc[a][b]);
   }
   const int NP = d.NP;
-  float* out = d.partial + (size_t)blockIdx.x * NP * NP;
+  float* out = d.partial + (size_t)bp.x * NP * NP;
 #pragma unroll
   for (int a = 0; a < T; ++a)
 #pragma unroll
@@ -156,7 +174,20 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
       const int r = ty * T + a, c = tx * T + b;
       if (r < NP && c < NP) out[r * NP + c] = acc[a][b];
     }
-  if (tid == 0 && total) atomicAdd(&d.stats[1], total);
+  if (tid == 0) {
+    d.jtj_rows[bp.x] = total;
+    atomicAdd(&d.stats[1], total);
+  }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kBlock) k_resid_jtj(BatchGrid g, Dev d0, int phi_buf) {
+  if (g.map == nullptr) {
+    resid_jtj_impl<T>(d0, grid_pos(), phi_buf);
+    return;
+  }
+  __shared__ Dev sd;
+  resid_jtj_impl<T>(sd, batch_block(g, sd), phi_buf);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -169,7 +200,7 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj(Dev d, int phi_buf) {
 // blocks per SM; their 2 x 128 TMEM columns fit the 512 of an SM, so tcgen05.alloc never waits.
 // ---------------------------------------------------------------------------------------------
 template <int PREC, int NB>
-__global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(Dev d, int phi_buf) {
+__device__ __forceinline__ void resid_jtj_tc_impl(const Dev& d, BlockPos bp, int phi_buf) {
   using TL = tc::Tile<PREC, 8>;
   constexpr int N = 16 * NB, ROW = N + 1, T = TL::T;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -184,7 +215,12 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(Dev d, int phi_buf) {
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int NP = d.NP;
-
+  RowSlot rs;
+  const int total = block_rows(d, bp.x, s_warp, rs);
+  if (total == 0) {  // nothing to add: no TMEM is taken and the reduction skips this block
+    if (tid == 0) d.jtj_rows[bp.x] = 0;
+    return;
+  }
   tc::zero_padding<PREC, TL::CH, kBlock>(tiles, 2, NP);
   if (tid == 0) {
     tc::mbar_init(&bar, 1);
@@ -192,8 +228,9 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(Dev d, int phi_buf) {
   }
   if (w == 0) tc::tmem_alloc(&tslot, tc::kTmemCols);
   load_link_tables(d, sHd, sXi, sPar);
+  __syncthreads();
   float r2;
-  const int total = jacobian_rows(d, phi_buf, Js, ROW, NP, sHd, sXi, sPar, s_warp, r2);
+  jacobian_row(d, rs, phi_buf, Js, ROW, NP, sHd, sXi, sPar, r2);
   for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
   if (lane == 0) s_e[w] = r2;
   tc::fence_before_sync();
@@ -229,7 +266,7 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(Dev d, int phi_buf) {
   float E = 0.f;
   for (int k = 0; k < kBlock / 32; ++k) E += s_e[k];
   // warps w and w + 4 read the same 32 TMEM lanes (parameters a), alternate 8-column groups (b)
-  float* out = d.partial + (size_t)blockIdx.x * NP * NP;
+  float* out = d.partial + (size_t)bp.x * NP * NP;
   const int a = 32 * (w & 3) + lane;
   const float bad = __int_as_float(0x7fc00000);
   for (int g = w >> 2; g < N / 8; g += 2) {
@@ -254,7 +291,20 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(Dev d, int phi_buf) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, tc::kTmemCols);
   }
-  if (tid == 0 && total) atomicAdd(&d.stats[1], total);
+  if (tid == 0) {
+    d.jtj_rows[bp.x] = total;
+    atomicAdd(&d.stats[1], total);
+  }
+}
+
+template <int PREC, int NB>
+__global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(BatchGrid g, Dev d0, int phi_buf) {
+  if (g.map == nullptr) {
+    resid_jtj_tc_impl<PREC, NB>(d0, grid_pos(), phi_buf);
+    return;
+  }
+  __shared__ Dev sd;
+  resid_jtj_tc_impl<PREC, NB>(sd, batch_block(g, sd), phi_buf);
 }
 
 // Fixed-order FP64 sum of the block partials -> [J r]^T [J r]; the last entry gives E_pose (with the
@@ -263,14 +313,33 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(Dev d, int phi_buf) {
 // adds the 32 warp sums in order.
 constexpr int kReduceThreads = 1024;
 
-__global__ void __launch_bounds__(kReduceThreads) k_reduce_jtj(Dev d, int slot) {
+__device__ __forceinline__ void reduce_jtj_impl(const Dev& d, BlockPos bp, int slot) {
   __shared__ double sm[kReduceThreads / 32][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int NP = d.NP, n2 = NP * NP;
-  const int e = blockIdx.x * 32 + lane;
-  double s = 0.0;
-  if (e < n2)
-    for (int b = w; b < d.nblk_jtj; b += kReduceThreads / 32) s += (double)d.partial[(size_t)b * n2 + e];
+  const int e = bp.x * 32 + lane;
+  // warp w takes blocks w, w + 32, ... (four at a time, loads in flight together); blocks that added no
+  // rows wrote no partial and count as zero
+  constexpr int S = kReduceThreads / 32;
+  const int nb = d.nblk_jtj;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (e < n2) {
+    int b = w;
+    for (; b + 3 * S < nb; b += 4 * S) {
+      const int r0 = d.jtj_rows[b], r1 = d.jtj_rows[b + S], r2 = d.jtj_rows[b + 2 * S], r3 = d.jtj_rows[b + 3 * S];
+      const float p0 = r0 > 0 ? d.partial[(size_t)b * n2 + e] : 0.f;
+      const float p1 = r1 > 0 ? d.partial[(size_t)(b + S) * n2 + e] : 0.f;
+      const float p2 = r2 > 0 ? d.partial[(size_t)(b + 2 * S) * n2 + e] : 0.f;
+      const float p3 = r3 > 0 ? d.partial[(size_t)(b + 3 * S) * n2 + e] : 0.f;
+      s0 += (double)p0;
+      s1 += (double)p1;
+      s2 += (double)p2;
+      s3 += (double)p3;
+    }
+    for (; b < nb; b += S)
+      if (d.jtj_rows[b] > 0) s0 += (double)d.partial[(size_t)b * n2 + e];
+  }
+  const double s = (s0 + s1) + (s2 + s3);
   sm[w][lane] = s;
   __syncthreads();
   if (w != 0 || e >= n2) return;
@@ -283,6 +352,15 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_jtj(Dev d, int slot) 
     if (slot >= 0) d.energy[slot] = E;
     d.lm_trials[6] = E;
   }
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_jtj(BatchGrid g, Dev d0, int slot) {
+  if (g.map == nullptr) {
+    reduce_jtj_impl(d0, grid_pos(), slot);
+    return;
+  }
+  __shared__ Dev sd;
+  reduce_jtj_impl(sd, batch_block(g, sd), slot);
 }
 
 static int jtj_smem_bytes(int T, int L) {
@@ -300,11 +378,11 @@ static void launch_resid_jtj_tc(const Dev& d, int phi_buf, cudaStream_t st) {
   const int g = d.nblk_jtj;
   const int sm = jtj_tc_smem_bytes<PREC>(NB, d.L);
   switch (NB) {
-    case 1: k_resid_jtj_tc<PREC, 1><<<g, kBlock, sm, st>>>(d, phi_buf); break;
-    case 2: k_resid_jtj_tc<PREC, 2><<<g, kBlock, sm, st>>>(d, phi_buf); break;
-    case 3: k_resid_jtj_tc<PREC, 3><<<g, kBlock, sm, st>>>(d, phi_buf); break;
-    case 4: k_resid_jtj_tc<PREC, 4><<<g, kBlock, sm, st>>>(d, phi_buf); break;
-    default: k_resid_jtj_tc<PREC, 5><<<g, kBlock, sm, st>>>(d, phi_buf); break;
+    case 1: k_resid_jtj_tc<PREC, 1><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
+    case 2: k_resid_jtj_tc<PREC, 2><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
+    case 3: k_resid_jtj_tc<PREC, 3><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
+    case 4: k_resid_jtj_tc<PREC, 4><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
+    default: k_resid_jtj_tc<PREC, 5><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
   }
 }
 
@@ -324,17 +402,17 @@ void launch_resid_jtj(const Dev& d, int phi_buf, cudaStream_t st) {
   const int g = d.nblk_jtj;
   const int sm = jtj_smem_bytes(T, d.L);
   switch (T) {
-    case 1: k_resid_jtj<1><<<g, kBlock, sm, st>>>(d, phi_buf); break;
-    case 2: k_resid_jtj<2><<<g, kBlock, sm, st>>>(d, phi_buf); break;
-    case 3: k_resid_jtj<3><<<g, kBlock, sm, st>>>(d, phi_buf); break;
-    case 4: k_resid_jtj<4><<<g, kBlock, sm, st>>>(d, phi_buf); break;
-    default: k_resid_jtj<5><<<g, kBlock, sm, st>>>(d, phi_buf); break;
+    case 1: k_resid_jtj<1><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
+    case 2: k_resid_jtj<2><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
+    case 3: k_resid_jtj<3><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
+    case 4: k_resid_jtj<4><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
+    default: k_resid_jtj<5><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
   }
 }
 
 void launch_reduce_jtj(const Dev& d, int slot, cudaStream_t st) {
   const int n2 = d.NP * d.NP;
-  k_reduce_jtj<<<(n2 + 31) / 32, kReduceThreads, 0, st>>>(d, slot);
+  k_reduce_jtj<<<(n2 + 31) / 32, kReduceThreads, 0, st>>>(kSingle, d, slot);
 }
 
 void launch_normal_equations(const Dev& d, int phi_buf, int slot, cudaStream_t st) {
@@ -528,11 +606,11 @@ __device__ void solve_blocked(float (*F)[kMaxPad + 1], const float* ivd, float* 
   }
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_lm_solve(Dev d) {
+__device__ __forceinline__ void lm_solve_impl(const Dev& d, BlockPos bp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float F[kMaxPad][kMaxPad + 1];  // FP32 scaled system -> its Cholesky factor
   __shared__ float ivd[kMaxPad], ys[kMaxPad], sc[kMaxPad];
-  const int P = d.L, NP = d.NP, c = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int P = d.L, NP = d.NP, c = bp.x, tid = threadIdx.x, nt = blockDim.x;
   const int Pp = (P + kBlk - 1) / kBlk * kBlk;
   double* M = reinterpret_cast<double*>(smem_raw);  // [P][P] FP64 system for the residuals
   double* x = M + P * P;
@@ -630,27 +708,43 @@ __global__ void __launch_bounds__(kSolveThreads) k_lm_solve(Dev d) {
   fk_all(*lt, thc, H0, d.Hd_c + (size_t)c * P, d.xi_c + (size_t)c * P * 8, 8);
 }
 
+__global__ void __launch_bounds__(kSolveThreads) k_lm_solve(BatchGrid g, Dev d0) {
+  if (g.map == nullptr) {
+    lm_solve_impl(d0, grid_pos());
+    return;
+  }
+  __shared__ Dev sd;
+  lm_solve_impl(sd, batch_block(g, sd));
+}
+
 // Energy of each candidate at the fixed association (normals and p~ held), then the accept step:
 // the first candidate with E_c <= E wins (lambda <- lambda_c / 10); if none, Theta stays and
 // lambda <- min(lambda_5 * 10, 1e7).  The last block to finish does the selection.
-__global__ void __launch_bounds__(kBlock) k_lm_eval(Dev d, int phi_buf) {
+__device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_buf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DQ* sH = reinterpret_cast<DQ*>(smem_raw);  // [kCandidates][L]
   __shared__ int sok[kCandidates];
   __shared__ double swarp[kBlock / 32][kCandidates];
   __shared__ bool last;
   const int L = d.L, tid = threadIdx.x;
-  for (int t = tid; t < kCandidates * L; t += kBlock) sH[t] = d.Hd_c[t];
+  const int i = bp.x * kBlock + tid;
+  Acc4 a4 = Acc4{0, 0, 0, 0};
+  float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i < d.V) {
+    a4 = d.acc[i];
+    nn = d.n[i];
+  }
+  const bool inA = i < d.V && a4.w >= 1 && nn.w > 0.f;
   if (tid < kCandidates) sok[tid] = d.lm_ok[tid];
-  __syncthreads();
+  if (__syncthreads_or(inA)) {  // the candidates' tables are needed only where a vertex of A is
+    for (int t = tid; t < kCandidates * L; t += kBlock) sH[t] = d.Hd_c[t];
+    __syncthreads();
+  }
   float e[kCandidates];
 #pragma unroll
   for (int c = 0; c < kCandidates; ++c) e[c] = 0.f;
-  const int i = blockIdx.x * kBlock + tid;
-  if (i < d.V) {
-    const Acc4 a4 = d.acc[i];
-    const float4 nn = d.n[i];
-    if (a4.w >= 1 && nn.w > 0.f) {
+  {
+    if (inA) {
       const float inv = 1.f / ((float)a4.w * kFix);
       const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
       const float4 v = d.v[i], x0 = d.v0[i], ph = d.phi[phi_buf][i];
@@ -677,11 +771,11 @@ __global__ void __launch_bounds__(kBlock) k_lm_eval(Dev d, int phi_buf) {
   if (tid < kCandidates) {
     double s = 0.0;
     for (int w = 0; w < kBlock / 32; ++w) s += swarp[w][tid];
-    d.epart[(size_t)blockIdx.x * 8 + tid] = s;
+    d.epart[(size_t)bp.x * 8 + tid] = s;
   }
   __threadfence();
   __syncthreads();
-  if (tid == 0) last = atomicAdd(&d.counter[0], 1u) == gridDim.x - 1;
+  if (tid == 0) last = atomicAdd(&d.counter[0], 1u) == (unsigned)bp.gx - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -689,7 +783,7 @@ __global__ void __launch_bounds__(kBlock) k_lm_eval(Dev d, int phi_buf) {
   __shared__ double Ec[kCandidates];
   {
     double s6[kCandidates] = {0, 0, 0, 0, 0, 0};
-    for (int b = tid; b < (int)gridDim.x; b += kBlock)
+    for (int b = tid; b < bp.gx; b += kBlock)
       for (int c = 0; c < kCandidates; ++c) s6[c] += __ldcg(d.epart + (size_t)b * 8 + c);
     for (int c = 0; c < kCandidates; ++c) red[tid][c] = s6[c];
   }
@@ -737,17 +831,26 @@ __global__ void __launch_bounds__(kBlock) k_lm_eval(Dev d, int phi_buf) {
   }
 }
 
+__global__ void __launch_bounds__(kBlock) k_lm_eval(BatchGrid g, Dev d0, int phi_buf) {
+  if (g.map == nullptr) {
+    lm_eval_impl(d0, grid_pos(), phi_buf);
+    return;
+  }
+  __shared__ Dev sd;
+  lm_eval_impl(sd, batch_block(g, sd), phi_buf);
+}
+
 static int lm_solve_smem(int L) {
   return (int)(((((size_t)L * L + 4 * L) * 8 + 15) & ~(size_t)15) + ((sizeof(LinkTable) + 15) & ~(size_t)15) +
                (size_t)L * sizeof(DQ));
 }
 
 void launch_lm_solve(const Dev& d, cudaStream_t st) {
-  k_lm_solve<<<kCandidates, kSolveThreads, lm_solve_smem(d.L), st>>>(d);
+  k_lm_solve<<<kCandidates, kSolveThreads, lm_solve_smem(d.L), st>>>(kSingle, d);
 }
 
 void launch_lm_eval(const Dev& d, int phi_buf, cudaStream_t st) {
-  k_lm_eval<<<d.nblk_v, kBlock, kCandidates * d.L * sizeof(DQ), st>>>(d, phi_buf);
+  k_lm_eval<<<d.nblk_v, kBlock, kCandidates * d.L * sizeof(DQ), st>>>(kSingle, d, phi_buf);
 }
 
 void launch_lm(const Dev& d, int phi_buf, cudaStream_t st) {
@@ -775,7 +878,7 @@ __device__ __forceinline__ float3 solve3_damped(float3 g, float cdiag, float lw,
                      (c02 * rhs.x + c12 * rhs.y + c22 * rhs.z) * id);
 }
 
-__device__ __forceinline__ void block_energy_to_slot(Dev& d, float e, int slot, int ticket) {
+__device__ __forceinline__ void block_energy_to_slot(const Dev& d, BlockPos bp, float e, int slot, int ticket) {
   __shared__ double sw[kBlock];
   __shared__ bool last;
   for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -784,15 +887,15 @@ __device__ __forceinline__ void block_energy_to_slot(Dev& d, float e, int slot, 
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kBlock / 32; ++w) s += sw[w];
-    d.epart[(size_t)blockIdx.x * 8] = s;
+    d.epart[(size_t)bp.x * 8] = s;
     __threadfence();
-    last = atomicAdd(&d.counter[ticket], 1u) == gridDim.x - 1;
+    last = atomicAdd(&d.counter[ticket], 1u) == (unsigned)bp.gx - 1;
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double s = 0.0;  // fixed order: strided per thread, then a tree over the threads
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += kBlock) s += __ldcg(d.epart + (size_t)b * 8);
+  for (int b = threadIdx.x; b < bp.gx; b += kBlock) s += __ldcg(d.epart + (size_t)b * 8);
   sw[threadIdx.x] = s;
   __syncthreads();
   for (int h = kBlock / 2; h > 0; h >>= 1) {
@@ -805,12 +908,16 @@ __device__ __forceinline__ void block_energy_to_slot(Dev& d, float e, int slot, 
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_shape(Dev d, int src, int slot) {
+__device__ __forceinline__ void shape_impl(const Dev& d, BlockPos bp, int src, int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DQ* sHd = reinterpret_cast<DQ*>(smem_raw);
-  for (int j = threadIdx.x; j < d.L; j += kBlock) sHd[j] = d.Hd[j];
-  __syncthreads();
-  const int i = blockIdx.x * kBlock + threadIdx.x;
+  const int i = bp.x * kBlock + threadIdx.x;
+  bool anyA = false;
+  if (i < d.V) anyA = d.acc[i].w >= 1 && d.n[i].w > 0.f;
+  if (__syncthreads_or(anyA)) {  // the pose tables are needed only where a vertex of A is
+    for (int j = threadIdx.x; j < d.L; j += kBlock) sHd[j] = d.Hd[j];
+    __syncthreads();
+  }
   float e = 0.f;
   int inA_count = 0;
   if (i < d.V) {
@@ -856,12 +963,21 @@ __global__ void __launch_bounds__(kBlock) k_shape(Dev d, int src, int slot) {
   }
   const unsigned m = __ballot_sync(0xffffffffu, inA_count != 0);
   if ((threadIdx.x & 31) == 0 && m) atomicAdd(&d.stats[1], __popc(m));
-  block_energy_to_slot(d, e, slot, 1);
+  block_energy_to_slot(d, bp, e, slot, 1);
+}
+
+__global__ void __launch_bounds__(kBlock) k_shape(BatchGrid g, Dev d0, int src, int slot) {
+  if (g.map == nullptr) {
+    shape_impl(d0, grid_pos(), src, slot);
+    return;
+  }
+  __shared__ Dev sd;
+  shape_impl(sd, batch_block(g, sd), src, slot);
 }
 
 // Further Jacobi sweeps: r_i is updated linearly, r_i = r0_i + g_i . (phi_i - phi0_i).
-__global__ void __launch_bounds__(kBlock) k_shape_sweep(Dev d, int src) {
-  const int i = blockIdx.x * kBlock + threadIdx.x;
+__device__ __forceinline__ void shape_sweep_impl(const Dev& d, BlockPos bp, int src) {
+  const int i = bp.x * kBlock + threadIdx.x;
   if (i >= d.V) return;
   const float4* phi = d.phi[src];
   const float3 pi = f3(phi[i]);
@@ -886,21 +1002,92 @@ __global__ void __launch_bounds__(kBlock) k_shape_sweep(Dev d, int src) {
   d.phi[1 - src][i] = make_float4(pi.x + dl.x, pi.y + dl.y, pi.z + dl.z, 0.f);
 }
 
+__global__ void __launch_bounds__(kBlock) k_shape_sweep(BatchGrid g, Dev d0, int src) {
+  if (g.map == nullptr) {
+    shape_sweep_impl(d0, grid_pos(), src);
+    return;
+  }
+  __shared__ Dev sd;
+  shape_sweep_impl(sd, batch_block(g, sd), src);
+}
+
 // Returns the buffer that holds Phi after the step.
 int launch_shape(const Dev& d, int phi_src, int slot, cudaStream_t st) {
-  k_shape<<<d.nblk_v, kBlock, d.L * sizeof(DQ), st>>>(d, phi_src, slot);
+  k_shape<<<d.nblk_v, kBlock, d.L * sizeof(DQ), st>>>(kSingle, d, phi_src, slot);
   int cur = 1 - phi_src;
   for (int s = 1; s < d.shape_sweeps; ++s) {
-    k_shape_sweep<<<d.nblk_v, kBlock, 0, st>>>(d, cur);
+    k_shape_sweep<<<d.nblk_v, kBlock, 0, st>>>(kSingle, d, cur);
     cur = 1 - cur;
   }
   return cur;
+}
+
+// ---- batched launches ------------------------------------------------------------------------
+template <int PREC>
+static void launch_resid_jtj_tc_b(const BatchGrid& g, int nblk, int max_np, int max_links, int phi_buf,
+                                  cudaStream_t st) {
+  const int NB = (max_np + 15) / 16;
+  const int sm = jtj_tc_smem_bytes<PREC>(NB, max_links);
+  switch (NB) {
+    case 1: k_resid_jtj_tc<PREC, 1><<<nblk, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+    case 2: k_resid_jtj_tc<PREC, 2><<<nblk, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+    case 3: k_resid_jtj_tc<PREC, 3><<<nblk, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+    case 4: k_resid_jtj_tc<PREC, 4><<<nblk, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+    default: k_resid_jtj_tc<PREC, 5><<<nblk, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+  }
+}
+
+// gj[t - 1], nj[t - 1]: the blocks of the sessions whose [J r] tile width class is t = ceil(NP / 16)
+// (one launch per class, so a small skeleton does not pay for the largest one's tiles).
+void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGrid& gr, int nr, int max_links,
+                               int precision, int phi_buf, int slot, cudaStream_t st) {
+  for (int T = 1; T <= 5; ++T) {
+    const BatchGrid& g = gj[T - 1];
+    const int n = nj[T - 1];
+    if (n == 0) continue;
+    if (precision == 1) {
+      launch_resid_jtj_tc_b<1>(g, n, 16 * T, max_links, phi_buf, st);
+    } else if (precision == 2) {
+      launch_resid_jtj_tc_b<2>(g, n, 16 * T, max_links, phi_buf, st);
+    } else {
+      const int sm = jtj_smem_bytes(T, max_links);
+      switch (T) {
+        case 1: k_resid_jtj<1><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+        case 2: k_resid_jtj<2><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+        case 3: k_resid_jtj<3><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+        case 4: k_resid_jtj<4><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+        default: k_resid_jtj<5><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+      }
+    }
+  }
+  if (nr > 0) k_reduce_jtj<<<nr, kReduceThreads, 0, st>>>(gr, Dev{}, slot);
+}
+
+void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int max_links, int phi_buf,
+                 cudaStream_t st) {
+  if (nlm > 0) k_lm_solve<<<nlm, kSolveThreads, lm_solve_smem(max_links), st>>>(glm, Dev{});
+  if (nv > 0) k_lm_eval<<<nv, kBlock, kCandidates * max_links * sizeof(DQ), st>>>(gv, Dev{}, phi_buf);
+}
+
+int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int phi_src, int slot, cudaStream_t st) {
+  if (nv > 0) k_shape<<<nv, kBlock, max_links * sizeof(DQ), st>>>(gv, Dev{}, phi_src, slot);
+  int cur = 1 - phi_src;
+  for (int s = 1; s < sweeps; ++s) {
+    if (nv > 0) k_shape_sweep<<<nv, kBlock, 0, st>>>(gv, Dev{}, cur);
+    cur = 1 - cur;
+  }
+  return cur;
+}
+
+static void configure_batched() {
+  cudaFuncSetAttribute(k_lm_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, lm_solve_smem(kMaxLinks));
 }
 
 void configure_tc_kernels();
 
 void configure_kernels() {
   configure_tc_kernels();
+  configure_batched();
   configure_resid_jtj_tc<1>();
   configure_resid_jtj_tc<2>();
   cudaFuncSetAttribute(k_resid_jtj<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, jtj_smem_bytes(1, kMaxLinks));

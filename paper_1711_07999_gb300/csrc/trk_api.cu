@@ -275,6 +275,9 @@ trk_status sync_check(trk_session* s) {
 // ---- helpers of the frame server (server.cu) --------------------------------------------------
 namespace trk {
 size_t session_device_bytes(const trk_session* s) { return s->device_bytes; }
+const Dev& session_dev(const trk_session* s) { return s->d; }
+const trk_params& session_params(const trk_session* s) { return s->prm; }
+void session_set_last_stream(trk_session* s, cudaStream_t st) { s->last_stream = st; }
 int session_device(const trk_session* s) { return s->device; }
 void session_result_sizes(const trk_session* s, int* n_links, int* n_verts, int* n_energy) {
   *n_links = s->d.L;
@@ -456,6 +459,7 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   TRY(dalloc(s, &ddepth, npx));
   TRY(dalloc(s, &s->d_render, npx));
   TRY(dalloc(s, &d.partial, (size_t)d.nblk_jtj * NP * NP));
+  TRY(dalloc(s, &d.jtj_rows, (size_t)d.nblk_jtj));
   TRY(dalloc(s, &d.A, (size_t)NP * NP));
   TRY(dalloc(s, &d.epart, (size_t)std::max(d.nblk_v, 1) * 8));
   TRY(dalloc(s, &d.counter, 4));

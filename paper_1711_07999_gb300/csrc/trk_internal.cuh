@@ -284,6 +284,7 @@ struct Dev {
   const float* depth;
   // reductions
   float* partial;   // [nblk_jtj][NP*NP]
+  int* jtj_rows;    // [nblk_jtj] rows of [J r] each block contributed (0: its partial is not written)
   int nblk_jtj;
   double* A;        // [NP*NP]
   double* epart;    // [nblk_v][8]
@@ -292,5 +293,52 @@ struct Dev {
   int* stats;             // [0] associated pixels, [1] associated vertices, [3] tensor-core wait ran out
   int precision;          // TRK_PRECISION_*: arithmetic of [J r]^T [J r]
 };
+
+}  // namespace trk
+
+namespace trk {
+
+struct BatchGrid;
+// Batched launches: one launch runs a stage for every session of a batch (block tables built by the batch).
+void launch_skin_b(const BatchGrid& g, int nblk, int max_links, int phi_buf, unsigned* ctl, cudaStream_t st);
+void launch_raster_b(const BatchGrid& g, int nblk, cudaStream_t st);
+void launch_visibility_b(const BatchGrid& g, int nblk, cudaStream_t st);
+void launch_associate_b(const Dev* devs, int n_sessions, const int4* tiles, unsigned* ctl, unsigned* prefix,
+                        int assoc_blocks, int tail_blocks, cudaStream_t st);
+void launch_gather_depth_b(const BatchGrid& g, int nblk, const float* const* srcs, int4* tiles, unsigned* ctl,
+                           cudaStream_t st);
+void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGrid& gr, int nr, int max_links,
+                               int precision, int phi_buf, int slot, cudaStream_t st);
+void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int max_links, int phi_buf,
+                 cudaStream_t st);
+int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int phi_src, int slot, cudaStream_t st);
+
+// Position of a block within its session's grid.  The single-session kernels take it from blockIdx and
+// gridDim; the batched kernels (one launch over the blocks of many sessions) from a per-launch table.
+struct BlockPos {
+  int x, y, gx;
+};
+__device__ __forceinline__ BlockPos grid_pos() { return BlockPos{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x}; }
+
+// A batched launch: block b works for session map[b].x at position (map[b].y, map[b].z) of a grid of
+// map[b].w blocks along x.
+struct BatchGrid {
+  const Dev* devs;
+  const int4* map;
+};
+
+// Every stage kernel serves one session (g.map == nullptr: the descriptor is the kernel parameter and the
+// block's position its blockIdx) and batches (descriptor and position from the tables, the descriptor
+// staged in shared memory).  The device code is compiled without implicit multiply-add contraction, so
+// the two inlined copies of a stage body round identically: a session computes bit for bit the same
+// alone and in a batch.
+__device__ __forceinline__ BlockPos batch_block(const BatchGrid& g, Dev& sd) {
+  const int4 m = g.map[blockIdx.x];
+  const int* src = reinterpret_cast<const int*>(g.devs + m.x);
+  for (int t = threadIdx.x; t < (int)(sizeof(Dev) / 4); t += blockDim.x) reinterpret_cast<int*>(&sd)[t] = src[t];
+  __syncthreads();
+  return BlockPos{m.y, m.z, m.w};
+}
+constexpr BatchGrid kSingle{nullptr, nullptr};
 
 }  // namespace trk

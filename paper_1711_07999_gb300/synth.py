@@ -126,6 +126,38 @@ def small_tree_bones(rng) -> list:
     return b
 
 
+def random_tree_bones(rng, n_bones: int, max_dof: int = 72) -> list:
+    """n_bones capsules in a random tree: a 6-DoF root, then bones hung from the end of a random earlier
+    bone (chains at most 5 deep) in a direction turned up to 60 degrees from the parent's, mostly in
+    the image plane; each joint a ball (3 DoF), 2-DoF or hinge, with the total held to max_dof;
+    radius U[2,6] cm, length U[6,18] cm."""
+    w = rng.uniform(0.10, 0.20)
+    b = [_bone("root", -1, (0, 0, 0), (-w / 2, 0, 0), (w / 2, 0, 0), rng.uniform(0.04, 0.07), ROOT_DOFS)]
+    ends, dirs, depth = [np.zeros(3)], [np.array([0.0, -1.0, 0.0])], [0]
+    budget = max_dof - 6
+    for k in range(1, n_bones):
+        cand = [i for i in range(len(b)) if depth[i] < 5]
+        pa = int(rng.choice(cand))
+        ang = rng.uniform(-math.pi / 3, math.pi / 3)
+        d0 = dirs[pa] if pa > 0 else np.array([math.cos(rng.uniform(0, 2 * math.pi)), math.sin(rng.uniform(0, 2 * math.pi)), 0.0])
+        c, s_ = math.cos(ang), math.sin(ang)
+        d = np.array([c * d0[0] - s_ * d0[1], s_ * d0[0] + c * d0[1], rng.uniform(-0.2, 0.2)])
+        d /= np.linalg.norm(d)
+        length = rng.uniform(0.06, 0.18)
+        piv = ends[pa]
+        left = n_bones - 1 - k  # bones still to place after this one need at least one DoF each
+        r = rng.random()
+        nd = 3 if r < 0.4 else (2 if r < 0.7 else 1)
+        nd = max(1, min(nd, budget - left))
+        dofs = BALL if nd == 3 else ([("h", X), ("h", Z)] if nd == 2 else [("h", Z)])
+        budget -= nd
+        b.append(_bone(f"b{k}", pa, piv, piv, piv + d * length, rng.uniform(0.02, 0.06), dofs))
+        ends.append(piv + d * length)
+        dirs.append(d)
+        depth.append(depth[pa] + 1)
+    return b
+
+
 def build_skeleton(bones: list, root_pos) -> tuple:
     """Links: one per DoF.  The first link of a bone carries the fixed offset H_{P(j),j} (a pure
     translation from the parent bone's pivot); the others have identity offsets.  The bone's capsule
@@ -270,12 +302,24 @@ CONFIGS = {
     2: dict(width=640, height=480, fx=525.0, fy=525.0, cx=320.0, cy=240.0, V=50000, root_z=3.0, body="humanoid"),
     3: dict(width=1280, height=720, fx=920.0, fy=920.0, cx=640.0, cy=360.0, V=200000, root_z=3.0, body="humanoid"),
 }
+# the uneven batch: per session, |V| ~ U[5k, 200k], bones ~ U{12..40} (DoF <= 72), one of three images
+BATCH_IMAGES = [dict(width=320, height=240, fx=262.5, fy=262.5, cx=160.0, cy=120.0),
+                dict(width=640, height=480, fx=525.0, fy=525.0, cx=320.0, cy=240.0),
+                dict(width=1280, height=720, fx=920.0, fy=920.0, cx=640.0, cy=360.0)]
+
+
+def batch_session_config(session: int) -> dict:
+    """Size class of session `session` of the uneven batch (seeded per session)."""
+    rng = np.random.default_rng(seed_for(4, session))
+    c = dict(BATCH_IMAGES[int(rng.integers(0, 3))])
+    c.update(V=int(rng.integers(5000, 200001)), bones=int(rng.integers(12, 41)), root_z=3.0, body="random")
+    return c
 
 
 def make_model(config: int = 1, session: int = 0, V: int | None = None, width: int | None = None,
                height: int | None = None, **param_over) -> dict:
     """Template model + camera + parameters + ground-truth motion description for one session."""
-    c = dict(CONFIGS[config])
+    c = dict(CONFIGS[config]) if config != 4 else batch_session_config(session)
     if width is not None:
         s = width / c["width"]
         c.update(width=width, height=height if height is not None else int(round(c["height"] * s)),
@@ -285,7 +329,12 @@ def make_model(config: int = 1, session: int = 0, V: int | None = None, width: i
         c["V"] = V
     seed = seed_for(config, session)
     rng = np.random.default_rng(seed)
-    bones = small_tree_bones(rng) if c["body"] == "small" else humanoid_bones()
+    if c["body"] == "small":
+        bones = small_tree_bones(rng)
+    elif c["body"] == "random":
+        bones = random_tree_bones(rng, c["bones"])
+    else:
+        bones = humanoid_bones()
     root = (0.0, 0.2 if c["body"] == "small" else 0.0, c["root_z"])
     sk, link_of_bone, first_link = build_skeleton(bones, root)
     verts, tris, nrm0, bone_of = tessellate(bones, root, c["V"])

@@ -25,7 +25,8 @@ EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_dev
            "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
            "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc",
-           "trk_jtj_rows_tc", "trk_server_create", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
+           "trk_jtj_rows_tc", "trk_batch_create", "trk_batch_track_device", "trk_batch_destroy",
+           "trk_server_create", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
            "trk_server_get_stats", "trk_server_destroy"]
 
 STAGES = ["skin", "raster", "visibility", "associate", "resid_jtj", "reduce", "lm_solve", "lm_eval", "shape"]
@@ -97,6 +98,7 @@ def lib(build_if_missing: bool = True):
             "trk_read": [vp, i32, vp, sz], "trk_get_info": [vp, vp], "trk_profile_iteration": [vp, i32, sz, vp],
             "trk_jtj_rows": [vp, i32, i32, i32, vp, vp], "trk_jtj_rows_noalloc": [vp, i32, i32, i32, vp, vp],
             "trk_jtj_rows_tc": [vp, i32, i32, i32, i32, vp, vp],
+            "trk_batch_create": [C.POINTER(vp), i32, C.POINTER(vp)], "trk_batch_track_device": [vp, C.POINTER(vp), vp],
             "trk_server_create": [sz, i32, C.POINTER(vp)], "trk_server_attach": [vp, vp], "trk_server_detach": [vp, vp],
             "trk_server_submit": [vp, vp, vp, C.POINTER(C.c_uint64)], "trk_server_wait": [vp, C.c_uint64, C.c_int64, vp],
             "trk_server_get_stats": [vp, vp],
@@ -109,6 +111,8 @@ def lib(build_if_missing: bool = True):
         L.trk_destroy.restype = None
         L.trk_server_destroy.argtypes = [vp]
         L.trk_server_destroy.restype = None
+        L.trk_batch_destroy.argtypes = [vp]
+        L.trk_batch_destroy.restype = None
         L.trk_last_error.argtypes = []
         L.trk_last_error.restype = C.c_char_p
         _lib = L
@@ -260,6 +264,39 @@ class Session:
         out = np.empty(shp, dt)
         _check(lib().trk_read(self.h, FIELDS[field], _p(out), out.nbytes))
         return out
+
+
+class Batch:
+    """Sessions stepped together (trk_batch_*): one launch per stage over all members' blocks."""
+
+    def __init__(self, sessions):
+        self.sessions = list(sessions)
+        arr = (C.c_void_p * len(self.sessions))(*[x.h.value for x in self.sessions])
+        h = C.c_void_p()
+        _check(lib().trk_batch_create(arr, len(self.sessions), C.byref(h)))
+        self.h = h
+
+    def track_device(self, depth_ptrs, stream_ptr: int = 0):
+        """One frame of every member; depth_ptrs[k] is a device pointer to member k's depth image."""
+        arr = (C.c_void_p * len(self.sessions))(*depth_ptrs)
+        _check(lib().trk_batch_track_device(self.h, arr, C.c_void_p(stream_ptr or None)))
+
+    def close(self):
+        if self.h:
+            lib().trk_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
