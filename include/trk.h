@@ -290,6 +290,55 @@ trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, vo
 /* Waits for the batch's outstanding work and releases its device tables and graph. */
 void trk_batch_destroy(trk_batch* b);
 
+/* ---- schedules and the autotuner --------------------------------------------------------------------
+ * A schedule steps a set of sessions each frame as `groups` work-balanced groups on concurrent streams:
+ * a group of several sessions as one fused batch (trk_batch), a group of one as the session's own frame
+ * graph (groups = 1: one fused batch; groups = n: one graph per session).  The fused groups' association
+ * launches use assoc_blocks persistent tile blocks and tail_blocks queue-draining blocks.  Every session
+ * computes bitwise the same under every schedule.  The members follow the batch rules (same device,
+ * schedule of iterations and precision when grouped). */
+typedef struct {
+  int32_t groups;        /* 1 <= groups <= n                                     */
+  int32_t assoc_blocks;  /* >= 1 */
+  int32_t tail_blocks;   /* >= 1 */
+} trk_schedule_config;
+
+typedef struct trk_schedule trk_schedule;
+
+/* cfg: the schedule to use; NULL = the entry of cache_path for this size class (trk_schedule_signature)
+ * if there is one, else groups = 1, assoc_blocks = 608, tail_blocks = 304.  Session pointers are
+ * borrowed.  Errors: TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA. */
+trk_status trk_schedule_create(trk_session* const* sessions, int32_t n_sessions, const trk_schedule_config* cfg,
+                               const char* cache_path, trk_schedule** out);
+
+/* One frame of every session (depth of session k from the device buffer d_depths[k]), enqueued on
+ * cuda_stream; results via trk_read_result(session) in that stream's order. */
+trk_status trk_schedule_track_device(trk_schedule* s, const float* const* d_depths, void* cuda_stream);
+
+trk_status trk_schedule_get_config(const trk_schedule* s, trk_schedule_config* out);
+
+/* Times candidate schedules (groups from {1, 2, 4, ..., 32, n}, then the association block counts around
+ * the best; 1 warm-up and `reps` timed frames each, CUDA events) on the frames d_depths, keeps the
+ * fastest, optionally stores it in cache_path under this size class and returns it with its time per
+ * frame.  The timed frames are real: every session advances by (1 + reps) frames per candidate, so tune
+ * on warm-up frames.  Synchronises the device.  Errors: as trk_schedule_create; TRK_ERR_INVALID_ARG if
+ * the cache cannot be written. */
+trk_status trk_schedule_autotune(trk_schedule* s, const float* const* d_depths, int32_t reps, const char* cache_path,
+                                 trk_schedule_config* chosen, double* ms_per_step);
+
+void trk_schedule_destroy(trk_schedule* s);
+
+/* The size class a schedule is cached under: session count, precision, total vertices and pixels (two
+ * significant digits) and the largest skeleton, e.g. "n16_p0_v800000_px4900000_L55".  Host only. */
+trk_status trk_schedule_signature(trk_session* const* sessions, int32_t n_sessions, char* out, size_t out_size);
+
+/* The tuning cache, a JSON object {"<size class>": {"groups": .., "assoc_blocks": .., "tail_blocks": ..,
+ * "ms_per_step": ..}, ...}.  Host only (no device calls).  lookup: TRK_ERR_INVALID_ARG when the file or
+ * the entry is missing or malformed; store: adds or replaces the entry (written through a temporary
+ * file and a rename). */
+trk_status trk_tuning_cache_lookup(const char* path, const char* signature, trk_schedule_config* out, double* ms);
+trk_status trk_tuning_cache_store(const char* path, const char* signature, const trk_schedule_config* cfg, double ms);
+
 /* The same contraction on the tensor cores (Eqs. JTJ, JTr): out = R^T R for the FP32 rows R as in
  * trk_jtj_rows, with precision TRK_PRECISION_BF16X3 or TRK_PRECISION_TF32X3.  Each CTA accumulates
  * 64-row chunks in tensor memory (FP32) and drains them every 512 rows into Kahan-compensated FP32 sums;

@@ -144,12 +144,17 @@ void free_batch(trk_batch* b) {
 
 }  // namespace
 
-extern "C" {
+namespace trk {
 
-trk_status trk_batch_create(trk_session* const* sessions, int32_t n_sessions, trk_batch** out) {
-  if (!sessions || n_sessions < 1 || n_sessions > kMaxBatch || !out)
+// trk_batch_create with the association's launch sizes: assoc_blocks persistent tile blocks and
+// tail_blocks queue-draining blocks (the schedule's tunables).
+trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_blocks, int tail_blocks,
+                        trk_batch** out) {
+  if (!sessions || n_sessions < 1 || n_sessions > kMaxBatch || !out || assoc_blocks < 1 || tail_blocks < 1)
     return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: bad arguments (1 <= n_sessions <= 4096)");
   trk_batch* b = new trk_batch();
+  b->assoc_blocks = assoc_blocks;
+  b->tail_blocks = tail_blocks;
   const trk_params& p0 = session_params(sessions[0]);
   b->device = session_device(sessions[0]);
   b->pose_iters = p0.pose_iters;
@@ -220,6 +225,14 @@ trk_status trk_batch_create(trk_session* const* sessions, int32_t n_sessions, tr
   BCK(e);
   *out = b;
   return TRK_OK;
+}
+
+}  // namespace trk
+
+extern "C" {
+
+trk_status trk_batch_create(trk_session* const* sessions, int32_t n_sessions, trk_batch** out) {
+  return batch_create(sessions, n_sessions, 4 * 152, 2 * 152, out);
 }
 
 trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, void* cuda_stream) {

@@ -26,6 +26,8 @@ EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_dev
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
            "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc",
            "trk_jtj_rows_tc", "trk_batch_create", "trk_batch_track_device", "trk_batch_destroy",
+           "trk_schedule_create", "trk_schedule_track_device", "trk_schedule_get_config", "trk_schedule_autotune",
+           "trk_schedule_destroy", "trk_schedule_signature", "trk_tuning_cache_lookup", "trk_tuning_cache_store",
            "trk_server_create", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
            "trk_server_get_stats", "trk_server_destroy"]
 
@@ -65,6 +67,10 @@ class Info(C.Structure):
                 ("height", C.c_int32), ("kernels_per_frame", C.c_int32), ("device_bytes", C.c_size_t)]
 
 
+class ScheduleConfig(C.Structure):
+    _fields_ = [("groups", C.c_int32), ("assoc_blocks", C.c_int32), ("tail_blocks", C.c_int32)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("frames_done", C.c_uint64), ("in_flight", C.c_int32), ("sessions", C.c_int32),
                 ("hbm_used_bytes", C.c_size_t), ("latency_p50_us", C.c_double), ("latency_p99_us", C.c_double),
@@ -99,6 +105,12 @@ def lib(build_if_missing: bool = True):
             "trk_jtj_rows": [vp, i32, i32, i32, vp, vp], "trk_jtj_rows_noalloc": [vp, i32, i32, i32, vp, vp],
             "trk_jtj_rows_tc": [vp, i32, i32, i32, i32, vp, vp],
             "trk_batch_create": [C.POINTER(vp), i32, C.POINTER(vp)], "trk_batch_track_device": [vp, C.POINTER(vp), vp],
+            "trk_schedule_create": [C.POINTER(vp), i32, vp, C.c_char_p, C.POINTER(vp)],
+            "trk_schedule_track_device": [vp, C.POINTER(vp), vp], "trk_schedule_get_config": [vp, vp],
+            "trk_schedule_autotune": [vp, C.POINTER(vp), i32, C.c_char_p, vp, C.POINTER(C.c_double)],
+            "trk_schedule_signature": [C.POINTER(vp), i32, C.c_char_p, sz],
+            "trk_tuning_cache_lookup": [C.c_char_p, C.c_char_p, vp, C.POINTER(C.c_double)],
+            "trk_tuning_cache_store": [C.c_char_p, C.c_char_p, vp, C.c_double],
             "trk_server_create": [sz, i32, C.POINTER(vp)], "trk_server_attach": [vp, vp], "trk_server_detach": [vp, vp],
             "trk_server_submit": [vp, vp, vp, C.POINTER(C.c_uint64)], "trk_server_wait": [vp, C.c_uint64, C.c_int64, vp],
             "trk_server_get_stats": [vp, vp],
@@ -113,6 +125,8 @@ def lib(build_if_missing: bool = True):
         L.trk_server_destroy.restype = None
         L.trk_batch_destroy.argtypes = [vp]
         L.trk_batch_destroy.restype = None
+        L.trk_schedule_destroy.argtypes = [vp]
+        L.trk_schedule_destroy.restype = None
         L.trk_last_error.argtypes = []
         L.trk_last_error.restype = C.c_char_p
         _lib = L
@@ -284,6 +298,77 @@ class Batch:
     def close(self):
         if self.h:
             lib().trk_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _cfg_dict(c: ScheduleConfig) -> dict:
+    return {"groups": c.groups, "assoc_blocks": c.assoc_blocks, "tail_blocks": c.tail_blocks}
+
+
+def tuning_cache_lookup(path: str, signature: str):
+    """The cached schedule of a size class as (config dict, ms per frame), or None."""
+    c, ms = ScheduleConfig(), C.c_double()
+    st = lib().trk_tuning_cache_lookup(path.encode(), signature.encode(), C.byref(c), C.byref(ms))
+    return None if st != TRK_OK else (_cfg_dict(c), ms.value)
+
+
+def tuning_cache_store(path: str, signature: str, cfg: dict, ms: float):
+    _check(lib().trk_tuning_cache_store(path.encode(), signature.encode(), C.byref(ScheduleConfig(**cfg)), ms))
+
+
+class Schedule:
+    """How a set of sessions is stepped per frame (trk_schedule_*): work-balanced groups on concurrent
+    streams, each a fused batch or a session's own graph; autotune() picks the fastest and caches it."""
+
+    def __init__(self, sessions, config: dict | None = None, cache_path: str | None = None):
+        self.sessions = list(sessions)
+        arr = (C.c_void_p * len(self.sessions))(*[x.h.value for x in self.sessions])
+        cfg = C.byref(ScheduleConfig(**config)) if config else None
+        h = C.c_void_p()
+        _check(lib().trk_schedule_create(arr, len(self.sessions), cfg, cache_path.encode() if cache_path else None,
+                                         C.byref(h)))
+        self.h = h
+
+    @staticmethod
+    def signature(sessions) -> str:
+        arr = (C.c_void_p * len(sessions))(*[x.h.value for x in sessions])
+        buf = C.create_string_buffer(256)
+        _check(lib().trk_schedule_signature(arr, len(sessions), buf, 256))
+        return buf.value.decode()
+
+    def track_device(self, depth_ptrs, stream_ptr: int = 0):
+        arr = (C.c_void_p * len(self.sessions))(*depth_ptrs)
+        _check(lib().trk_schedule_track_device(self.h, arr, C.c_void_p(stream_ptr or None)))
+
+    def config(self) -> dict:
+        c = ScheduleConfig()
+        _check(lib().trk_schedule_get_config(self.h, C.byref(c)))
+        return _cfg_dict(c)
+
+    def autotune(self, depth_ptrs, reps: int = 3, cache_path: str | None = None):
+        """Times candidate schedules on real frames (the sessions advance) and keeps the fastest;
+        returns (config dict, ms per frame)."""
+        arr = (C.c_void_p * len(self.sessions))(*depth_ptrs)
+        c, ms = ScheduleConfig(), C.c_double()
+        _check(lib().trk_schedule_autotune(self.h, arr, reps, cache_path.encode() if cache_path else None,
+                                           C.byref(c), C.byref(ms)))
+        return _cfg_dict(c), ms.value
+
+    def close(self):
+        if self.h:
+            lib().trk_schedule_destroy(self.h)
             self.h = None
 
     def __enter__(self):
