@@ -17,6 +17,9 @@ Prints one JSON line (rank 0):
   precision  per [J r]^T [J r] arithmetic (fp32, bf16x3, tf32x3; the last two on the tensor cores): batched
              frames/s, the contraction stage's time and each result's error against the oracle on the
              CPU-baseline frames
+  uneven     --uneven-sessions sessions of random-tree bodies (5k-200k vertices, 12-40 bones, 320x240 to
+             1280x720): frames/s one by one, on one stream each, as one fused batch (trk_batch_*), and
+             under the schedule the autotuner picks (trk_schedule_*)
   roofline   the dominant kernel's achieved rate against the measured peak of MEASURED_PEAKS.json
   cpu_baseline  the FP64 oracle on the host, one core, a bounded sample of the same sequence
 --impl reference times the oracle itself (on host cores) on the same workload and metric.
@@ -118,33 +121,49 @@ class ClockSampler:
 # algorithmic work per launch of each stage (bytes a minimal implementation must move / flops)
 # ------------------------------------------------------------------------------------------------
 def algorithmic(stage, V, F, npx, NP, nvis, nassoc_px, nA, n_valid_px, nblk):
-    if stage == "skin":  # v0, phi, bone idx, bone w in; v out; z-buffer, bucket heads, sums cleared
-        return "hbm", V * (16 + 16 + 4 + 16 + 16 + 32) + npx * (8 + 4)
+    """Minimum bytes (or FP64 flops) a stage must move for one session: V vertices, F triangles, npx
+    pixels, NP = links + 1, nvis visible vertices, nassoc_px associated pixels, nA vertices in A,
+    n_valid_px valid depth pixels, nblk [J r] blocks that hold rows."""
+    if stage == "skin":  # v0, phi, bone idx, bone w in; v out; sums cleared; z-buffer, heads, corr cleared
+        return "hbm", V * (16 + 16 + 4 + 16 + 16 + 32) + npx * (8 + 4 + 4)
     if stage == "raster":  # triangles, posed vertices, face normals out, covered z-buffer words
         return "hbm", F * (16 + 16) + V * 16 + n_valid_px * 8
     if stage == "visibility":  # CSR, face normals, v, normals out, z-buffer probes, bucket records
         return "hbm", V * (4 + 16 + 16 + 4) + 3 * F * 4 + F * 16 + nvis * (8 + 4 + 16)
     if stage == "associate":  # depth in, corr out, bucket heads, visible records, per-vertex sums
-        return "hbm", npx * (4 + 4 + 4) + nvis * 16 + nassoc_px * 32
-    if stage == "resid_jtj":  # per-vertex streams in, block partials out
-        return "hbm", V * (32 + 16 + 4 + 16 + 16 + 16 + 16) + nblk * NP * NP * 4
+        return "hbm", n_valid_px * (4 + 4 + 4) + nvis * 16 + nassoc_px * 32
+    if stage == "resid_jtj":  # sums and normals of every vertex; streams of A; partials of blocks with rows
+        return "hbm", V * (32 + 16) + nA * (4 + 16 + 16 + 16 + 16) + nblk * NP * NP * 4
     if stage == "reduce":
         return "hbm", nblk * NP * NP * 4 + NP * NP * 8
-    if stage == "lm_eval":
-        return "hbm", V * (32 + 16 + 16 + 16 + 16 + 4 + 16)
-    if stage == "shape":
-        return "hbm", V * (16 * 4 + 32 + 16 + 4 + 16 + 16 + 16 + 16)
+    if stage == "lm_eval":  # sums and normals of every vertex; the streams of A for six candidates
+        return "hbm", V * (32 + 16) + nA * (16 + 16 + 16 + 4 + 16)
+    if stage == "shape":  # phi, neighbours, sums, normals in; phi, r/g, phi0 out; bones of A
+        return "hbm", V * (16 + 16 + 32 + 16 + 16 + 16 + 16) + nA * (4 + 16)
     if stage == "lm_solve":  # 6 FP64 Cholesky factorisations + solves of the P x P system
         P = NP - 1
         return "fp64", 6 * (P ** 3 / 3.0 + 2 * P * P)
     return None, 0
 
 
+def session_counts(sess, depth):
+    """The per-session counts the byte model needs, read back at the session's current state."""
+    info = sess.info()
+    acc = sess.read("ACC")
+    NP = info["n_links"] + 1
+    nA = int((acc[:, 3] > 0).sum())
+    blocks = (np.nonzero(acc[:, 3] > 0)[0] // 256)
+    return dict(V=info["n_verts"], F=info["n_tris"], npx=info["width"] * info["height"], NP=NP,
+                nvis=int((sess.read("VISPIX") >= 0).sum()), nassoc_px=int(acc[:, 3].sum()), nA=nA,
+                n_valid_px=int((np.asarray(depth) > 0).sum()), nblk=int(len(np.unique(blocks))))
+
+
 def kernel_source_hash():
+    """Hash of the device-kernel sources (the host runtime files do not change a kernel's traffic)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1711_07999_gb300", "csrc")
     for n in sorted(os.listdir(csrc)):
-        if n.endswith((".cu", ".cuh")):
+        if n.startswith("kernels_") and n.endswith(".cu") or n.endswith(".cuh"):
             with open(os.path.join(csrc, n), "rb") as f:
                 h.update(f.read())
     return h.hexdigest()[:16]
@@ -438,6 +457,90 @@ def run_serving(sessions, host_frames, n_seq, duration_s, fps, seed):
                                                       "max": st["latency_max_us"] / 1000}}
 
 
+def run_uneven(args, rank, flush):
+    """The uneven batch: --uneven-sessions sessions of the random-tree bodies (5k-200k vertices, 12-40
+    bones, three image sizes), the same frames stepped one by one, on one stream each, as one fused
+    batch, and under the schedule the autotuner picks (tuned on warm-up frames).  Device-timed steps,
+    L2 flushed before each."""
+    import torch
+    from paper_1711_07999_gb300 import synth, trk
+    B = args.uneven_sessions
+    models = [synth.make_model(4, session=rank * 10000 + k) for k in range(B)]
+    sess = [trk.Session(m) for m in models]
+    nf = 4
+    frames = []
+    for i, (m, s) in enumerate(zip(models, sess)):
+        rng = np.random.default_rng(synth.seed_for(4, 7000 + rank * 10000 + i))
+        frames.append([torch.from_numpy(synth.add_noise(
+            s.render_depth(synth.gt_theta(m, f / 30.0), synth.gt_offsets(m, f / 30.0)), 4, rng)).cuda()
+            for f in range(nf)])
+        s.set_pose(synth.gt_theta(m, 0.0))
+    st = torch.cuda.Stream()
+    steps = max(3, args.steps // 3)
+
+    def timed(fn, n):
+        for k in range(3):
+            fn(k)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for k in range(n):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn(3 + k)
+            e1.record(st)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / n
+
+    def ptrs(k):
+        return [frames[i][k % nf].data_ptr() for i in range(B)]
+
+    def one_by_one(k):
+        for i, s in enumerate(sess):
+            s.track_frame_device(frames[i][k % nf].data_ptr(), st.cuda_stream)
+
+    out = {"sessions": B, "total_verts": int(sum(s.V for s in sess)),
+           "total_pixels": int(sum(s.W * s.H for s in sess)), "steps": steps}
+    out["one_by_one_fps"] = B * 1000.0 / timed(one_by_one, 2)
+    strs = [torch.cuda.Stream() for _ in sess]
+
+    def streams(k):
+        e = torch.cuda.Event()
+        e.record(st)
+        ends = []
+        for i, (s, x) in enumerate(zip(sess, strs)):
+            x.wait_event(e)
+            s.track_frame_device(frames[i][k % nf].data_ptr(), x.cuda_stream)
+            ee = torch.cuda.Event()
+            ee.record(x)
+            ends.append(ee)
+        for ee in ends:
+            st.wait_event(ee)
+    out["streams_fps"] = B * 1000.0 / timed(streams, steps)
+    with trk.Batch(sess) as b:
+        out["fused_batch_fps"] = B * 1000.0 / timed(lambda k: b.track_device(ptrs(k), st.cuda_stream), steps)
+        prof = b.profile(ptrs(0), reps=3, flush_bytes=L2_FLUSH_BYTES)
+    counts = [session_counts(s, frames[i][0].cpu().numpy()) for i, s in enumerate(sess)]
+    pk = peaks()
+    roof = {}
+    for stage in ("skin", "raster", "visibility", "associate", "resid_jtj", "reduce", "lm_eval", "shape"):
+        amount = sum(algorithmic(stage, **c)[1] for c in counts)
+        gbs = amount / (prof[stage] / 1000.0) / 1e9
+        roof[stage] = {"ms": round(prof[stage], 4), "algorithmic_bytes": int(amount), "achieved_gbs": round(gbs, 1),
+                       "frac": round(gbs / pk["hbm_gbs"], 4)}
+    out["fused_stage_roofline"] = {"peak_gbs": pk["hbm_gbs"], "peak_source": pk["src"] + " (burst copy)",
+                                   "l2": "flushed before each stage", "stages": roof}
+    with trk.Schedule(sess) as sc:
+        cfg, _ = sc.autotune(ptrs(0), reps=2)
+        out["schedule"] = cfg
+        out["schedule_fps"] = B * 1000.0 / timed(lambda k: sc.track_device(ptrs(k), st.cuda_stream), steps)
+    for s in sess:
+        s.close()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -510,14 +613,9 @@ def run_ours(args, rank, world, local_rank):
         n = P + S if st in ("skin", "raster", "visibility", "associate") else (S if st == "shape" else P)
         per_frame[st] = ms * n
     dom = max(per_frame, key=per_frame.get)
-    nvis = int((sess.read("VISPIX") >= 0).sum())
-    acc = sess.read("ACC")
-    nA = int((acc[:, 3] > 0).sum())
-    nassoc = int(acc[:, 3].sum())
-    nvalid = int((frames[0] > 0).sum())
-    NP = info["n_links"] + 1
-    nblk = (info["n_verts"] + 255) // 256
-    kind, amount = algorithmic(dom, info["n_verts"], info["n_tris"], W * H, NP, nvis, nassoc, nA, nvalid, nblk)
+    cnt = session_counts(sess, frames[(args.warmup + 2 * args.steps) % n_seq])
+    nA, NP = cnt["nA"], cnt["NP"]
+    kind, amount = algorithmic(dom, **cnt)
     pk = peaks()
     dur_s = prof[dom] / 1000.0
     if kind == "hbm":
@@ -576,6 +674,7 @@ def run_ours(args, rank, world, local_rank):
     precision = None
     if args.precision_modes and B > 1:
         precision = run_precision_modes(args, model, rank, dev, n_seq, flush, nA, NP, sample)
+    uneven = run_uneven(args, rank, flush) if args.uneven_sessions > 0 else None
     if rank == 0:
         plain = {"value": value, "ms_per_step": max_ms / args.steps,
                  "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
@@ -598,6 +697,7 @@ def run_ours(args, rank, world, local_rank):
             "plain": plain,
             "batched": batched,
             "precision": precision,
+            "uneven": uneven,
             "gpu_launches": info["kernels_per_frame"] * args.steps * (B if batched is not None else 1),
             "roofline": roof,
             "stage_ms": {k: round(v, 5) for k, v in prof.items()},
@@ -622,6 +722,8 @@ def main():
     ap.add_argument("--sessions", type=int, default=16, help="concurrent sessions of the batched measurement")
     ap.add_argument("--serve-streams", type=int, default=32, help="Poisson streams (30 fps each) of the serving run")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--uneven-sessions", type=int, default=64,
+                    help="sessions of the uneven batch (one by one / streams / fused batch / tuned schedule)")
     ap.add_argument("--precision-modes", type=int, default=1,
                     help="also time the tensor-core [J r]^T [J r] modes and their error against the oracle")
     args = ap.parse_args()

@@ -287,6 +287,12 @@ trk_status trk_batch_create(trk_session* const* sessions, int32_t n_sessions, tr
  * reads them in stream order.  The depth buffers must stay valid until the stream reaches the frame. */
 trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, void* cuda_stream);
 
+/* Mean CUDA-event time (ms) of each stage of one pose iteration (TRK_STAGE_*: skin ... lm_eval) and of
+ * the shape step, as ONE batched launch each, over reps repetitions at the members' current state on the
+ * depth images d_depths (flush_bytes > 0: that many bytes are written before each stage, so the stage
+ * starts with a cold L2).  The stages run for real: the members' state advances.  Synchronises. */
+trk_status trk_batch_profile(trk_batch* b, const float* const* d_depths, int32_t reps, size_t flush_bytes, float* ms);
+
 /* Waits for the batch's outstanding work and releases its device tables and graph. */
 void trk_batch_destroy(trk_batch* b);
 

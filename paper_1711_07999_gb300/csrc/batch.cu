@@ -257,6 +257,87 @@ trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, vo
   return TRK_OK;
 }
 
+trk_status trk_batch_profile(trk_batch* b, const float* const* d_depths, int32_t reps, size_t flush_bytes, float* ms) {
+  if (!b || !d_depths || !ms || reps <= 0) return set_error(TRK_ERR_INVALID_ARG, "trk_batch_profile: bad arguments");
+  const int B = (int)b->sessions.size();
+  const int L = b->max_links;
+  cudaStream_t st = b->cap;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void* flush = nullptr;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (!err) err = cudaEventCreate(&e1);
+  if (!err && flush_bytes) err = cudaMalloc(&flush, flush_bytes);
+  // this frame's depth (the profile starts like a frame)
+  const float** h = b->h_srcs;  // slot 0; wait for any copy still reading it
+  if (!err) err = cudaEventSynchronize(b->src_ev[0]);
+  if (!err) {
+    for (int k = 0; k < B; ++k) h[k] = d_depths[k];
+    err = cudaMemcpyAsync(b->d_srcs, h, sizeof(float*) * B, cudaMemcpyHostToDevice, st);
+  }
+  if (!err) err = cudaEventRecord(b->src_ev[0], st);
+  if (!err) err = cudaMemsetAsync(b->d_ctl, 0, sizeof(unsigned) * 3, st);
+  if (!err) launch_gather_depth_b(grid_of(b, kAssoc), b->tables[kAssoc].n, b->d_srcs, b->d_tiles, b->d_ctl, st);
+  double acc[TRK_STAGE_COUNT] = {0};
+  int flushes = 0;
+  auto timed = [&](int stage, auto&& fn) -> cudaError_t {
+    if (flush) cudaMemsetAsync(flush, (flushes++) & 0xFF, flush_bytes, st);
+    cudaEventRecord(e0, st);
+    fn();
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) return e;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    acc[stage] += t;
+    return cudaGetLastError();
+  };
+  BatchGrid gj[5];
+  int nj[5], nz[5] = {0, 0, 0, 0, 0};
+  for (int t = 0; t < 5; ++t) {
+    gj[t] = grid_of(b, (Kind)(kJtj1 + t));
+    nj[t] = b->tables[kJtj1 + t].n;
+  }
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    err = timed(TRK_STAGE_SKIN, [&] { launch_skin_b(grid_of(b, kSkin), b->tables[kSkin].n, L, 0, b->d_ctl, st); });
+    if (!err) err = timed(TRK_STAGE_RASTER, [&] { launch_raster_b(grid_of(b, kTris), b->tables[kTris].n, st); });
+    if (!err) err = timed(TRK_STAGE_VISIBILITY, [&] { launch_visibility_b(grid_of(b, kVerts), b->tables[kVerts].n, st); });
+    if (!err)
+      err = timed(TRK_STAGE_ASSOCIATE, [&] {
+        launch_associate_b(b->d_devs, B, b->d_tiles, b->d_ctl, b->d_prefix, b->assoc_blocks, b->tail_blocks, st);
+      });
+    if (!err)
+      err = timed(TRK_STAGE_RESID_JTJ, [&] {
+        launch_normal_equations_b(gj, nj, grid_of(b, kReduce), 0, L, b->precision, 0, -1, st);
+      });
+    if (!err)
+      err = timed(TRK_STAGE_REDUCE, [&] {
+        launch_normal_equations_b(gj, nz, grid_of(b, kReduce), b->tables[kReduce].n, L, b->precision, 0, -1, st);
+      });
+    if (!err) err = timed(TRK_STAGE_LM_SOLVE, [&] { launch_lm_b(grid_of(b, kLm), b->tables[kLm].n, grid_of(b, kVerts), 0, L, 0, st); });
+    if (!err) err = timed(TRK_STAGE_LM_EVAL, [&] { launch_lm_b(grid_of(b, kLm), 0, grid_of(b, kVerts), b->tables[kVerts].n, L, 0, st); });
+  }
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    launch_skin_b(grid_of(b, kSkin), b->tables[kSkin].n, L, 0, b->d_ctl, st);
+    launch_raster_b(grid_of(b, kTris), b->tables[kTris].n, st);
+    launch_visibility_b(grid_of(b, kVerts), b->tables[kVerts].n, st);
+    launch_associate_b(b->d_devs, B, b->d_tiles, b->d_ctl, b->d_prefix, b->assoc_blocks, b->tail_blocks, st);
+    int cur = 0;
+    err = timed(TRK_STAGE_SHAPE, [&] { cur = launch_shape_b(grid_of(b, kVerts), b->tables[kVerts].n, L, b->shape_sweeps, 0, -1, st); });
+    if (!err && cur != 0)
+      for (trk_session* s : b->sessions) {
+        const Dev& d = session_dev(s);
+        cudaMemcpyAsync(d.phi[0], d.phi[cur], sizeof(float4) * d.V, cudaMemcpyDeviceToDevice, st);
+      }
+  }
+  cudaStreamSynchronize(st);
+  if (flush) cudaFree(flush);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (err != cudaSuccess) return set_error(TRK_ERR_CUDA, cudaGetErrorString(err));
+  for (int k = 0; k < TRK_STAGE_COUNT; ++k) ms[k] = (float)(acc[k] / reps);
+  return TRK_OK;
+}
+
 void trk_batch_destroy(trk_batch* b) { free_batch(b); }
 
 }  // extern "C"

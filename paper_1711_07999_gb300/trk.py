@@ -25,7 +25,8 @@ EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_dev
            "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
            "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc",
-           "trk_jtj_rows_tc", "trk_batch_create", "trk_batch_track_device", "trk_batch_destroy",
+           "trk_jtj_rows_tc", "trk_batch_create", "trk_batch_track_device", "trk_batch_profile",
+           "trk_batch_destroy",
            "trk_schedule_create", "trk_schedule_track_device", "trk_schedule_get_config", "trk_schedule_autotune",
            "trk_schedule_destroy", "trk_schedule_signature", "trk_tuning_cache_lookup", "trk_tuning_cache_store",
            "trk_server_create", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
@@ -105,6 +106,7 @@ def lib(build_if_missing: bool = True):
             "trk_jtj_rows": [vp, i32, i32, i32, vp, vp], "trk_jtj_rows_noalloc": [vp, i32, i32, i32, vp, vp],
             "trk_jtj_rows_tc": [vp, i32, i32, i32, i32, vp, vp],
             "trk_batch_create": [C.POINTER(vp), i32, C.POINTER(vp)], "trk_batch_track_device": [vp, C.POINTER(vp), vp],
+            "trk_batch_profile": [vp, C.POINTER(vp), i32, sz, vp],
             "trk_schedule_create": [C.POINTER(vp), i32, vp, C.c_char_p, C.POINTER(vp)],
             "trk_schedule_track_device": [vp, C.POINTER(vp), vp], "trk_schedule_get_config": [vp, vp],
             "trk_schedule_autotune": [vp, C.POINTER(vp), i32, C.c_char_p, vp, C.POINTER(C.c_double)],
@@ -294,6 +296,13 @@ class Batch:
         """One frame of every member; depth_ptrs[k] is a device pointer to member k's depth image."""
         arr = (C.c_void_p * len(self.sessions))(*depth_ptrs)
         _check(lib().trk_batch_track_device(self.h, arr, C.c_void_p(stream_ptr or None)))
+
+    def profile(self, depth_ptrs, reps: int = 5, flush_bytes: int = 0) -> dict:
+        """Mean CUDA-event duration (ms) of each stage as one batched launch (the members advance)."""
+        arr = (C.c_void_p * len(self.sessions))(*depth_ptrs)
+        ms = np.empty(len(STAGES), np.float32)
+        _check(lib().trk_batch_profile(self.h, arr, reps, flush_bytes, _p(ms)))
+        return dict(zip(STAGES, ms.tolist()))
 
     def close(self):
         if self.h:
