@@ -42,6 +42,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "frames/s and p99 frame latency, 50k-vert/640x480, batched vs plain, same GPU"
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "tf32x3": 2}
 WORKLOAD = "humanoid-22bone-55dof-50k-vert-640x480-30fps-sinusoidal"
 L2_FLUSH_BYTES = 256 << 20
 
@@ -501,9 +502,11 @@ def run_uneven(args, rank, flush):
         for i, s in enumerate(sess):
             s.track_frame_device(frames[i][k % nf].data_ptr(), st.cuda_stream)
 
+    modes = set(args.uneven_modes.split(","))
     out = {"sessions": B, "total_verts": int(sum(s.V for s in sess)),
            "total_pixels": int(sum(s.W * s.H for s in sess)), "steps": steps}
-    out["one_by_one_fps"] = B * 1000.0 / timed(one_by_one, 2)
+    if "one_by_one" in modes:
+        out["one_by_one_fps"] = B * 1000.0 / timed(one_by_one, 2)
     strs = [torch.cuda.Stream() for _ in sess]
 
     def streams(k):
@@ -518,10 +521,24 @@ def run_uneven(args, rank, flush):
             ends.append(ee)
         for ee in ends:
             st.wait_event(ee)
-    out["streams_fps"] = B * 1000.0 / timed(streams, steps)
-    with trk.Batch(sess) as b:
-        out["fused_batch_fps"] = B * 1000.0 / timed(lambda k: b.track_device(ptrs(k), st.cuda_stream), steps)
-        prof = b.profile(ptrs(0), reps=3, flush_bytes=L2_FLUSH_BYTES)
+    if "streams" in modes:
+        out["streams_fps"] = B * 1000.0 / timed(streams, steps)
+    if "fused" in modes:
+        with trk.Batch(sess) as b:
+            out["fused_batch_fps"] = B * 1000.0 / timed(lambda k: b.track_device(ptrs(k), st.cuda_stream), steps)
+            prof = b.profile(ptrs(0), reps=3, flush_bytes=L2_FLUSH_BYTES)
+        out["fused_stage_roofline"] = fused_rooflines(sess, frames, prof)
+    if "schedule" in modes:
+        with trk.Schedule(sess) as sc:
+            cfg, _ = sc.autotune(ptrs(0), reps=2)
+            out["schedule"] = cfg
+            out["schedule_fps"] = B * 1000.0 / timed(lambda k: sc.track_device(ptrs(k), st.cuda_stream), steps)
+    for s in sess:
+        s.close()
+    return out
+
+
+def fused_rooflines(sess, frames, prof):
     counts = [session_counts(s, frames[i][0].cpu().numpy()) for i, s in enumerate(sess)]
     pk = peaks()
     roof = {}
@@ -530,15 +547,8 @@ def run_uneven(args, rank, flush):
         gbs = amount / (prof[stage] / 1000.0) / 1e9
         roof[stage] = {"ms": round(prof[stage], 4), "algorithmic_bytes": int(amount), "achieved_gbs": round(gbs, 1),
                        "frac": round(gbs / pk["hbm_gbs"], 4)}
-    out["fused_stage_roofline"] = {"peak_gbs": pk["hbm_gbs"], "peak_source": pk["src"] + " (burst copy)",
-                                   "l2": "flushed before each stage", "stages": roof}
-    with trk.Schedule(sess) as sc:
-        cfg, _ = sc.autotune(ptrs(0), reps=2)
-        out["schedule"] = cfg
-        out["schedule_fps"] = B * 1000.0 / timed(lambda k: sc.track_device(ptrs(k), st.cuda_stream), steps)
-    for s in sess:
-        s.close()
-    return out
+    return {"peak_gbs": pk["hbm_gbs"], "peak_source": pk["src"] + " (burst copy)",
+            "l2": "flushed before each stage", "stages": roof}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -547,7 +557,11 @@ def run_ours(args, rank, world, local_rank):
     from paper_1711_07999_gb300 import synth, trk
 
     torch.cuda.set_device(local_rank)
-    model = synth.make_model(2, session=rank)
+    if args.only == "uneven":  # the uneven batch alone (a diagnostic line, not the benchmark line)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        return {"uneven": run_uneven(args, rank, flush)} if rank == 0 else None
+    prec = PRECISIONS[args.precision]
+    model = synth.make_model(2, session=rank, precision=prec)
     sess = trk.Session(model)
     info = sess.info()
     n_seq = max(args.frames, 1)
@@ -635,7 +649,7 @@ def run_ours(args, rank, world, local_rank):
     batched = None
     B = args.sessions
     if B > 1:
-        extra = [trk.Session(synth.make_model(2, session=rank * 1000 + b + 1)) for b in range(B - 1)]
+        extra = [trk.Session(synth.make_model(2, session=rank * 1000 + b + 1, precision=prec)) for b in range(B - 1)]
         group = [sess] + extra
         for b, x in enumerate(group):
             x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
@@ -654,7 +668,7 @@ def run_ours(args, rank, world, local_rank):
                            "p50_ms": float(np.percentile(lat_be, 50)), "p99_ms": float(np.percentile(lat_be, 99))}}
         serving = None
         if args.serve_streams > 0:
-            more = [trk.Session(synth.make_model(2, session=rank * 1000 + 100 + b))
+            more = [trk.Session(synth.make_model(2, session=rank * 1000 + 100 + b, precision=prec))
                     for b in range(max(0, args.serve_streams - len(group)))]
             streams = (group + more)[:args.serve_streams]
             for b, x in enumerate(streams):
@@ -722,12 +736,19 @@ def main():
     ap.add_argument("--sessions", type=int, default=16, help="concurrent sessions of the batched measurement")
     ap.add_argument("--serve-streams", type=int, default=32, help="Poisson streams (30 fps each) of the serving run")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32",
+                    help="arithmetic of [J r]^T [J r] in the plain and batched sessions")
+    ap.add_argument("--only", choices=["all", "plain", "uneven"], default="all",
+                    help="plain: the one-session and batched measurements only; uneven: the uneven batch only")
+    ap.add_argument("--uneven-modes", default="one_by_one,streams,fused,schedule")
     ap.add_argument("--uneven-sessions", type=int, default=64,
                     help="sessions of the uneven batch (one by one / streams / fused batch / tuned schedule)")
     ap.add_argument("--precision-modes", type=int, default=1,
                     help="also time the tensor-core [J r]^T [J r] modes and their error against the oracle")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.only == "plain":
+        args.uneven_sessions, args.precision_modes = 0, 0
     rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank, world)
