@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
 
 class Params(C.Structure):
     _fields_ = [("pose_iters", C.c_int32), ("shape_iters", C.c_int32), ("shape_sweeps", C.c_int32),
-                ("window_half", C.c_int32), ("knn", C.c_int32), ("pad_", C.c_int32),
+                ("window_half", C.c_int32), ("knn", C.c_int32), ("shape_solver", C.c_int32),
                 ("lambda_k0", C.c_double), ("lambda_s", C.c_double), ("lambda_phi", C.c_double),
                 ("lambda_N", C.c_double), ("lambda_w", C.c_double), ("cutoff", C.c_double),
                 ("eps_vis", C.c_double), ("z_near", C.c_double)]
@@ -143,7 +143,8 @@ class Oracle:
         self.fx, self.fy, self.cx, self.cy = (float(cam[k]) for k in ("fx", "fy", "cx", "cy"))
         self.params = pr
         p = Params(pose_iters=pr["pose_iters"], shape_iters=pr["shape_iters"], shape_sweeps=pr["shape_sweeps"],
-                   window_half=pr["window_half"], knn=pr["knn"], pad_=0, lambda_k0=pr["lambda_k0"],
+                   window_half=pr["window_half"], knn=pr["knn"], shape_solver=pr.get("shape_solver", 0),
+                   lambda_k0=pr["lambda_k0"],
                    lambda_s=pr["lambda_s"], lambda_phi=pr["lambda_phi"], lambda_N=pr["lambda_N"],
                    lambda_w=pr["lambda_w"], cutoff=pr["cutoff"], eps_vis=pr["eps_vis"], z_near=pr["z_near"])
         self._keep = dict(

@@ -18,6 +18,7 @@
  *   R8  association ties go to the smaller vertex index
  *   R9  association window half-size W and cutoff tau are parameters
  *   R10 pose prior weight S_kk = n_k/|V| (n_k = vertices weighted to the subtree of link k), times a mask
+ *   R22 the coupled shape step: the whole shape energy's damped Gauss-Newton system, solved by PCG
  *   R12 derivative block of link j's offset w.r.t. theta_k uses the chain from k to j (no double count)
  *   R13 LM damping uses diag of the prior-augmented matrix; a parameter with zero diagonal is frozen
  *   R14 LM schedule: lambda x10 on reject (<= 5 retries, energy at fixed association), /10 on accept
@@ -132,7 +133,7 @@ static void q_to_rot(quat q, double* R) {
 /* Model                                                                                             */
 /* ------------------------------------------------------------------------------------------------ */
 typedef struct {
-  int32_t pose_iters, shape_iters, shape_sweeps, window_half, knn, pad_;
+  int32_t pose_iters, shape_iters, shape_sweeps, window_half, knn, shape_solver; /* 0 Jacobi (R15), 1 PCG (R22) */
   double lambda_k0, lambda_s, lambda_phi, lambda_N, lambda_w, cutoff, eps_vis, z_near;
 } orc_params;
 
@@ -813,9 +814,110 @@ static int solve3(const double* M, const double* b, double* x) {
 }
 int orc_solve3(const double* M, const double* b, double* x) { return solve3(M, b, x); }
 
+/* R22: the coupled Gauss-Newton step of the whole shape energy of Sec. 4.3,
+ *   E(Phi) = sum_{i in A} r_i^2 + lambda_phi sum_i |phi_i|^2 + lambda_N sum_i sum_{n in N(i)} |phi_i - phi_n|^2,
+ * with r_i linearised as r_i + g_i . delta_i:  (H + lambda_w D) delta = -b, where
+ *   H_ii = [i in A] g_i g_i^T + (lambda_phi + lambda_N deg_i) I,  H_ij = -lambda_N m_ij I,
+ *   b_i  = [i in A] g_i r_i + lambda_phi phi_i + lambda_N sum_{j in adj(i)} (phi_i - phi_j),
+ * adj(i) = the neighbourhood edges at i in either direction (the multiset of n in N(i) and of m with
+ * i in N(m)), deg_i = |adj(i)|, m_ij the multiplicity of j in adj(i), D = diag(H).  Solved by conjugate
+ * gradients from delta = 0, preconditioned with the 3x3 diagonal blocks of H + lambda_w D, for `iters`
+ * iterations (or until r.z = 0 or p.Ap <= 0).  phi += delta. */
+static int cmp_int(const void* a, const void* b) {
+  const int x = *(const int*)a, y = *(const int*)b;
+  return (x > y) - (x < y);
+}
+
+static void shape_pcg(orc_model* m, double* phi, const double* r0, const double* g, const int32_t* inA, int iters) {
+  const int V = m->V, K = m->p.knn;
+  const double lp = m->p.lambda_phi, lN = m->p.lambda_N, lw = m->p.lambda_w;
+  /* adjacency in both directions, each list sorted by vertex index */
+  int* deg = (int*)xcalloc(V + 1, sizeof(int));
+  for (int i = 0; i < V; ++i)
+    for (int t = 0; t < K; ++t) {
+      const int q = m->nbr[K * i + t];
+      if (q < 0) continue;
+      ++deg[i];
+      ++deg[q];
+    }
+  int* off = (int*)xcalloc(V + 1, sizeof(int));
+  for (int i = 0; i < V; ++i) off[i + 1] = off[i] + deg[i];
+  int* adj = (int*)xcalloc(off[V] > 0 ? off[V] : 1, sizeof(int));
+  int* fill = (int*)xcalloc(V, sizeof(int));
+  for (int i = 0; i < V; ++i)
+    for (int t = 0; t < K; ++t) {
+      const int q = m->nbr[K * i + t];
+      if (q < 0) continue;
+      adj[off[i] + fill[i]++] = q;
+      adj[off[q] + fill[q]++] = i;
+    }
+  for (int i = 0; i < V; ++i) qsort(adj + off[i], deg[i], sizeof(int), cmp_int);
+  /* per-vertex damped diagonal blocks B_i = H_ii + lambda_w diag(H_ii) */
+  double* Bk = (double*)xcalloc(9 * (size_t)V, sizeof(double));
+  for (int i = 0; i < V; ++i) {
+    const double* gi = g + 3 * i;
+    const double c = lp + lN * deg[i];
+    for (int a = 0; a < 3; ++a)
+      for (int e = 0; e < 3; ++e) Bk[9 * i + 3 * a + e] = (inA[i] ? gi[a] * gi[e] : 0.0) + (a == e ? c : 0.0);
+    for (int a = 0; a < 3; ++a) Bk[9 * i + 4 * a] += lw * Bk[9 * i + 4 * a];
+  }
+  const size_t n3 = 3 * (size_t)V;
+  double* x = (double*)xcalloc(n3, sizeof(double));
+  double* r = (double*)xcalloc(n3, sizeof(double));
+  double* z = (double*)xcalloc(n3, sizeof(double));
+  double* pv = (double*)xcalloc(n3, sizeof(double));
+  double* Ap = (double*)xcalloc(n3, sizeof(double));
+  /* r = -b */
+  for (int i = 0; i < V; ++i) {
+    const double* gi = g + 3 * i;
+    const double* pi = phi + 3 * i;
+    for (int c = 0; c < 3; ++c) {
+      double bc = (inA[i] ? gi[c] * r0[i] : 0.0) + lp * pi[c];
+      for (int t = off[i]; t < off[i + 1]; ++t) bc += lN * (pi[c] - phi[3 * adj[t] + c]);
+      r[3 * i + c] = -bc;
+    }
+  }
+  double rz = 0.0;
+  for (int i = 0; i < V; ++i) {
+    if (solve3(Bk + 9 * i, r + 3 * i, z + 3 * i) != 0) z[3 * i] = z[3 * i + 1] = z[3 * i + 2] = 0.0;
+    for (int c = 0; c < 3; ++c) rz += r[3 * i + c] * z[3 * i + c];
+  }
+  memcpy(pv, z, n3 * sizeof(double));
+  for (int it = 0; it < iters && rz > 0.0; ++it) {
+    double pAp = 0.0;
+    for (int i = 0; i < V; ++i) {
+      const double* Bi = Bk + 9 * i;
+      const double* p = pv + 3 * i;
+      for (int a = 0; a < 3; ++a) {
+        double s = Bi[3 * a] * p[0] + Bi[3 * a + 1] * p[1] + Bi[3 * a + 2] * p[2];
+        for (int t = off[i]; t < off[i + 1]; ++t) s -= lN * pv[3 * adj[t] + a];
+        Ap[3 * i + a] = s;
+        pAp += p[a] * s;
+      }
+    }
+    if (!(pAp > 0.0)) break;
+    const double alpha = rz / pAp;
+    double rz_new = 0.0;
+    for (int i = 0; i < V; ++i) {
+      for (int c = 0; c < 3; ++c) {
+        x[3 * i + c] += alpha * pv[3 * i + c];
+        r[3 * i + c] -= alpha * Ap[3 * i + c];
+      }
+      if (solve3(Bk + 9 * i, r + 3 * i, z + 3 * i) != 0) z[3 * i] = z[3 * i + 1] = z[3 * i + 2] = 0.0;
+      for (int c = 0; c < 3; ++c) rz_new += r[3 * i + c] * z[3 * i + c];
+    }
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (size_t k = 0; k < n3; ++k) pv[k] = z[k] + beta * pv[k];
+  }
+  for (size_t k = 0; k < n3; ++k) phi[k] += x[k];
+  free(deg); free(off); free(adj); free(fill); free(Bk); free(x); free(r); free(z); free(pv); free(Ap);
+}
+
 /* Sec. 4.3 shape step (R15): per-vertex Gauss-Newton on
  *   e_i = [i in A] r_i^2 + lambda_phi |phi_i|^2 + lambda_N sum_{n in N(i)} |phi_i - phi_n|^2
- * with the neighbours frozen, one 3x3 damped system per vertex (Jacobi), shape_sweeps sweeps.
+ * with the neighbours frozen, one 3x3 damped system per vertex (Jacobi), shape_sweeps sweeps;
+ * with shape_solver = 1 the coupled system of R22 instead, shape_sweeps PCG iterations.
  * g_i = dr_i/dphi_i = -R(a^_i)^T n_i (a^_i the normalised real part of H_iSigma).
  * Returns the shape energy sum_i e_i before the update.  phi is updated in place.
  * r_out, g_out (optional): r_i and g_i. */
@@ -851,7 +953,8 @@ double orc_shape_step(void* h, const double* theta, double* phi, const double* n
       for (int c = 0; c < 3; ++c) { double d = pi[c] - phi[3 * q + c]; E += lN * d * d; }
     }
   }
-  for (int sw = 0; sw < m->p.shape_sweeps; ++sw) {
+  if (m->p.shape_solver == 1) shape_pcg(m, phi, r0, g, inA, m->p.shape_sweeps);
+  for (int sw = 0; sw < (m->p.shape_solver == 1 ? 0 : m->p.shape_sweeps); ++sw) {
     memcpy(cur, phi, sizeof(double) * 3 * V);
     for (int i = 0; i < V; ++i) {
       const double* pi = cur + 3 * i;
