@@ -82,6 +82,10 @@ typedef struct {
   float cutoff_m, eps_vis_m, z_near_m;
   int32_t window_half_px, knn;
   int32_t precision; /* TRK_PRECISION_*: how [J r]^T [J r] is formed in each pose iteration      */
+  int32_t shape_solver; /* 0: Jacobi sweeps with the neighbours frozen (Sec. 4.3; shape_sweeps
+                           sweeps); 1: the coupled damped Gauss-Newton system of the whole shape
+                           energy by block-Jacobi-preconditioned conjugate gradients (shape_sweeps
+                           iterations)                                                               */
 } trk_params;
 
 /* Arithmetic of the contraction [J r]^T [J r] (Eqs. JTJ, JTr).  FP32: products and per-CTA sums on the

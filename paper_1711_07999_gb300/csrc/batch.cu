@@ -40,7 +40,7 @@ struct Table {
 struct trk_batch {
   std::vector<trk_session*> sessions;
   int device = 0;
-  int pose_iters = 0, shape_iters = 0, shape_sweeps = 0, precision = 0;
+  int pose_iters = 0, shape_iters = 0, shape_sweeps = 0, precision = 0, shape_solver = 0;
   int max_links = 0, max_np = 0;
   int assoc_blocks = 608;     // persistent association blocks
   int tail_blocks = 304;      // association-tail blocks (shared by all sessions' queues)
@@ -104,7 +104,7 @@ void enqueue_batch_frame(trk_batch* b, cudaStream_t st) {
   }
   for (int it = 0; it < S; ++it) {
     geometry();
-    cur = launch_shape_b(grid_of(b, kVerts), b->tables[kVerts].n, L, b->shape_sweeps, cur, P + it, st);
+    cur = launch_shape_b(grid_of(b, kVerts), b->tables[kVerts].n, L, b->shape_sweeps, b->shape_solver, cur, P + it, st);
   }
   if (cur != 0)
     for (trk_session* s : b->sessions) {
@@ -161,6 +161,7 @@ trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_
   b->shape_iters = p0.shape_iters;
   b->shape_sweeps = p0.shape_sweeps;
   b->precision = p0.precision;
+  b->shape_solver = p0.shape_solver;
   for (int k = 0; k < n_sessions; ++k) {
     trk_session* s = sessions[k];
     if (!s) {
@@ -174,10 +175,10 @@ trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_
       }
     const trk_params& p = session_params(s);
     if (session_device(s) != b->device || p.pose_iters != b->pose_iters || p.shape_iters != b->shape_iters ||
-        p.shape_sweeps != b->shape_sweeps || p.precision != b->precision) {
+        p.shape_sweeps != b->shape_sweeps || p.precision != b->precision || p.shape_solver != b->shape_solver) {
       free_batch(b);
       return set_error(TRK_ERR_INVALID_ARG,
-                       "trk_batch_create: sessions differ in device, iteration schedule or precision");
+                       "trk_batch_create: sessions differ in device, iteration schedule, precision or shape solver");
     }
     const Dev& d = session_dev(s);
     b->max_links = std::max(b->max_links, d.L);
@@ -322,7 +323,9 @@ trk_status trk_batch_profile(trk_batch* b, const float* const* d_depths, int32_t
     launch_visibility_b(grid_of(b, kVerts), b->tables[kVerts].n, st);
     launch_associate_b(b->d_devs, B, b->d_tiles, b->d_ctl, b->d_prefix, b->assoc_blocks, b->tail_blocks, st);
     int cur = 0;
-    err = timed(TRK_STAGE_SHAPE, [&] { cur = launch_shape_b(grid_of(b, kVerts), b->tables[kVerts].n, L, b->shape_sweeps, 0, -1, st); });
+    err = timed(TRK_STAGE_SHAPE, [&] {
+      cur = launch_shape_b(grid_of(b, kVerts), b->tables[kVerts].n, L, b->shape_sweeps, b->shape_solver, 0, -1, st);
+    });
     if (!err && cur != 0)
       for (trk_session* s : b->sessions) {
         const Dev& d = session_dev(s);

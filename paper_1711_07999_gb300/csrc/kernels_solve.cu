@@ -908,6 +908,18 @@ __device__ __forceinline__ void block_energy_to_slot(const Dev& d, BlockPos bp, 
   }
 }
 
+// r_i (the mean offset of the associated pixels along n_i) and g_i = dr_i/dphi_i = -R(a^_i)^T n_i.
+__device__ __forceinline__ void vertex_r_g(const Dev& d, const DQ* sHd, int i, const Acc4& a4, const float4& nn,
+                                           float& r, float3& g) {
+  const float inv = 1.f / ((float)a4.w * kFix);
+  r = nn.x * (float)a4.x * inv + nn.y * (float)a4.y * inv + nn.z * (float)a4.z * inv;
+  float sg[4];
+  const DQ H = blend_bones(sHd, d.bidx[i], d.bw[i], sg);
+  const float4 ah = qscale(H.r, rsqrtf(qdot(H.r, H.r)));
+  const float4 q = qmul(qmul(qconj(ah), make_float4(0.f, nn.x, nn.y, nn.z)), ah);  // R^T n
+  g = make_float3(-q.y, -q.z, -q.w);
+}
+
 __device__ __forceinline__ void shape_impl(const Dev& d, BlockPos bp, int src, int slot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DQ* sHd = reinterpret_cast<DQ*>(smem_raw);
@@ -931,13 +943,7 @@ __device__ __forceinline__ void shape_impl(const Dev& d, BlockPos bp, int src, i
     float3 g = make_float3(0.f, 0.f, 0.f);
     if (inA) {
       inA_count = 1;
-      const float inv = 1.f / ((float)a4.w * kFix);
-      r = nn.x * (float)a4.x * inv + nn.y * (float)a4.y * inv + nn.z * (float)a4.z * inv;
-      float sg[4];
-      const DQ H = blend_bones(sHd, d.bidx[i], d.bw[i], sg);
-      const float4 ah = qscale(H.r, rsqrtf(qdot(H.r, H.r)));
-      const float4 q = qmul(qmul(qconj(ah), make_float4(0.f, nn.x, nn.y, nn.z)), ah);  // R^T n
-      g = make_float3(-q.y, -q.z, -q.w);
+      vertex_r_g(d, sHd, i, a4, nn, r, g);
     }
     e = r * r + d.lambda_phi * dot3(pi, pi);
     float3 sd = make_float3(0.f, 0.f, 0.f);
@@ -1011,8 +1017,227 @@ __global__ void __launch_bounds__(kBlock) k_shape_sweep(BatchGrid g, Dev d0, int
   shape_sweep_impl(sd, batch_block(g, sd), src);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Coupled shape step (the whole shape energy of Sec. 4.3, linearised in r): (H + lambda_w diag H) delta
+// = -b with H_ii = [A] g g^T + (lambda_phi + lambda_N deg_i) I and H_ij = -lambda_N I per neighbourhood
+// edge (either direction), by conjugate gradients preconditioned with the 3x3 diagonal blocks.  Vectors
+// in FP32, dot products in FP64 with fixed-order block sums (deterministic); a breakdown (r.z = 0 or
+// p.Ap <= 0) stops the iteration as in exact arithmetic.  One kernel per CG phase.
+// ---------------------------------------------------------------------------------------------
+// Block sum of v (FP64) into epart[bp.x * 8 + slot]; returns true in every thread of the session's last
+// block, with the fixed-order total of all its blocks in `total`.
+__device__ __forceinline__ bool block_total(const Dev& d, BlockPos bp, double v, int slot, int ticket, double& total) {
+  __shared__ double sw[kBlock / 32];
+  __shared__ double red[kBlock];
+  __shared__ bool last;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) s += sw[w];
+    d.epart[(size_t)bp.x * 8 + slot] = s;
+    __threadfence();
+    last = atomicAdd(&d.counter[ticket], 1u) == (unsigned)bp.gx - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < bp.gx; b += kBlock) s += __ldcg(d.epart + (size_t)b * 8 + slot);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = kBlock / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  total = red[0];
+  if (threadIdx.x == 0) d.counter[ticket] = 0;
+  return true;
+}
+
+// B_i = M_i + lambda_w diag(M_i), M_i = g g^T + c I (g = 0 outside A): B_i p and B_i^-1 p.
+__device__ __forceinline__ float3 block_apply(float3 g, float c, float lw, float3 p) {
+  const float gp = g.x * p.x + g.y * p.y + g.z * p.z;
+  return make_float3(g.x * gp + c * p.x + lw * (g.x * g.x + c) * p.x, g.y * gp + c * p.y + lw * (g.y * g.y + c) * p.y,
+                     g.z * gp + c * p.z + lw * (g.z * g.z + c) * p.z);
+}
+
+// r_i, g_i, E_shape (energy[slot]) as the Jacobi step; b; x = 0, r = -b, z = B^-1 r, p = z, rz = r.z.
+__device__ __forceinline__ void cg_init_impl(const Dev& d, BlockPos bp, int src, int slot) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DQ* sHd = reinterpret_cast<DQ*>(smem_raw);
+  const int i = bp.x * kBlock + threadIdx.x;
+  bool anyA = false;
+  if (i < d.V) anyA = d.acc[i].w >= 1 && d.n[i].w > 0.f;
+  if (__syncthreads_or(anyA)) {
+    for (int j = threadIdx.x; j < d.L; j += kBlock) sHd[j] = d.Hd[j];
+    __syncthreads();
+  }
+  float e = 0.f;
+  double rz = 0.0;
+  int inA_count = 0;
+  if (i < d.V) {
+    const float4* phi = d.phi[src];
+    const float4 p4 = phi[i];
+    const float3 pi = f3(p4);
+    const Acc4 a4 = d.acc[i];
+    const float4 nn = d.n[i];
+    float r = 0.f;
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    if (a4.w >= 1 && nn.w > 0.f) {
+      inA_count = 1;
+      vertex_r_g(d, sHd, i, a4, nn, r, g);
+    }
+    e = r * r + d.lambda_phi * dot3(pi, pi);
+    const int4 nb = d.nbr[i];
+    const int nbs[4] = {nb.x, nb.y, nb.z, nb.w};
+    for (int t = 0; t < d.knn; ++t) {
+      if (nbs[t] < 0) continue;
+      const float3 q = f3(phi[nbs[t]]);
+      const float3 df = make_float3(pi.x - q.x, pi.y - q.y, pi.z - q.z);
+      e += d.lambda_N * dot3(df, df);
+    }
+    float3 sd = make_float3(0.f, 0.f, 0.f);
+    const int a0 = d.adj_off[i], a1 = d.adj_off[i + 1];
+    for (int t = a0; t < a1; ++t) {
+      const float3 q = f3(phi[d.adj[t]]);
+      sd.x += pi.x - q.x; sd.y += pi.y - q.y; sd.z += pi.z - q.z;
+    }
+    const float3 rr = make_float3(-(g.x * r + d.lambda_phi * pi.x + d.lambda_N * sd.x),
+                                  -(g.y * r + d.lambda_phi * pi.y + d.lambda_N * sd.y),
+                                  -(g.z * r + d.lambda_phi * pi.z + d.lambda_N * sd.z));
+    const float3 z = solve3_damped(g, d.lambda_phi + d.lambda_N * (float)(a1 - a0), d.lambda_w, rr);
+    d.rg[i] = make_float4(g.x, g.y, g.z, r);
+    d.phi0[i] = p4;
+    d.cg_x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    d.cg_r[i] = make_float4(rr.x, rr.y, rr.z, 0.f);
+    d.cg_z[i] = make_float4(z.x, z.y, z.z, 0.f);
+    d.cg_p[i] = make_float4(z.x, z.y, z.z, 0.f);
+    rz = (double)rr.x * z.x + (double)rr.y * z.y + (double)rr.z * z.z;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, inA_count != 0);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(&d.stats[1], __popc(m));
+  double tot;
+  if (block_total(d, bp, rz, 1, 2, tot) && threadIdx.x == 0) {
+    d.cg[0] = tot;
+    d.cg[3] = tot > 0.0 ? 0.0 : 1.0;  // stopped if the preconditioned residual is already zero
+  }
+  block_energy_to_slot(d, bp, e, slot, 1);
+}
+
+// Ap = (B - lambda_N Adj) p; alpha = r.z / p.Ap (0 and stop on a breakdown).
+__device__ __forceinline__ void cg_apply_impl(const Dev& d, BlockPos bp) {
+  const int i = bp.x * kBlock + threadIdx.x;
+  double pap = 0.0;
+  if (i < d.V) {
+    const float4 rg = d.rg[i];
+    const float3 p = f3(d.cg_p[i]);
+    const int a0 = d.adj_off[i], a1 = d.adj_off[i + 1];
+    float3 ap = block_apply(f3(rg), d.lambda_phi + d.lambda_N * (float)(a1 - a0), d.lambda_w, p);
+    for (int t = a0; t < a1; ++t) {
+      const float3 q = f3(d.cg_p[d.adj[t]]);
+      ap.x -= d.lambda_N * q.x; ap.y -= d.lambda_N * q.y; ap.z -= d.lambda_N * q.z;
+    }
+    d.cg_ap[i] = make_float4(ap.x, ap.y, ap.z, 0.f);
+    pap = (double)p.x * ap.x + (double)p.y * ap.y + (double)p.z * ap.z;
+  }
+  double tot;
+  if (block_total(d, bp, pap, 2, 3, tot) && threadIdx.x == 0) {
+    const bool go = d.cg[3] == 0.0 && tot > 0.0;
+    d.cg[1] = go ? d.cg[0] / tot : 0.0;
+    if (!go) d.cg[3] = 1.0;
+  }
+}
+
+// x += alpha p, r -= alpha Ap, z = B^-1 r; beta = r.z_new / r.z.
+__device__ __forceinline__ void cg_update_impl(const Dev& d, BlockPos bp) {
+  const int i = bp.x * kBlock + threadIdx.x;
+  const float alpha = (float)d.cg[1];
+  double rz = 0.0;
+  if (i < d.V) {
+    const float4 rg = d.rg[i];
+    const float3 p = f3(d.cg_p[i]), ap = f3(d.cg_ap[i]);
+    float3 x = f3(d.cg_x[i]), r = f3(d.cg_r[i]);
+    x.x += alpha * p.x; x.y += alpha * p.y; x.z += alpha * p.z;
+    r.x -= alpha * ap.x; r.y -= alpha * ap.y; r.z -= alpha * ap.z;
+    const int deg = d.adj_off[i + 1] - d.adj_off[i];
+    const float3 z = solve3_damped(f3(rg), d.lambda_phi + d.lambda_N * (float)deg, d.lambda_w, r);
+    d.cg_x[i] = make_float4(x.x, x.y, x.z, 0.f);
+    d.cg_r[i] = make_float4(r.x, r.y, r.z, 0.f);
+    d.cg_z[i] = make_float4(z.x, z.y, z.z, 0.f);
+    rz = (double)r.x * z.x + (double)r.y * z.y + (double)r.z * z.z;
+  }
+  double tot;
+  if (block_total(d, bp, rz, 1, 2, tot) && threadIdx.x == 0) {
+    const bool go = d.cg[3] == 0.0 && d.cg[0] > 0.0;
+    d.cg[2] = go ? tot / d.cg[0] : 0.0;
+    d.cg[0] = tot;
+    if (!(tot > 0.0)) d.cg[3] = 1.0;
+  }
+}
+
+// p = z + beta p.
+__device__ __forceinline__ void cg_dir_impl(const Dev& d, BlockPos bp) {
+  const int i = bp.x * kBlock + threadIdx.x;
+  if (i >= d.V) return;
+  const float beta = (float)d.cg[2];
+  const float3 z = f3(d.cg_z[i]), p = f3(d.cg_p[i]);
+  d.cg_p[i] = make_float4(z.x + beta * p.x, z.y + beta * p.y, z.z + beta * p.z, 0.f);
+}
+
+// phi[1 - src] = phi[src] + x.
+__device__ __forceinline__ void cg_finish_impl(const Dev& d, BlockPos bp, int src) {
+  const int i = bp.x * kBlock + threadIdx.x;
+  if (i >= d.V) return;
+  const float4 p = d.phi[src][i], x = d.cg_x[i];
+  d.phi[1 - src][i] = make_float4(p.x + x.x, p.y + x.y, p.z + x.z, 0.f);
+}
+
+#define TRK_CG_KERNEL(name, impl, ...)                                                     \
+  __global__ void __launch_bounds__(kBlock) name(BatchGrid g, Dev d0 ARGS_##name) {         \
+    if (g.map == nullptr) {                                                                  \
+      impl(d0, grid_pos() CALL_##name);                                                      \
+      return;                                                                                \
+    }                                                                                        \
+    __shared__ Dev sd;                                                                       \
+    impl(sd, batch_block(g, sd) CALL_##name);                                                \
+  }
+#define ARGS_k_cg_init , int src, int slot
+#define CALL_k_cg_init , src, slot
+#define ARGS_k_cg_apply
+#define CALL_k_cg_apply
+#define ARGS_k_cg_update
+#define CALL_k_cg_update
+#define ARGS_k_cg_dir
+#define CALL_k_cg_dir
+#define ARGS_k_cg_finish , int src
+#define CALL_k_cg_finish , src
+TRK_CG_KERNEL(k_cg_init, cg_init_impl)
+TRK_CG_KERNEL(k_cg_apply, cg_apply_impl)
+TRK_CG_KERNEL(k_cg_update, cg_update_impl)
+TRK_CG_KERNEL(k_cg_dir, cg_dir_impl)
+TRK_CG_KERNEL(k_cg_finish, cg_finish_impl)
+
+// The whole coupled step (g, n: the block table and its size for a batch; kSingle and nblk_v alone).
+static void launch_shape_pcg(const BatchGrid& g, int n, const Dev& d0, int max_links, int iters, int src, int slot,
+                             cudaStream_t st) {
+  if (n <= 0) return;
+  k_cg_init<<<n, kBlock, max_links * sizeof(DQ), st>>>(g, d0, src, slot);
+  for (int k = 0; k < iters; ++k) {
+    k_cg_apply<<<n, kBlock, 0, st>>>(g, d0);
+    k_cg_update<<<n, kBlock, 0, st>>>(g, d0);
+    if (k + 1 < iters) k_cg_dir<<<n, kBlock, 0, st>>>(g, d0);
+  }
+  k_cg_finish<<<n, kBlock, 0, st>>>(g, d0, src);
+}
+
 // Returns the buffer that holds Phi after the step.
 int launch_shape(const Dev& d, int phi_src, int slot, cudaStream_t st) {
+  if (d.shape_solver == 1) {
+    launch_shape_pcg(kSingle, d.nblk_v, d, d.L, d.shape_sweeps, phi_src, slot, st);
+    return 1 - phi_src;
+  }
   k_shape<<<d.nblk_v, kBlock, d.L * sizeof(DQ), st>>>(kSingle, d, phi_src, slot);
   int cur = 1 - phi_src;
   for (int s = 1; s < d.shape_sweeps; ++s) {
@@ -1069,7 +1294,12 @@ void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int
   if (nv > 0) k_lm_eval<<<nv, kBlock, kCandidates * max_links * sizeof(DQ), st>>>(gv, Dev{}, phi_buf);
 }
 
-int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int phi_src, int slot, cudaStream_t st) {
+int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int solver, int phi_src, int slot,
+                   cudaStream_t st) {
+  if (solver == 1) {
+    launch_shape_pcg(gv, nv, Dev{}, max_links, sweeps, phi_src, slot, st);
+    return 1 - phi_src;
+  }
   if (nv > 0) k_shape<<<nv, kBlock, max_links * sizeof(DQ), st>>>(gv, Dev{}, phi_src, slot);
   int cur = 1 - phi_src;
   for (int s = 1; s < sweeps; ++s) {

@@ -166,6 +166,8 @@ trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsi
   if (p->precision != TRK_PRECISION_FP32 && p->precision != TRK_PRECISION_BF16X3 &&
       p->precision != TRK_PRECISION_TF32X3)
     return fail(TRK_ERR_INVALID_ARG, "precision %d not supported", p->precision);
+  if (p->shape_solver != 0 && p->shape_solver != 1)
+    return fail(TRK_ERR_INVALID_ARG, "shape_solver %d not supported", p->shape_solver);
   if (p->pose_iters < 0 || p->shape_iters < 0 || p->shape_sweeps < 1 || p->knn < 0 || p->knn > 4 ||
       p->window_half_px < 0 || !(p->cutoff_m > 0) || !(p->lambda_k0 > 0) || p->lambda_s < 0 || p->lambda_phi < 0 ||
       p->lambda_N < 0 || p->lambda_w < 0 || !(p->z_near_m > 0) || !(p->eps_vis_m >= 0))
@@ -344,6 +346,7 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   d.pose_iters = prm->pose_iters; d.shape_iters = prm->shape_iters; d.shape_sweeps = prm->shape_sweeps;
   d.knn = prm->knn;
   d.precision = prm->precision;
+  d.shape_solver = prm->shape_solver;
   d.lambda_phi = prm->lambda_phi; d.lambda_N = prm->lambda_N; d.lambda_w = prm->lambda_w;
   d.cam.W = W; d.cam.H = H; d.cam.fx = cam->fx; d.cam.fy = cam->fy; d.cam.cx = cam->cx; d.cam.cy = cam->cy;
   d.cam.z_near = prm->z_near_m; d.cam.eps_vis = prm->eps_vis_m; d.cam.tau = prm->cutoff_m; d.cam.R = prm->window_half_px;
@@ -416,6 +419,28 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   }
   std::vector<int> nbr;
   knn_grid(V, mesh->verts, prm->knn, nbr);
+  // neighbourhood edges in both directions (the coupled shape step), each list sorted
+  std::vector<int> adj_off(V + 1, 0), adj;
+  for (int i = 0; i < V; ++i)
+    for (int k = 0; k < 4; ++k) {
+      const int q = nbr[4 * (size_t)i + k];
+      if (q < 0) continue;
+      adj_off[i + 1]++;
+      adj_off[q + 1]++;
+    }
+  for (int i = 0; i < V; ++i) adj_off[i + 1] += adj_off[i];
+  adj.resize(std::max(adj_off[V], 1));
+  {
+    std::vector<int> fill(adj_off.begin(), adj_off.end() - 1);
+    for (int i = 0; i < V; ++i)
+      for (int k = 0; k < 4; ++k) {
+        const int q = nbr[4 * (size_t)i + k];
+        if (q < 0) continue;
+        adj[fill[i]++] = q;
+        adj[fill[q]++] = i;
+      }
+    for (int i = 0; i < V; ++i) std::sort(adj.begin() + adj_off[i], adj.begin() + adj_off[i + 1]);
+  }
   // ---- host staging of per-vertex / per-face arrays -----------------------------------------------
   std::vector<float4> v0(V), bw(V);
   std::vector<uchar4> bidx(V);
@@ -455,6 +480,13 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   TRY(dalloc(s, &d.head, npx)); TRY(dalloc(s, &d.zbuf, npx)); TRY(dalloc(s, &d.corr, npx));
   TRY(dalloc(s, &d.pixrec, npx)); TRY(dalloc(s, &d.queue, npx)); TRY(dalloc(s, &d.qctl, 4));
   TRY(dalloc(s, &d.acc, V)); TRY(dalloc(s, &d.vispix, V)); TRY(dalloc(s, &d.rg, V)); TRY(dalloc(s, &d.phi0, V));
+  int *dadj_off, *dadj;
+  TRY(dalloc(s, &dadj_off, V + 1)); TRY(dalloc(s, &dadj, adj.size()));
+  if (prm->shape_solver == 1) {
+    TRY(dalloc(s, &d.cg_x, V)); TRY(dalloc(s, &d.cg_r, V)); TRY(dalloc(s, &d.cg_z, V));
+    TRY(dalloc(s, &d.cg_p, V)); TRY(dalloc(s, &d.cg_ap, V));
+  }
+  TRY(dalloc(s, &d.cg, 4));
   float* ddepth;
   TRY(dalloc(s, &ddepth, npx));
   TRY(dalloc(s, &s->d_render, npx));
@@ -467,6 +499,8 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   d.links = dlt; d.v0 = dv0; d.bw = dbw; d.bidx = dbidx; d.tris = dtris; d.nbr = dnb;
   d.csr_off = dcsr_off; d.csr_face = dcsr_face; d.prior2 = dprior; d.phi[0] = phi0buf; d.phi[1] = phi1buf;
   d.depth = ddepth;
+  d.adj_off = dadj_off;
+  d.adj = dadj;
   CK(cudaMallocHost(&s->h_pinned, sizeof(double) * (L + prm->pose_iters + prm->shape_iters + 4)));
   cudaStream_t st = s->stream;
   CK(cudaMemcpyAsync(dlt, &lt, sizeof(lt), cudaMemcpyHostToDevice, st));
@@ -478,6 +512,9 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   CK(cudaMemcpyAsync(dcsr_off, csr_off.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, st));
   if (F) CK(cudaMemcpyAsync(dcsr_face, csr_face.data(), sizeof(int) * 3 * F, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dprior, prior2.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dadj_off, adj_off.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dadj, adj.data(), sizeof(int) * adj.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d.cg, 0, sizeof(double) * 4, st));
   CK(cudaMemsetAsync(d.counter, 0, sizeof(unsigned) * 4, st));
   CK(cudaMemsetAsync(d.qctl, 0, sizeof(unsigned) * 4, st));
   CK(cudaMemsetAsync(d.stats, 0, sizeof(int) * 4, st));
@@ -662,7 +699,8 @@ trk_status trk_get_info(trk_session* s, trk_info* out) {
   out->width = d.cam.W;
   out->height = d.cam.H;
   const int per_assoc = (d.F > 0 ? 5 : 4);  // skin, raster, visibility, associate (2 kernels)
-  out->kernels_per_frame = s->prm.pose_iters * (per_assoc + 4) + s->prm.shape_iters * (per_assoc + s->prm.shape_sweeps);
+  const int shape_k = s->prm.shape_solver == 1 ? 3 * s->prm.shape_sweeps + 1 : s->prm.shape_sweeps;
+  out->kernels_per_frame = s->prm.pose_iters * (per_assoc + 4) + s->prm.shape_iters * (per_assoc + shape_k);
   out->device_bytes = s->device_bytes;
   return TRK_OK;
 }

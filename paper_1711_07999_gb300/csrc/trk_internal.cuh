@@ -292,6 +292,11 @@ struct Dev {
   unsigned int* counter;  // [4] last-block tickets
   int* stats;             // [0] associated pixels, [1] associated vertices, [3] tensor-core wait ran out
   int precision;          // TRK_PRECISION_*: arithmetic of [J r]^T [J r]
+  int shape_solver;       // 0 Jacobi sweeps, 1 coupled PCG
+  const int* adj_off;     // [V + 1] neighbourhood edges of each vertex in both directions (CSR) ...
+  const int* adj;         // ... sorted by vertex index
+  float4 *cg_x, *cg_r, *cg_z, *cg_p, *cg_ap;  // [V] PCG vectors
+  double* cg;             // [4] rz, alpha, beta, stopped
 };
 
 }  // namespace trk
@@ -311,7 +316,8 @@ void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGr
                                int precision, int phi_buf, int slot, cudaStream_t st);
 void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int max_links, int phi_buf,
                  cudaStream_t st);
-int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int phi_src, int slot, cudaStream_t st);
+int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int solver, int phi_src, int slot,
+                   cudaStream_t st);
 
 // Position of a block within its session's grid.  The single-session kernels take it from blockIdx and
 // gridDim; the batched kernels (one launch over the blocks of many sessions) from a per-launch table.

@@ -60,7 +60,8 @@ class Params(C.Structure):
     _fields_ = [("pose_iters", C.c_int32), ("shape_iters", C.c_int32), ("shape_sweeps", C.c_int32),
                 ("lambda_k0", C.c_float), ("lambda_s", C.c_float), ("lambda_phi", C.c_float), ("lambda_N", C.c_float),
                 ("lambda_w", C.c_float), ("cutoff_m", C.c_float), ("eps_vis_m", C.c_float), ("z_near_m", C.c_float),
-                ("window_half_px", C.c_int32), ("knn", C.c_int32), ("precision", C.c_int32)]
+                ("window_half_px", C.c_int32), ("knn", C.c_int32), ("precision", C.c_int32),
+                ("shape_solver", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -169,7 +170,7 @@ def params_struct(p: dict) -> Params:
                   lambda_k0=p["lambda_k0"], lambda_s=p["lambda_s"], lambda_phi=p["lambda_phi"],
                   lambda_N=p["lambda_N"], lambda_w=p["lambda_w"], cutoff_m=p["cutoff"], eps_vis_m=p["eps_vis"],
                   z_near_m=p["z_near"], window_half_px=p["window_half"], knn=p["knn"],
-                  precision=p.get("precision", PRECISION_FP32))
+                  precision=p.get("precision", PRECISION_FP32), shape_solver=p.get("shape_solver", 0))
 
 
 class Session:

@@ -335,3 +335,4 @@ def test_smallest_meshes_and_ragged_sizes():
     (g, e_ref, th_ref, phi_ref, na_ref), = _track_both(m, o, depth, gt)
     assert np.abs(g["theta"] - th_ref).max() < 1e-3
     _assert_offsets_close(g["offsets"], phi_ref)
+
