@@ -20,6 +20,8 @@ Prints one JSON line (rank 0):
   uneven     --uneven-sessions sessions of random-tree bodies (5k-200k vertices, 12-40 bones, 320x240 to
              1280x720): frames/s one by one, on one stream each, as one fused batch (trk_batch_*), and
              under the schedule the autotuner picks (trk_schedule_*)
+  experiments  the paper's conditions (full tracking, shape-match, smooth-bind) on the sequence with its
+             ground truth: joint accuracy (AUC up to 10 cm) and reconstruction error
   roofline   the dominant kernel's achieved rate against the measured peak of MEASURED_PEAKS.json
   cpu_baseline  the FP64 oracle on the host, one core, a bounded sample of the same sequence
 --impl reference times the oracle itself (on host cores) on the same workload and metric.
@@ -551,6 +553,41 @@ def fused_rooflines(sess, frames, prof):
             "l2": "flushed before each stage", "stages": roof}
 
 
+def run_experiments(args, rank):
+    """The paper's experiment conditions (Sec. 5) on the synthetic sequence with its ground truth: full
+    tracking, shape-match and smooth-bind, each tracking the same frames from the true first pose.
+    Reported per condition: pose accuracy (area under the joint-accuracy curve up to 10 cm, mean joint
+    error) and reconstruction error (visible vertex to the nearest observed point)."""
+    from paper_1711_07999_gb300 import metrics, synth, trk
+    n = args.experiment_frames
+    out = {"frames": n, "auc_up_to_m": 0.1, "modes": {}}
+    for name, mode in (("track", trk.MODE_TRACK), ("shape_match", trk.MODE_SHAPE_MATCH),
+                       ("smooth_bind", trk.MODE_SMOOTH_BIND)):
+        model = synth.make_model(2, session=rank, mode=mode)
+        cam = model["camera"]
+        joints = metrics.joint_links(model["skeleton"])
+        errs, recon = [], []
+        with trk.Session(model) as s:
+            frames = render_sequence(model, s, n, seed=synth.seed_for(2, 800 + rank))
+            s.set_pose(synth.gt_theta(model, 0.0))
+            for f in range(n):
+                g = s.track_frame(frames[f], want_offsets=False)
+                gt = trk.joint_positions(model["skeleton"], synth.gt_theta(model, f / 30.0))[joints]
+                est = trk.joint_positions(model["skeleton"], g["theta"])[joints]
+                errs.append(metrics.joint_errors(est, gt))
+                verts = s.read("VERTS")[:, :3]
+                vis = s.read("VISPIX") >= 0
+                recon.append(metrics.reconstruction_error(verts, vis, frames[f], cam["fx"], cam["fy"], cam["cx"],
+                                                          cam["cy"]))
+        e = np.concatenate(errs)
+        r = np.concatenate(recon)
+        out["modes"][name] = {"joint_auc": round(metrics.auc(e, 0.1), 4), "joint_err_mean_mm": round(1e3 * e.mean(), 3),
+                              "joint_err_max_mm": round(1e3 * e.max(), 3),
+                              "recon_err_mean_mm": round(1e3 * r.mean(), 4),
+                              "recon_err_median_mm": round(1e3 * float(np.median(r)), 4)}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -689,6 +726,7 @@ def run_ours(args, rank, world, local_rank):
     if args.precision_modes and B > 1:
         precision = run_precision_modes(args, model, rank, dev, n_seq, flush, nA, NP, sample)
     uneven = run_uneven(args, rank, flush) if args.uneven_sessions > 0 else None
+    experiments = run_experiments(args, rank) if (args.experiment_frames > 0 and rank == 0) else None
     if rank == 0:
         plain = {"value": value, "ms_per_step": max_ms / args.steps,
                  "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
@@ -712,6 +750,7 @@ def run_ours(args, rank, world, local_rank):
             "batched": batched,
             "precision": precision,
             "uneven": uneven,
+            "experiments": experiments,
             "gpu_launches": info["kernels_per_frame"] * args.steps * (B if batched is not None else 1),
             "roofline": roof,
             "stage_ms": {k: round(v, 5) for k, v in prof.items()},
@@ -741,6 +780,8 @@ def main():
     ap.add_argument("--only", choices=["all", "plain", "uneven"], default="all",
                     help="plain: the one-session and batched measurements only; uneven: the uneven batch only")
     ap.add_argument("--uneven-modes", default="one_by_one,streams,fused,schedule")
+    ap.add_argument("--experiment-frames", type=int, default=30,
+                    help="frames of the sequence tracked in each of the paper's experiment conditions")
     ap.add_argument("--uneven-sessions", type=int, default=64,
                     help="sessions of the uneven batch (one by one / streams / fused batch / tuned schedule)")
     ap.add_argument("--precision-modes", type=int, default=1,
@@ -748,7 +789,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.only == "plain":
-        args.uneven_sessions, args.precision_modes = 0, 0
+        args.uneven_sessions, args.precision_modes, args.experiment_frames = 0, 0, 0
     rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank, world)

@@ -86,7 +86,16 @@ typedef struct {
                            sweeps); 1: the coupled damped Gauss-Newton system of the whole shape
                            energy by block-Jacobi-preconditioned conjugate gradients (shape_sweeps
                            iterations)                                                               */
+  int32_t mode;         /* TRK_MODE_*: which frames run the shape iterations (the paper's experiment
+                           conditions, Sec. 5)                                                       */
 } trk_params;
+
+/* TRACK: every frame estimates the shape (the full method).  SHAPE_MATCH: only the first frame after
+ * trk_set_pose does; Phi is frozen afterwards.  SMOOTH_BIND: no frame does (Phi stays as set).  A frame
+ * without shape iterations reports NaN for their energies. */
+#define TRK_MODE_TRACK 0
+#define TRK_MODE_SHAPE_MATCH 1
+#define TRK_MODE_SMOOTH_BIND 2
 
 /* Arithmetic of the contraction [J r]^T [J r] (Eqs. JTJ, JTr).  FP32: products and per-CTA sums on the
  * FP32 cores.  BF16X3 / TF32X3: every value of [J r] split as hi + lo (BF16 or TF32), the products
@@ -107,6 +116,12 @@ typedef struct {
   int32_t n_assoc_px;    /* pixels associated in the last association of the frame      */
   int32_t n_assoc_verts; /* vertices with at least one associated pixel, same pass      */
 } trk_result;
+
+/* The 3D position of every link's frame origin (its joint) in the camera frame for joint values theta,
+ * by forward kinematics in FP64 (Sec. 3.1: H_{0,j} = H_{0,P(j)} H_{P(j),j} J_j(theta_j)).  out: [n_links][3]
+ * metres.  Host only (no device call): the joint positions the pose-accuracy curves of Sec. 5 compare.
+ * Errors: TRK_ERR_INVALID_ARG (NULL arguments, a parent not before its child). */
+trk_status trk_fk_joint_positions(const trk_skeleton* sk, const double* theta, double* out);
 
 /* Creates a session on the current CUDA device: validates and copies the model, derives the bind pose
  * H^0 (Sec. 3.2), the prior weights S_kk = n_k/|V| (vertices weighted to the subtree of link k), the

@@ -174,6 +174,10 @@ trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_
         return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: a session appears twice");
       }
     const trk_params& p = session_params(s);
+    if (p.mode != TRK_MODE_TRACK) {
+      free_batch(b);
+      return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: batched sessions must be in TRK_MODE_TRACK");
+    }
     if (session_device(s) != b->device || p.pose_iters != b->pose_iters || p.shape_iters != b->shape_iters ||
         p.shape_sweeps != b->shape_sweeps || p.precision != b->precision || p.shape_solver != b->shape_solver) {
       free_batch(b);

@@ -121,7 +121,9 @@ struct trk_session {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t last_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;       // a frame with the shape iterations
+  cudaGraphExec_t graph_pose = nullptr;  // a frame of pose iterations only (shape-match after frame 0, smooth-bind)
+  int frames_done = 0;                   // frames since the last trk_set_pose
   trk_params prm{};
   std::vector<void*> allocs;
   size_t device_bytes = 0;
@@ -168,6 +170,8 @@ trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsi
     return fail(TRK_ERR_INVALID_ARG, "precision %d not supported", p->precision);
   if (p->shape_solver != 0 && p->shape_solver != 1)
     return fail(TRK_ERR_INVALID_ARG, "shape_solver %d not supported", p->shape_solver);
+  if (p->mode != TRK_MODE_TRACK && p->mode != TRK_MODE_SHAPE_MATCH && p->mode != TRK_MODE_SMOOTH_BIND)
+    return fail(TRK_ERR_INVALID_ARG, "mode %d not supported", p->mode);
   if (p->pose_iters < 0 || p->shape_iters < 0 || p->shape_sweeps < 1 || p->knn < 0 || p->knn > 4 ||
       p->window_half_px < 0 || !(p->cutoff_m > 0) || !(p->lambda_k0 > 0) || p->lambda_s < 0 || p->lambda_phi < 0 ||
       p->lambda_N < 0 || p->lambda_w < 0 || !(p->z_near_m > 0) || !(p->eps_vis_m >= 0))
@@ -202,10 +206,12 @@ trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsi
 }
 
 // Records the whole frame (pose iterations, then shape iterations) on st.
-void enqueue_frame(trk_session* s, cudaStream_t st) {
+void enqueue_frame(trk_session* s, cudaStream_t st, bool with_shape) {
   const Dev& d = s->d;
-  const int P = s->prm.pose_iters, S = s->prm.shape_iters;
+  const int P = s->prm.pose_iters, S = with_shape ? s->prm.shape_iters : 0;
   int cur = 0;
+  // a frame without shape iterations reports NaN for their energies (all-ones bytes are a NaN)
+  if (!with_shape && s->prm.shape_iters > 0) cudaMemsetAsync(d.energy + P, 0xFF, sizeof(double) * s->prm.shape_iters, st);
   for (int it = 0; it < P; ++it) {
     launch_skin(d, cur, st);
     launch_raster(d, st);
@@ -224,15 +230,26 @@ void enqueue_frame(trk_session* s, cudaStream_t st) {
   if (cur != 0) cudaMemcpyAsync(d.phi[0], d.phi[cur], sizeof(float4) * d.V, cudaMemcpyDeviceToDevice, st);
 }
 
-trk_status ensure_graph(trk_session* s) {
-  if (s->graph) return TRK_OK;
-  cudaGraph_t g = nullptr;
-  CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_frame(s, s->stream);
-  CK(cudaStreamEndCapture(s->stream, &g));
-  cudaError_t e = cudaGraphInstantiate(&s->graph, g, 0);
-  cudaGraphDestroy(g);
-  CK(e);
+// Whether the next frame runs the shape iterations: always in tracking mode, on the first frame after
+// trk_set_pose in shape-match mode, never in smooth-bind mode.
+bool next_frame_with_shape(const trk_session* s) {
+  return s->prm.mode == TRK_MODE_TRACK || (s->prm.mode == TRK_MODE_SHAPE_MATCH && s->frames_done == 0);
+}
+
+// The frame graph for the next frame (captured on first use).
+trk_status frame_graph(trk_session* s, cudaGraphExec_t* out) {
+  const bool with_shape = next_frame_with_shape(s);
+  cudaGraphExec_t& ge = with_shape ? s->graph : s->graph_pose;
+  if (!ge) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_frame(s, s->stream, with_shape);
+    CK(cudaStreamEndCapture(s->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+  }
+  *out = ge;
   return TRK_OK;
 }
 
@@ -288,10 +305,12 @@ void session_result_sizes(const trk_session* s, int* n_links, int* n_verts, int*
 }
 // H2D of the frame's depth and the frame graph, on the session's stream
 trk_status session_enqueue_frame(trk_session* s, const float* host_depth, cudaStream_t* stream_out) {
-  TRY(ensure_graph(s));
+  cudaGraphExec_t ge;
+  TRY(frame_graph(s, &ge));
   CK(cudaMemcpyAsync(const_cast<float*>(s->d.depth), host_depth, sizeof(float) * s->d.cam.W * s->d.cam.H,
                      cudaMemcpyHostToDevice, s->stream));
-  CK(cudaGraphLaunch(s->graph, s->stream));
+  CK(cudaGraphLaunch(ge, s->stream));
+  ++s->frames_done;
   s->last_stream = s->stream;
   *stream_out = s->stream;
   return TRK_OK;
@@ -319,6 +338,7 @@ void trk_destroy(trk_session* s) {
   cudaSetDevice(s->device);
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->graph_pose) cudaGraphExecDestroy(s->graph_pose);
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_pinned) cudaFreeHost(s->h_pinned);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -529,11 +549,46 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   return TRK_OK;
 }
 
+trk_status trk_fk_joint_positions(const trk_skeleton* sk, const double* theta, double* out) {
+  if (!sk || !theta || !out || sk->n_links < 1 || sk->n_links > TRK_MAX_LINKS || !sk->parent || !sk->type ||
+      !sk->axis || !sk->offset_dq)
+    return fail(TRK_ERR_INVALID_ARG, "trk_fk_joint_positions: bad arguments");
+  const int L = sk->n_links;
+  std::vector<HDQ> H(L);
+  for (int j = 0; j < L; ++j) {
+    const int p = sk->parent[j];
+    if (p >= j) return fail(TRK_ERR_INVALID_ARG, "trk_fk_joint_positions: parent %d of link %d", p, j);
+    const float* a = sk->axis + 3 * j;
+    const double an = std::sqrt((double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2]);
+    const double ax = a[0] / an, ay = a[1] / an, az = a[2] / an;
+    HDQ J{{1, 0, 0, 0}, {0, 0, 0, 0}};
+    if (sk->type[j] == 0) {  // hinge: rotation by theta about the axis
+      const double c = std::cos(0.5 * theta[j]), sn = std::sin(0.5 * theta[j]);
+      J.r = {c, sn * ax, sn * ay, sn * az};
+    } else {  // prismatic: translation by theta along the axis
+      J.d = {0, 0.5 * theta[j] * ax, 0.5 * theta[j] * ay, 0.5 * theta[j] * az};
+    }
+    const float* o = sk->offset_dq + 8 * j;
+    const HDQ off{{o[0], o[1], o[2], o[3]}, {o[4], o[5], o[6], o[7]}};
+    const HDQ base = p < 0 ? HDQ{{1, 0, 0, 0}, {0, 0, 0, 0}} : H[p];
+    H[j] = hdmul(hdmul(base, off), J);
+    // translation of a unit dual quaternion: 2 vec(d r*)
+    const HQ rc{H[j].r.w, -H[j].r.x, -H[j].r.y, -H[j].r.z};
+    const HQ t = hmul(H[j].d, rc);
+    const double n2 = H[j].r.w * H[j].r.w + H[j].r.x * H[j].r.x + H[j].r.y * H[j].r.y + H[j].r.z * H[j].r.z;
+    out[3 * j] = 2 * t.x / n2;
+    out[3 * j + 1] = 2 * t.y / n2;
+    out[3 * j + 2] = 2 * t.z / n2;
+  }
+  return TRK_OK;
+}
+
 trk_status trk_set_pose(trk_session* s, const double* theta, const float* offsets) {
   if (!s || !theta) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
   Dev& d = s->d;
   for (int j = 0; j < d.L; ++j)
     if (!std::isfinite(theta[j])) return fail(TRK_ERR_NUMERIC, "theta[%d] not finite", j);
+  s->frames_done = 0;  // a new sequence starts (shape-match fits the shape on its first frame)
   std::vector<float4> phi(d.V, make_float4(0.f, 0.f, 0.f, 0.f));
   if (offsets)
     for (int i = 0; i < d.V; ++i) {
@@ -551,11 +606,13 @@ trk_status trk_set_pose(trk_session* s, const double* theta, const float* offset
 
 trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out) {
   if (!s || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
-  TRY(ensure_graph(s));
+  cudaGraphExec_t ge;
+  TRY(frame_graph(s, &ge));
   const Dev& d = s->d;
   CK(cudaMemcpyAsync(const_cast<float*>(d.depth), depth_m, sizeof(float) * d.cam.W * d.cam.H, cudaMemcpyHostToDevice,
                      s->stream));
-  CK(cudaGraphLaunch(s->graph, s->stream));
+  CK(cudaGraphLaunch(ge, s->stream));
+  ++s->frames_done;
   s->last_stream = s->stream;
   TRY(fetch_result(s, s->stream, out));
   return sync_check(s);
@@ -563,12 +620,14 @@ trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out
 
 trk_status trk_track_frame_device(trk_session* s, const float* d_depth_m, void* cuda_stream) {
   if (!s || !d_depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
-  TRY(ensure_graph(s));
+  cudaGraphExec_t ge;
+  TRY(frame_graph(s, &ge));
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : s->stream;
   const Dev& d = s->d;
   CK(cudaMemcpyAsync(const_cast<float*>(d.depth), d_depth_m, sizeof(float) * d.cam.W * d.cam.H,
                      cudaMemcpyDeviceToDevice, st));
-  CK(cudaGraphLaunch(s->graph, st));
+  CK(cudaGraphLaunch(ge, st));
+  ++s->frames_done;
   CK(cudaGetLastError());
   s->last_stream = st;
   return TRK_OK;

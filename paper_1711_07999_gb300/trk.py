@@ -16,6 +16,7 @@ LIB_PATH = _build.LIB
 TRK_OK, TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA, TRK_ERR_NO_CAPACITY, TRK_ERR_TIMEOUT, TRK_ERR_NUMERIC = range(7)
 MAX_LINKS = 79
 PRECISION_FP32, PRECISION_BF16X3, PRECISION_TF32X3 = 0, 1, 2
+MODE_TRACK, MODE_SHAPE_MATCH, MODE_SMOOTH_BIND = 0, 1, 2
 
 FIELDS = dict(VERTS=0, NORMALS=1, ZBUF=2, VISPIX=3, CORR=4, ACC=5, NORMAL_EQ=6, THETA=7, PHI=8, LAMBDA=9, ENERGY=10,
               LM_TRIALS=11, SHAPE_RG=12, NEIGHBOURS=13, PRIOR=14, LM_SOLVER=15)
@@ -25,7 +26,7 @@ EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_dev
            "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
            "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc",
-           "trk_jtj_rows_tc", "trk_batch_create", "trk_batch_track_device", "trk_batch_profile",
+           "trk_jtj_rows_tc", "trk_fk_joint_positions", "trk_batch_create", "trk_batch_track_device", "trk_batch_profile",
            "trk_batch_destroy",
            "trk_schedule_create", "trk_schedule_track_device", "trk_schedule_get_config", "trk_schedule_autotune",
            "trk_schedule_destroy", "trk_schedule_signature", "trk_tuning_cache_lookup", "trk_tuning_cache_store",
@@ -61,7 +62,7 @@ class Params(C.Structure):
                 ("lambda_k0", C.c_float), ("lambda_s", C.c_float), ("lambda_phi", C.c_float), ("lambda_N", C.c_float),
                 ("lambda_w", C.c_float), ("cutoff_m", C.c_float), ("eps_vis_m", C.c_float), ("z_near_m", C.c_float),
                 ("window_half_px", C.c_int32), ("knn", C.c_int32), ("precision", C.c_int32),
-                ("shape_solver", C.c_int32)]
+                ("shape_solver", C.c_int32), ("mode", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -106,6 +107,7 @@ def lib(build_if_missing: bool = True):
             "trk_read": [vp, i32, vp, sz], "trk_get_info": [vp, vp], "trk_profile_iteration": [vp, i32, sz, vp],
             "trk_jtj_rows": [vp, i32, i32, i32, vp, vp], "trk_jtj_rows_noalloc": [vp, i32, i32, i32, vp, vp],
             "trk_jtj_rows_tc": [vp, i32, i32, i32, i32, vp, vp],
+            "trk_fk_joint_positions": [vp, vp, vp],
             "trk_batch_create": [C.POINTER(vp), i32, C.POINTER(vp)], "trk_batch_track_device": [vp, C.POINTER(vp), vp],
             "trk_batch_profile": [vp, C.POINTER(vp), i32, sz, vp],
             "trk_schedule_create": [C.POINTER(vp), i32, vp, C.c_char_p, C.POINTER(vp)],
@@ -165,12 +167,29 @@ def jtj_rows_tc(rows_ptr: int, n_rows: int, n_cols: int, ld: int, precision: int
                                  C.c_void_p(stream_ptr or None)))
 
 
+def joint_positions(skeleton: dict, theta) -> np.ndarray:
+    """[n_links, 3] camera-frame joint positions (each link's frame origin) for joint values theta
+    (trk_fk_joint_positions: FP64 forward kinematics on the host)."""
+    parent = np.ascontiguousarray(skeleton["parent"], np.int32)
+    typ = np.ascontiguousarray(skeleton["type"], np.int32)
+    axis = np.ascontiguousarray(skeleton["axis"], np.float32)
+    off = np.ascontiguousarray(skeleton["offset_dq"], np.float32)
+    mask = np.ascontiguousarray(skeleton["prior_mask"], np.float32)
+    L = len(parent)
+    sk = Skeleton(L, _p(parent), _p(typ), _p(axis), _p(off), _p(mask))
+    th = np.ascontiguousarray(theta, np.float64)
+    out = np.empty((L, 3))
+    _check(lib().trk_fk_joint_positions(C.byref(sk), _p(th), _p(out)))
+    return out
+
+
 def params_struct(p: dict) -> Params:
     return Params(pose_iters=p["pose_iters"], shape_iters=p["shape_iters"], shape_sweeps=p["shape_sweeps"],
                   lambda_k0=p["lambda_k0"], lambda_s=p["lambda_s"], lambda_phi=p["lambda_phi"],
                   lambda_N=p["lambda_N"], lambda_w=p["lambda_w"], cutoff_m=p["cutoff"], eps_vis_m=p["eps_vis"],
                   z_near_m=p["z_near"], window_half_px=p["window_half"], knn=p["knn"],
-                  precision=p.get("precision", PRECISION_FP32), shape_solver=p.get("shape_solver", 0))
+                  precision=p.get("precision", PRECISION_FP32), shape_solver=p.get("shape_solver", 0),
+                  mode=p.get("mode", MODE_TRACK))
 
 
 class Session:
