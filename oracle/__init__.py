@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("window_half", C.c_int32), ("knn", C.c_int32), ("shape_solver", C.c_int32),
                 ("lambda_k0", C.c_double), ("lambda_s", C.c_double), ("lambda_phi", C.c_double),
                 ("lambda_N", C.c_double), ("lambda_w", C.c_double), ("cutoff", C.c_double),
-                ("eps_vis", C.c_double), ("z_near", C.c_double)]
+                ("eps_vis", C.c_double), ("z_near", C.c_double), ("association", C.c_int32), ("pad2_", C.c_int32)]
 
 
 def _P(t):
@@ -64,6 +64,7 @@ def lib():
             "orc_raster": (None, [ci, ci, cd, cd, cd, cd, cd, ci, f64, ci, i32, f64, i32, vp]),
             "orc_visibility": (None, [vp, f64, f64, i32, f64, vp, i32, i32, vp]),
             "orc_associate": (None, [vp, f64, i32, i32, vp, f32, i32, f64, i32, vp]),
+            "orc_associate_rid": (None, [vp, f64, i32, vp, f32, i32, f64, i32, vp]),
             "orc_accumulate": (None, [vp, f64, f32, i32, f64, i32]),
             "orc_residuals": (cd, [vp, f64, f64, i32, f64, i32, f64, i32]),
             "orc_jacobian": (None, [vp, f64, f64, f64, i32, f64]),
@@ -146,7 +147,8 @@ class Oracle:
                    window_half=pr["window_half"], knn=pr["knn"], shape_solver=pr.get("shape_solver", 0),
                    lambda_k0=pr["lambda_k0"],
                    lambda_s=pr["lambda_s"], lambda_phi=pr["lambda_phi"], lambda_N=pr["lambda_N"],
-                   lambda_w=pr["lambda_w"], cutoff=pr["cutoff"], eps_vis=pr["eps_vis"], z_near=pr["z_near"])
+                   lambda_w=pr["lambda_w"], cutoff=pr["cutoff"], eps_vis=pr["eps_vis"], z_near=pr["z_near"],
+                   association=pr.get("association", 0), pad2_=0)
         self._keep = dict(
             parent=np.ascontiguousarray(sk["parent"], np.int32), type=np.ascontiguousarray(sk["type"], np.int32),
             axis=np.ascontiguousarray(sk["axis"], np.float32), off=np.ascontiguousarray(sk["offset_dq"], np.float32),
@@ -225,6 +227,17 @@ class Oracle:
         lib().orc_associate(self.h, np.ascontiguousarray(v, np.float64), np.ascontiguousarray(vis, np.int32),
                             np.ascontiguousarray(pix, np.int32), _ptr(mg),
                             np.ascontiguousarray(depth, np.float32).ravel(), corr, acc, cnt, _ptr(tie))
+        return corr.reshape(self.H, self.W), acc, cnt, None if tie is None else tie.reshape(self.H, self.W)
+
+    def associate_rid(self, v, ztri, depth, zamb=None, with_tie=False):
+        """Raster-ID association (R23): nearest corner of the triangle the z-buffer holds at the pixel."""
+        corr = np.empty(self.W * self.H, np.int32)
+        acc = np.empty((self.V, 3))
+        cnt = np.empty(self.V, np.int32)
+        tie = np.empty(self.W * self.H, np.int32) if with_tie else None
+        za = None if zamb is None else np.ascontiguousarray(zamb, np.int32).ravel()
+        lib().orc_associate_rid(self.h, np.ascontiguousarray(v, np.float64), np.ascontiguousarray(ztri, np.int32).ravel(),
+                                _ptr(za), np.ascontiguousarray(depth, np.float32).ravel(), corr, acc, cnt, _ptr(tie))
         return corr.reshape(self.H, self.W), acc, cnt, None if tie is None else tie.reshape(self.H, self.W)
 
     def accumulate(self, v, depth, corr):

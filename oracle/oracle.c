@@ -19,6 +19,7 @@
  *   R9  association window half-size W and cutoff tau are parameters
  *   R10 pose prior weight S_kk = n_k/|V| (n_k = vertices weighted to the subtree of link k), times a mask
  *   R22 the coupled shape step: the whole shape energy's damped Gauss-Newton system, solved by PCG
+ *   R23 raster-ID association: the nearest corner of the triangle rasterised at the pixel
  *   R12 derivative block of link j's offset w.r.t. theta_k uses the chain from k to j (no double count)
  *   R13 LM damping uses diag of the prior-augmented matrix; a parameter with zero diagonal is frozen
  *   R14 LM schedule: lambda x10 on reject (<= 5 retries, energy at fixed association), /10 on accept
@@ -135,6 +136,7 @@ static void q_to_rot(quat q, double* R) {
 typedef struct {
   int32_t pose_iters, shape_iters, shape_sweeps, window_half, knn, shape_solver; /* 0 Jacobi (R15), 1 PCG (R22) */
   double lambda_k0, lambda_s, lambda_phi, lambda_N, lambda_w, cutoff, eps_vis, z_near;
+  int32_t association, pad2_; /* 0 window search (Sec. 4.1), 1 nearest corner of the rasterised triangle (R23) */
 } orc_params;
 
 typedef struct {
@@ -574,6 +576,49 @@ void orc_associate(void* h, const double* v, const int32_t* vis, const int32_t* 
       }
     }
   free(start); free(list); free(fill); free(mstart); free(mlist);
+}
+
+/* R23: the raster-ID association.  Each valid pixel back-projects to p_k and takes the nearest corner
+ * (squared distance, ties to the smaller index) of the triangle the z-buffer holds at that pixel, within
+ * the cutoff; a pixel the model does not cover gets none.  O(1) per pixel instead of the window search.
+ * tie (optional): 1 where the z-buffer decision there is marginal (zamb from orc_raster), where two corners
+ * are within 1e-5 m of each other, or where the best corner is within 1e-5 m of the cutoff. */
+void orc_associate_rid(void* h, const double* v, const int32_t* ztri, const int32_t* zamb, const float* depth,
+                       int32_t* corr, double* acc, int32_t* cnt, int32_t* tie) {
+  orc_model* m = (orc_model*)h;
+  const double tau = m->p.cutoff, tau2 = tau * tau, tol = 1e-5;
+  for (int i = 0; i < m->V; ++i) { acc[3 * i] = acc[3 * i + 1] = acc[3 * i + 2] = 0; cnt[i] = 0; }
+  for (int py = 0; py < m->H; ++py)
+    for (int px = 0; px < m->W; ++px) {
+      const int k = py * m->W + px;
+      corr[k] = -1;
+      if (tie) tie[k] = zamb ? zamb[k] : 0;
+      const double d = depth[k];
+      if (!(d > 0) || ztri[k] < 0) continue;
+      const double p[3] = {(px - m->cx) * d / m->fx, (py - m->cy) * d / m->fy, d};
+      const int* t = m->tri + 3 * (size_t)ztri[k];
+      int best = -1;
+      double bd2 = 0, dist[3];
+      for (int c = 0; c < 3; ++c) {
+        const int i = t[c];
+        const double dx = p[0] - v[3 * i], dy = p[1] - v[3 * i + 1], dz = p[2] - v[3 * i + 2];
+        const double dd = dx * dx + dy * dy + dz * dz;
+        dist[c] = sqrt(dd);
+        if (dd <= tau2 && (best < 0 || dd < bd2 || (dd == bd2 && i < best))) { best = i; bd2 = dd; }
+      }
+      if (tie) {
+        for (int c = 0; c < 3; ++c) {
+          if (fabs(dist[c] - tau) < tol) tie[k] = 1;
+          for (int e = c + 1; e < 3; ++e)
+            if (fabs(dist[c] - dist[e]) < tol && fmin(dist[c], dist[e]) <= tau + tol) tie[k] = 1;
+        }
+      }
+      corr[k] = best;
+      if (best >= 0) {
+        for (int c = 0; c < 3; ++c) acc[3 * best + c] += p[c] - v[3 * best + c];
+        cnt[best] += 1;
+      }
+    }
 }
 
 /* Given a correspondence map (from any source), the per-vertex sums of Sec. 4.1. */
@@ -1020,7 +1065,10 @@ static double associate_pass(orc_model* m, orc_ws* w, const float* depth) {
   orc_normals(m->V, m->F, m->tri, w->v, w->n, w->nvalid);
   orc_raster(m->W, m->H, m->fx, m->fy, m->cx, m->cy, m->p.z_near, m->V, w->v, m->F, m->tri, w->z, w->ztri, NULL);
   orc_visibility(m, w->v, w->n, w->nvalid, w->z, NULL, w->vis, w->pix, NULL);
-  orc_associate(m, w->v, w->vis, w->pix, NULL, depth, w->corr, w->acc, w->cnt, NULL);
+  if (m->p.association == 1)
+    orc_associate_rid(m, w->v, w->ztri, NULL, depth, w->corr, w->acc, w->cnt, NULL);
+  else
+    orc_associate(m, w->v, w->vis, w->pix, NULL, depth, w->corr, w->acc, w->cnt, NULL);
   return orc_residuals(m, m->theta, w->n, w->nvalid, w->acc, w->cnt, w->r, w->inA);
 }
 

@@ -1,0 +1,71 @@
+"""Pins of the oracle's raster-ID association (reading R23: a pixel takes the nearest corner of the
+triangle the z-buffer holds there)."""
+import numpy as np
+
+import oracle
+from paper_1711_07999_gb300 import synth
+
+
+def _setup(seed=4, V=3000):
+    m = synth.make_model(1, V=V, width=96)
+    o = oracle.Oracle(m)
+    gt = synth.gt_theta(m, 0)
+    depth = synth.add_noise(o.render(gt, synth.gt_offsets(m, 0)), 1, np.random.default_rng(seed))
+    P = o.pass_at(gt, None, depth)
+    return m, o, gt, depth, P
+
+
+def test_each_pixel_takes_the_nearest_corner_of_its_triangle():
+    m, o, gt, depth, P = _setup()
+    corr, acc, cnt, _ = o.associate_rid(P["v"], P["ztri"], depth)
+    tri = np.asarray(m["mesh"]["tris"])
+    H, W = depth.shape
+    fx, fy, cx, cy = (m["camera"][k] for k in ("fx", "fy", "cx", "cy"))
+    tau = m["params"]["cutoff"]
+    ys, xs = np.nonzero(depth > 0)
+    for py, px in list(zip(ys, xs))[::7]:
+        t = P["ztri"][py, px]
+        if t < 0:
+            assert corr[py, px] == -1
+            continue
+        z = float(depth[py, px])
+        p = np.array([(px - cx) * z / fx, (py - cy) * z / fy, z])
+        d2 = ((P["v"][tri[t]] - p) ** 2).sum(1)
+        c = [(d2[k], tri[t][k]) for k in range(3) if d2[k] <= tau * tau]
+        assert corr[py, px] == (min(c)[1] if c else -1)
+    # the sums are those of the map
+    acc2, cnt2 = o.accumulate(P["v"], depth, corr)
+    assert np.array_equal(cnt, cnt2) and np.allclose(acc, acc2, rtol=0, atol=1e-12)
+
+
+def test_never_closer_than_the_window_search():
+    # the window search returns the nearest visible vertex in the window; a corner of the rasterised
+    # triangle that is visible and inside the window is one of its candidates, so the raster-ID
+    # correspondence is never strictly closer than the window search's
+    m, o, gt, depth, P = _setup(seed=6)
+    corr_w = P["corr"]
+    corr_r, _, _, _ = o.associate_rid(P["v"], P["ztri"], depth)
+    H, W = depth.shape
+    fx, fy, cx, cy = (m["camera"][k] for k in ("fx", "fy", "cx", "cy"))
+    R = m["params"]["window_half"]
+    n_equal = n_both = 0
+    for py, px in zip(*np.nonzero((corr_w >= 0) & (corr_r >= 0))):
+        i_r, i_w = corr_r[py, px], corr_w[py, px]
+        pix = P["pix"][i_r]
+        if not P["vis"][i_r] or abs(pix % W - px) > R or abs(pix // W - py) > R:
+            continue
+        z = float(depth[py, px])
+        p = np.array([(px - cx) * z / fx, (py - cy) * z / fy, z])
+        d_r = ((P["v"][i_r] - p) ** 2).sum()
+        d_w = ((P["v"][i_w] - p) ** 2).sum()
+        assert d_w <= d_r
+        n_both += 1
+        n_equal += i_r == i_w
+    assert n_both > 200 and n_equal > 0.5 * n_both, (n_both, n_equal)
+
+
+def test_uncovered_pixels_get_no_correspondence():
+    m, o, gt, depth, P = _setup(seed=8)
+    ztri = np.full_like(P["ztri"], -1)
+    corr, acc, cnt, _ = o.associate_rid(P["v"], ztri, depth)
+    assert np.all(corr == -1) and np.all(cnt == 0)
