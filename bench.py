@@ -555,15 +555,16 @@ def fused_rooflines(sess, frames, prof):
 
 def run_experiments(args, rank):
     """The paper's experiment conditions (Sec. 5) on the synthetic sequence with its ground truth: full
-    tracking, shape-match and smooth-bind, each tracking the same frames from the true first pose.
-    Reported per condition: pose accuracy (area under the joint-accuracy curve up to 10 cm, mean joint
-    error) and reconstruction error (visible vertex to the nearest observed point)."""
+    tracking, shape-match and smooth-bind, each tracking the same frames from the true first pose, and full
+    tracking with the raster-ID association (accuracy against cost).  Reported per condition: pose accuracy
+    (area under the joint-accuracy curve up to 10 cm, mean joint error), reconstruction error (visible
+    vertex to the nearest observed point) and the association stage's time (CUDA events, cold L2)."""
     from paper_1711_07999_gb300 import metrics, synth, trk
     n = args.experiment_frames
     out = {"frames": n, "auc_up_to_m": 0.1, "modes": {}}
-    for name, mode in (("track", trk.MODE_TRACK), ("shape_match", trk.MODE_SHAPE_MATCH),
-                       ("smooth_bind", trk.MODE_SMOOTH_BIND)):
-        model = synth.make_model(2, session=rank, mode=mode)
+    for name, mode, assoc in (("track", trk.MODE_TRACK, 0), ("shape_match", trk.MODE_SHAPE_MATCH, 0),
+                              ("smooth_bind", trk.MODE_SMOOTH_BIND, 0), ("track_raster_id", trk.MODE_TRACK, 1)):
+        model = synth.make_model(2, session=rank, mode=mode, association=assoc)
         cam = model["camera"]
         joints = metrics.joint_links(model["skeleton"])
         errs, recon = [], []
@@ -579,12 +580,15 @@ def run_experiments(args, rank):
                 vis = s.read("VISPIX") >= 0
                 recon.append(metrics.reconstruction_error(verts, vis, frames[f], cam["fx"], cam["fy"], cam["cx"],
                                                           cam["cy"]))
+            s.set_depth(frames[0])
+            prof = s.profile_iteration(reps=5, flush_bytes=L2_FLUSH_BYTES)
         e = np.concatenate(errs)
         r = np.concatenate(recon)
         out["modes"][name] = {"joint_auc": round(metrics.auc(e, 0.1), 4), "joint_err_mean_mm": round(1e3 * e.mean(), 3),
                               "joint_err_max_mm": round(1e3 * e.max(), 3),
                               "recon_err_mean_mm": round(1e3 * r.mean(), 4),
-                              "recon_err_median_mm": round(1e3 * float(np.median(r)), 4)}
+                              "recon_err_median_mm": round(1e3 * float(np.median(r)), 4),
+                              "associate_ms": round(prof["associate"], 5)}
     return out
 
 

@@ -88,6 +88,8 @@ typedef struct {
                            iterations)                                                               */
   int32_t mode;         /* TRK_MODE_*: which frames run the shape iterations (the paper's experiment
                            conditions, Sec. 5)                                                       */
+  int32_t association;  /* 0: the closest visible vertex in the window (Sec. 4.1); 1: the nearest
+                           corner of the triangle the z-buffer holds at the pixel (O(1) per pixel)   */
 } trk_params;
 
 /* TRACK: every frame estimates the shape (the full method).  SHAPE_MATCH: only the first frame after

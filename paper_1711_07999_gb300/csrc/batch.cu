@@ -179,10 +179,11 @@ trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_
       return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: batched sessions must be in TRK_MODE_TRACK");
     }
     if (session_device(s) != b->device || p.pose_iters != b->pose_iters || p.shape_iters != b->shape_iters ||
-        p.shape_sweeps != b->shape_sweeps || p.precision != b->precision || p.shape_solver != b->shape_solver) {
+        p.shape_sweeps != b->shape_sweeps || p.precision != b->precision || p.shape_solver != b->shape_solver ||
+        p.association != session_params(sessions[0]).association) {
       free_batch(b);
       return set_error(TRK_ERR_INVALID_ARG,
-                       "trk_batch_create: sessions differ in device, iteration schedule, precision or shape solver");
+                       "trk_batch_create: sessions differ in device, schedule, precision, shape solver or association");
     }
     const Dev& d = session_dev(s);
     b->max_links = std::max(b->max_links, d.L);

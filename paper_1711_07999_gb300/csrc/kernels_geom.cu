@@ -298,7 +298,17 @@ __device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
   float bd2 = 0.f;
   float3 p = make_float3(0.f, 0.f, 0.f);
   bool open = false;
-  if (dep > 0.f) {
+  if (dep > 0.f && d.association == 1) {
+    // the nearest corner of the triangle the z-buffer holds at this pixel (O(1), no queue)
+    p = back_project(c, px, py, dep);
+    const unsigned long long key = d.zbuf[k];
+    if (key != ~0ull) {
+      const int4 t = d.tris[(int)(unsigned)(key & 0xffffffffu)];
+      consider(t.x, p, d.v[t.x], tau2, best, bd2);
+      consider(t.y, p, d.v[t.y], tau2, best, bd2);
+      consider(t.z, p, d.v[t.z], tau2, best, bd2);
+    }
+  } else if (dep > 0.f) {
     p = back_project(c, px, py, dep);
     open = true;
     for (int r = 0; r <= min(c.R, kRingsPerThread); ++r) {

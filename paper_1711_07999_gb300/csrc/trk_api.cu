@@ -172,6 +172,8 @@ trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsi
     return fail(TRK_ERR_INVALID_ARG, "shape_solver %d not supported", p->shape_solver);
   if (p->mode != TRK_MODE_TRACK && p->mode != TRK_MODE_SHAPE_MATCH && p->mode != TRK_MODE_SMOOTH_BIND)
     return fail(TRK_ERR_INVALID_ARG, "mode %d not supported", p->mode);
+  if (p->association != 0 && p->association != 1)
+    return fail(TRK_ERR_INVALID_ARG, "association %d not supported", p->association);
   if (p->pose_iters < 0 || p->shape_iters < 0 || p->shape_sweeps < 1 || p->knn < 0 || p->knn > 4 ||
       p->window_half_px < 0 || !(p->cutoff_m > 0) || !(p->lambda_k0 > 0) || p->lambda_s < 0 || p->lambda_phi < 0 ||
       p->lambda_N < 0 || p->lambda_w < 0 || !(p->z_near_m > 0) || !(p->eps_vis_m >= 0))
@@ -367,6 +369,7 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   d.knn = prm->knn;
   d.precision = prm->precision;
   d.shape_solver = prm->shape_solver;
+  d.association = prm->association;
   d.lambda_phi = prm->lambda_phi; d.lambda_N = prm->lambda_N; d.lambda_w = prm->lambda_w;
   d.cam.W = W; d.cam.H = H; d.cam.fx = cam->fx; d.cam.fy = cam->fy; d.cam.cx = cam->cx; d.cam.cy = cam->cy;
   d.cam.z_near = prm->z_near_m; d.cam.eps_vis = prm->eps_vis_m; d.cam.tau = prm->cutoff_m; d.cam.R = prm->window_half_px;

@@ -293,6 +293,7 @@ struct Dev {
   int* stats;             // [0] associated pixels, [1] associated vertices, [3] tensor-core wait ran out
   int precision;          // TRK_PRECISION_*: arithmetic of [J r]^T [J r]
   int shape_solver;       // 0 Jacobi sweeps, 1 coupled PCG
+  int association;        // 0 window search, 1 nearest corner of the rasterised triangle
   const int* adj_off;     // [V + 1] neighbourhood edges of each vertex in both directions (CSR) ...
   const int* adj;         // ... sorted by vertex index
   float4 *cg_x, *cg_r, *cg_z, *cg_p, *cg_ap;  // [V] PCG vectors

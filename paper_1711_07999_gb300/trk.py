@@ -62,7 +62,7 @@ class Params(C.Structure):
                 ("lambda_k0", C.c_float), ("lambda_s", C.c_float), ("lambda_phi", C.c_float), ("lambda_N", C.c_float),
                 ("lambda_w", C.c_float), ("cutoff_m", C.c_float), ("eps_vis_m", C.c_float), ("z_near_m", C.c_float),
                 ("window_half_px", C.c_int32), ("knn", C.c_int32), ("precision", C.c_int32),
-                ("shape_solver", C.c_int32), ("mode", C.c_int32)]
+                ("shape_solver", C.c_int32), ("mode", C.c_int32), ("association", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -189,7 +189,7 @@ def params_struct(p: dict) -> Params:
                   lambda_N=p["lambda_N"], lambda_w=p["lambda_w"], cutoff_m=p["cutoff"], eps_vis_m=p["eps_vis"],
                   z_near_m=p["z_near"], window_half_px=p["window_half"], knn=p["knn"],
                   precision=p.get("precision", PRECISION_FP32), shape_solver=p.get("shape_solver", 0),
-                  mode=p.get("mode", MODE_TRACK))
+                  mode=p.get("mode", MODE_TRACK), association=p.get("association", 0))
 
 
 class Session:
