@@ -65,6 +65,8 @@ def lib():
             "orc_visibility": (None, [vp, f64, f64, i32, f64, vp, i32, i32, vp]),
             "orc_associate": (None, [vp, f64, i32, i32, vp, f32, i32, f64, i32, vp]),
             "orc_associate_rid": (None, [vp, f64, i32, vp, f32, i32, f64, i32, vp]),
+            "orc_subdivide_counts": (None, [ci, ci, i32, i32, ci, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+            "orc_subdivide": (None, [ci, ci, i32, i32, ci, f64, ci, f64, i32]),
             "orc_accumulate": (None, [vp, f64, f32, i32, f64, i32]),
             "orc_residuals": (cd, [vp, f64, f64, i32, f64, i32, f64, i32]),
             "orc_jacobian": (None, [vp, f64, f64, f64, i32, f64]),
@@ -120,6 +122,22 @@ def solve3(M, b):
     x = np.zeros(3)
     rc = lib().orc_solve3(np.ascontiguousarray(M, np.float64).ravel(), np.ascontiguousarray(b, np.float64), x)
     return x if rc == 0 else None
+
+
+def subdivide(face_off, face_vert, attr, levels):
+    """Catmull-Clark subdivision (the paper's template construction) of the polygons (CSR face_off /
+    face_vert) carrying per-vertex attributes attr [V][A]; returns (attributes [V'][A], quads [Q][4])."""
+    fo = np.ascontiguousarray(face_off, np.int32)
+    fv = np.ascontiguousarray(face_vert, np.int32)
+    a = np.ascontiguousarray(attr, np.float64)
+    V, A = a.shape
+    F = len(fo) - 1
+    nv, nq = C.c_int32(), C.c_int32()
+    lib().orc_subdivide_counts(V, F, fo, fv, levels, C.byref(nv), C.byref(nq))
+    out = np.empty((nv.value, A))
+    quads = np.empty((nq.value, 4), np.int32)
+    lib().orc_subdivide(V, F, fo, fv, A, a, levels, out, quads)
+    return out, quads
 
 
 def normal_eq(J, r, inA):

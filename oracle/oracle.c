@@ -1103,3 +1103,180 @@ int orc_track_frame(void* h, const float* depth, double* energy, int32_t* accept
   free(J); free(JTJ); free(JTr);
   return nassoc;
 }
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Template authoring (the paper's template construction): Catmull-Clark subdivision of a polygon   */
+/* cage, the skin weights interpolated with the same stencils as the positions.                      */
+/* ------------------------------------------------------------------------------------------------ */
+/* Conventions (shared with the library's description, not its code): the new vertices of a level are
+ * the vertex points of the old vertices (same indices), then the edge points in the order in which the
+ * edges first appear when the faces are walked in order (face f, edges (v_i, v_{i+1})), then the face
+ * points in face order.  Face f = (v_0 .. v_{k-1}) becomes the quads (v_i', e(v_i, v_{i+1}), f', e(v_{i-1}, v_i)),
+ * i = 0 .. k-1.  Rules: face point = mean of the face's vertices; interior edge point = mean of its two
+ * end points and the two adjacent face points, boundary edge point = the midpoint; interior vertex point =
+ * (F + 2 R + (n - 3) P) / n with F the mean of the n adjacent face points, R the mean of the midpoints
+ * of the n incident edges; boundary vertex point = (6 P + the two boundary neighbours) / 8. */
+typedef struct { int a, b, fa, fb; } cc_edge;
+
+static int cc_find_edge(int* head, int* next, const cc_edge* E, int a, int b) {
+  int lo = a < b ? a : b, hi = a < b ? b : a;
+  for (int e = head[lo]; e >= 0; e = next[e]) {
+    int ea = E[e].a < E[e].b ? E[e].a : E[e].b, eb = E[e].a < E[e].b ? E[e].b : E[e].a;
+    if (ea == lo && eb == hi) return e;
+  }
+  return -1;
+}
+
+/* One level. face_off/face_vert: the polygons (CSR). attr: [V][A] (positions and other attributes).
+ * Outputs: out_attr [V + E + F][A], out_quads [sum_k][4]; returns the new vertex count (E via *nE). */
+static int cc_level(int V, int F, const int* face_off, const int* face_vert, int A, const double* attr,
+                    double* out_attr, int* out_quads, int* nE) {
+  int nf_v = face_off[F];
+  cc_edge* E = (cc_edge*)xcalloc(nf_v, sizeof(cc_edge));
+  int* head = (int*)xcalloc(V, sizeof(int));
+  int* next = (int*)xcalloc(nf_v, sizeof(int));
+  int* fedge = (int*)xcalloc(nf_v, sizeof(int)); /* edge of (v_i, v_{i+1}) of each face corner */
+  for (int i = 0; i < V; ++i) head[i] = -1;
+  int ne = 0;
+  for (int f = 0; f < F; ++f) {
+    int k = face_off[f + 1] - face_off[f];
+    for (int i = 0; i < k; ++i) {
+      int a = face_vert[face_off[f] + i], b = face_vert[face_off[f] + (i + 1) % k];
+      int e = cc_find_edge(head, next, E, a, b);
+      if (e < 0) {
+        e = ne++;
+        E[e].a = a; E[e].b = b; E[e].fa = f; E[e].fb = -1;
+        int lo = a < b ? a : b;
+        next[e] = head[lo];
+        head[lo] = e;
+      } else {
+        E[e].fb = f;
+      }
+      fedge[face_off[f] + i] = e;
+    }
+  }
+  double* FP = out_attr + (size_t)(V + ne) * A;  /* face points */
+  for (int f = 0; f < F; ++f) {
+    int k = face_off[f + 1] - face_off[f];
+    for (int c = 0; c < A; ++c) {
+      double s = 0;
+      for (int i = 0; i < k; ++i) s += attr[(size_t)face_vert[face_off[f] + i] * A + c];
+      FP[(size_t)f * A + c] = s / k;
+    }
+  }
+  double* EP = out_attr + (size_t)V * A;  /* edge points */
+  for (int e = 0; e < ne; ++e)
+    for (int c = 0; c < A; ++c) {
+      double pa = attr[(size_t)E[e].a * A + c], pb = attr[(size_t)E[e].b * A + c];
+      EP[(size_t)e * A + c] = E[e].fb < 0 ? 0.5 * (pa + pb)
+                                          : 0.25 * (pa + pb + FP[(size_t)E[e].fa * A + c] + FP[(size_t)E[e].fb * A + c]);
+    }
+  /* vertex points: accumulate the incident faces and edges */
+  double* Fs = (double*)xcalloc((size_t)V * A, sizeof(double));
+  double* Rs = (double*)xcalloc((size_t)V * A, sizeof(double));
+  double* Bs = (double*)xcalloc((size_t)V * A, sizeof(double));
+  int* nF = (int*)xcalloc(V, sizeof(int));
+  int* nR = (int*)xcalloc(V, sizeof(int));
+  int* nB = (int*)xcalloc(V, sizeof(int));
+  for (int f = 0; f < F; ++f)
+    for (int i = face_off[f]; i < face_off[f + 1]; ++i) {
+      int v = face_vert[i];
+      for (int c = 0; c < A; ++c) Fs[(size_t)v * A + c] += FP[(size_t)f * A + c];
+      nF[v]++;
+    }
+  for (int e = 0; e < ne; ++e) {
+    int ends[2] = {E[e].a, E[e].b};
+    for (int s = 0; s < 2; ++s) {
+      int v = ends[s], o = ends[1 - s];
+      for (int c = 0; c < A; ++c) Rs[(size_t)v * A + c] += 0.5 * (attr[(size_t)v * A + c] + attr[(size_t)o * A + c]);
+      nR[v]++;
+      if (E[e].fb < 0) {
+        for (int c = 0; c < A; ++c) Bs[(size_t)v * A + c] += attr[(size_t)o * A + c];
+        nB[v]++;
+      }
+    }
+  }
+  for (int v = 0; v < V; ++v)
+    for (int c = 0; c < A; ++c) {
+      double P = attr[(size_t)v * A + c];
+      double* o = out_attr + (size_t)v * A + c;
+      if (nB[v] > 0) {
+        *o = nB[v] == 2 ? (6.0 * P + Bs[(size_t)v * A + c]) / 8.0 : P;
+      } else if (nF[v] > 0) {
+        double n = nF[v];
+        *o = (Fs[(size_t)v * A + c] / n + 2.0 * Rs[(size_t)v * A + c] / nR[v] + (n - 3.0) * P) / n;
+      } else {
+        *o = P;
+      }
+    }
+  int q = 0;
+  for (int f = 0; f < F; ++f) {
+    int k = face_off[f + 1] - face_off[f];
+    for (int i = 0; i < k; ++i) {
+      out_quads[4 * q] = face_vert[face_off[f] + i];
+      out_quads[4 * q + 1] = V + fedge[face_off[f] + i];
+      out_quads[4 * q + 2] = V + ne + f;
+      out_quads[4 * q + 3] = V + fedge[face_off[f] + (i + k - 1) % k];
+      ++q;
+    }
+  }
+  *nE = ne;
+  free(E); free(head); free(next); free(fedge); free(Fs); free(Rs); free(Bs); free(nF); free(nR); free(nB);
+  return V + ne + F;
+}
+
+/* Counts after `levels` levels: vertices and quads (each level's faces are quads after the first). */
+void orc_subdivide_counts(int V, int F, const int32_t* face_off, const int32_t* face_vert, int levels, int32_t* Vout,
+                          int32_t* Qout) {
+  /* the edge count needs the topology: run the levels on a zero-width attribute */
+  int* fo = (int*)xcalloc(F + 1, sizeof(int));
+  int* fv = (int*)xcalloc(face_off[F] > 0 ? face_off[F] : 1, sizeof(int));
+  for (int f = 0; f <= F; ++f) fo[f] = face_off[f];
+  for (int i = 0; i < face_off[F]; ++i) fv[i] = face_vert[i];
+  int curV = V, curF = F;
+  for (int l = 0; l < levels; ++l) {
+    int nq = fo[curF], ne = 0;
+    int* quads = (int*)xcalloc(4 * (size_t)nq, sizeof(int));
+    double dummy[1];
+    double* outa = (double*)xcalloc(1, sizeof(double));
+    int newV = cc_level(curV, curF, fo, fv, 0, dummy, outa, quads, &ne);
+    free(outa);
+    free(fo); free(fv);
+    fo = (int*)xcalloc(nq + 1, sizeof(int));
+    for (int i = 0; i <= nq; ++i) fo[i] = 4 * i;
+    fv = quads;
+    curV = newV; curF = nq;
+  }
+  *Vout = curV;
+  *Qout = curF;
+  free(fo); free(fv);
+}
+
+/* `levels` levels of Catmull-Clark on attributes attr [V][A] (positions first); out_attr [Vout][A],
+ * out_quads [Qout][4] (sizes from orc_subdivide_counts). */
+void orc_subdivide(int V, int F, const int32_t* face_off, const int32_t* face_vert, int A, const double* attr,
+                   int levels, double* out_attr, int32_t* out_quads) {
+  int* fo = (int*)xcalloc(F + 1, sizeof(int));
+  int* fv = (int*)xcalloc(face_off[F] > 0 ? face_off[F] : 1, sizeof(int));
+  for (int f = 0; f <= F; ++f) fo[f] = face_off[f];
+  for (int i = 0; i < face_off[F]; ++i) fv[i] = face_vert[i];
+  double* cur = (double*)xcalloc((size_t)V * A + 1, sizeof(double));
+  memcpy(cur, attr, sizeof(double) * (size_t)V * A);
+  int curV = V, curF = F;
+  for (int l = 0; l < levels; ++l) {
+    int nq = fo[curF], ne = 0;
+    int* quads = (int*)xcalloc(4 * (size_t)nq, sizeof(int));
+    /* upper bound of the new vertex count: V + (corners) + F */
+    double* nxt = (double*)xcalloc((size_t)(curV + fo[curF] + curF) * A + 1, sizeof(double));
+    int newV = cc_level(curV, curF, fo, fv, A, cur, nxt, quads, &ne);
+    free(cur); free(fo); free(fv);
+    cur = nxt;
+    fo = (int*)xcalloc(nq + 1, sizeof(int));
+    for (int i = 0; i <= nq; ++i) fo[i] = 4 * i;
+    fv = quads;
+    curV = newV; curF = nq;
+  }
+  memcpy(out_attr, cur, sizeof(double) * (size_t)curV * A);
+  for (int i = 0; i < 4 * curF; ++i) out_quads[i] = fv[i];
+  free(cur); free(fo); free(fv);
+}
