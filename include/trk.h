@@ -125,6 +125,25 @@ typedef struct {
  * Errors: TRK_ERR_INVALID_ARG (NULL arguments, a parent not before its child). */
 trk_status trk_fk_joint_positions(const trk_skeleton* sk, const double* theta, double* out);
 
+/* ---- template authoring ------------------------------------------------------------------------------
+ * The template's construction: a low-resolution polygon cage with skin weights is refined by `levels`
+ * levels of Catmull-Clark subdivision, the weights interpolated with the same stencils as the positions
+ * (face point: mean of the face; edge point: (a + b + f_a + f_b)/4, midpoint on a boundary; vertex point:
+ * (F + 2R + (n - 3)P)/n, (6P + the two boundary neighbours)/8 on a boundary), then every vertex keeps its
+ * 4 largest weights (ties to the smaller bone) renormalised to sum 1, and every quad (a, b, c, d) becomes
+ * the triangles (a, b, c), (a, c, d).  New vertex order per level: the old vertices' points (same
+ * indices), the edge points (edges in order of first appearance walking the faces in order), the face
+ * points.  The cage: face_off [n_faces + 1] (face_off[0] = 0, >= 3 corners per face) and face_vert
+ * [face_off[n_faces]] (polygons, consistently oriented); host buffers in and out; the points are computed
+ * on the current device.  1 <= levels <= 4.  Errors: TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA. */
+trk_status trk_subdivide_counts(const int32_t* face_off, const int32_t* face_vert, int32_t n_verts, int32_t n_faces,
+                                int32_t levels, int32_t* n_verts_out, int32_t* n_tris_out);
+/* verts [n_verts][3], bone_idx [n_verts][4] (< n_bones), bone_w [n_verts][4]; outputs sized by
+ * trk_subdivide_counts: verts_out [V'][3], tris_out [T'][3], bone_idx_out [V'][4], bone_w_out [V'][4]. */
+trk_status trk_subdivide(const float* verts, const int32_t* face_off, const int32_t* face_vert, int32_t n_verts,
+                         int32_t n_faces, const uint8_t* bone_idx, const float* bone_w, int32_t n_bones, int32_t levels,
+                         float* verts_out, int32_t* tris_out, uint8_t* bone_idx_out, float* bone_w_out);
+
 /* Creates a session on the current CUDA device: validates and copies the model, derives the bind pose
  * H^0 (Sec. 3.2), the prior weights S_kk = n_k/|V| (vertices weighted to the subtree of link k), the
  * vertex-to-face lists and the neighbourhoods N(i) (the knn nearest bind-pose vertices, Sec. 4.3),

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libtrk.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["kernels_geom.cu", "kernels_solve.cu", "kernels_jtj.cu", "kernels_tc.cu", "trk_api.cu", "server.cu", "batch.cu",
-           "schedule.cu"]
+           "schedule.cu", "authoring.cu"]
 DEPS = ["trk_internal.cuh", "tcgen05.cuh", os.path.join(ROOT, "include", "trk.h")]
 # -fmad=false: no implicit multiply-add contraction in device code (the FMAs the kernels want are written
 # as fmaf), so a stage body inlined into different kernels rounds identically everywhere.

@@ -26,7 +26,8 @@ EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_dev
            "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
            "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc",
-           "trk_jtj_rows_tc", "trk_fk_joint_positions", "trk_batch_create", "trk_batch_track_device", "trk_batch_profile",
+           "trk_jtj_rows_tc", "trk_fk_joint_positions", "trk_subdivide_counts", "trk_subdivide",
+           "trk_batch_create", "trk_batch_track_device", "trk_batch_profile",
            "trk_batch_destroy",
            "trk_schedule_create", "trk_schedule_track_device", "trk_schedule_get_config", "trk_schedule_autotune",
            "trk_schedule_destroy", "trk_schedule_signature", "trk_tuning_cache_lookup", "trk_tuning_cache_store",
@@ -108,6 +109,8 @@ def lib(build_if_missing: bool = True):
             "trk_jtj_rows": [vp, i32, i32, i32, vp, vp], "trk_jtj_rows_noalloc": [vp, i32, i32, i32, vp, vp],
             "trk_jtj_rows_tc": [vp, i32, i32, i32, i32, vp, vp],
             "trk_fk_joint_positions": [vp, vp, vp],
+            "trk_subdivide_counts": [vp, vp, i32, i32, i32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+            "trk_subdivide": [vp, vp, vp, i32, i32, vp, vp, i32, i32, vp, vp, vp, vp],
             "trk_batch_create": [C.POINTER(vp), i32, C.POINTER(vp)], "trk_batch_track_device": [vp, C.POINTER(vp), vp],
             "trk_batch_profile": [vp, C.POINTER(vp), i32, sz, vp],
             "trk_schedule_create": [C.POINTER(vp), i32, vp, C.c_char_p, C.POINTER(vp)],
@@ -181,6 +184,25 @@ def joint_positions(skeleton: dict, theta) -> np.ndarray:
     out = np.empty((L, 3))
     _check(lib().trk_fk_joint_positions(C.byref(sk), _p(th), _p(out)))
     return out
+
+
+def subdivide(verts, face_off, face_vert, bone_idx, bone_w, n_bones: int, levels: int = 2):
+    """Template authoring (trk_subdivide): Catmull-Clark subdivision of a polygon cage with its skin
+    weights; returns (verts [V'][3] float32, tris [T'][3] int32, bone_idx [V'][4] uint8, bone_w [V'][4])."""
+    v = np.ascontiguousarray(verts, np.float32)
+    fo = np.ascontiguousarray(face_off, np.int32)
+    fv = np.ascontiguousarray(face_vert, np.int32)
+    bi = np.ascontiguousarray(bone_idx, np.uint8)
+    bw = np.ascontiguousarray(bone_w, np.float32)
+    nv, nt = C.c_int32(), C.c_int32()
+    _check(lib().trk_subdivide_counts(_p(fo), _p(fv), len(v), len(fo) - 1, levels, C.byref(nv), C.byref(nt)))
+    ov = np.empty((nv.value, 3), np.float32)
+    ot = np.empty((nt.value, 3), np.int32)
+    obi = np.empty((nv.value, 4), np.uint8)
+    obw = np.empty((nv.value, 4), np.float32)
+    _check(lib().trk_subdivide(_p(v), _p(fo), _p(fv), len(v), len(fo) - 1, _p(bi), _p(bw), n_bones, levels,
+                               _p(ov), _p(ot), _p(obi), _p(obw)))
+    return ov, ot, obi, obw
 
 
 def params_struct(p: dict) -> Params:
