@@ -20,6 +20,9 @@ Prints one JSON line (rank 0):
   uneven     --uneven-sessions sessions of random-tree bodies (5k-200k vertices, 12-40 bones, 320x240 to
              1280x720): frames/s one by one, on one stream each, as one fused batch (trk_batch_*), and
              under the schedule the autotuner picks (trk_schedule_*)
+  admission_serving  --admission-streams streams of uneven sessions with Poisson starts under a 1 GiB HBM
+             budget: admitted as capacity frees, 30 Poisson frames/s each, then leaving; served frames/s,
+             latency, admission waits, peak admitted bytes
   experiments  the paper's conditions (full tracking, shape-match, smooth-bind) on the sequence with its
              ground truth: joint accuracy (AUC up to 10 cm) and reconstruction error
   roofline   the dominant kernel's achieved rate against the measured peak of MEASURED_PEAKS.json
@@ -242,6 +245,33 @@ def determined_dofs(o, model, th, phi, depth, tol=1e-3):
     return np.sqrt(1e-5 * P["E"] * np.diag(np.linalg.inv(H))) < tol
 
 
+def _oracle_worker(k, n_frames):
+    """One independent oracle session (the all-cores baseline): its own model and frames; returns the
+    frames tracked and the seconds the tracking took."""
+    import oracle
+    from paper_1711_07999_gb300 import synth
+    model = synth.make_model(2, session=3000 + k)
+    o, frames = oracle_frames(model, n_frames, seed=synth.seed_for(2, 3100 + k))
+    o.set_state(synth.gt_theta(model, 0.0), None)
+    t0 = time.perf_counter()
+    for d in frames:
+        o.track_frame(d)
+    return n_frames, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(n_frames):
+    """The oracle over all host cores: one independent session per core (spawned processes), each
+    tracking n_frames frames; aggregate frames/s over the slowest worker's tracking time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_worker, [(k, n_frames) for k in range(cores)])
+    frames = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    return {"value": frames / secs, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} independent sessions of the 50k-vertex workload, {n_frames} frames each, one per process"}
+
+
 def errors_vs_oracle(model, prec, frames, states):
     """Per-result error of one precision mode against the oracle on the same frames (free-running from
     the same start): joint values, offsets (99th percentile and max over vertices), energies."""
@@ -458,6 +488,100 @@ def run_serving(sessions, host_frames, n_seq, duration_s, fps, seed):
             "latency_ms": {"p50": st["latency_p50_us"] / 1000,
                                                       "p99": st["latency_p99_us"] / 1000,
                                                       "max": st["latency_max_us"] / 1000}}
+
+
+def run_admission_serving(args, rank):
+    """Streams of uneven sessions arriving over time under an HBM budget that binds: --admission-streams
+    sessions of the random-tree bodies; stream starts form a Poisson process (rate: all streams within
+    about a second); each stream, once admitted (attach succeeds within the budget, otherwise it waits in
+    arrival order until a departing stream frees enough), submits --admission-frames frames at Poisson
+    arrivals of 30 frames/s, collects them and leaves (detach).  Reports served frames/s, submit ->
+    completion latency, admission waits and the peak of the admitted device bytes."""
+    import threading
+    import torch
+    from paper_1711_07999_gb300 import synth, trk
+    N, K, fps = args.admission_streams, args.admission_frames, 30.0
+    budget = int(args.admission_budget_gib * (1 << 30))
+    rng = np.random.default_rng(synth.seed_for(5, rank))
+    models = [synth.make_model(4, session=20000 + rank * 1000 + k) for k in range(N)]
+    sess = [trk.Session(m) for m in models]
+    frames = []
+    for i, (m, s) in enumerate(zip(models, sess)):
+        r = np.random.default_rng(synth.seed_for(5, 100 + i))
+        frames.append([synth.add_noise(s.render_depth(synth.gt_theta(m, f / 30.0), synth.gt_offsets(m, f / 30.0)), 4, r)
+                       for f in range(4)])
+        s.set_pose(synth.gt_theta(m, 0.0))
+    need = [s.info()["device_bytes"] for s in sess]
+    starts = np.cumsum(rng.exponential(1.0 / N, N))
+    gaps = [rng.exponential(1.0 / fps, K) for _ in range(N)]
+    torch.cuda.synchronize()
+    lock = threading.Condition()
+    queue = []  # streams waiting for admission, in arrival order
+    used = [0]
+    peak = [0]
+    waits, served = [0.0] * N, [0] * N
+    with trk.Server(budget, max_inflight=N) as sv:
+        def admit(b, t0):
+            with lock:
+                queue.append(b)
+                while True:
+                    if queue[0] == b:
+                        try:
+                            sv.attach(sess[b])
+                            used[0] += need[b]
+                            peak[0] = max(peak[0], used[0])
+                            queue.pop(0)
+                            lock.notify_all()
+                            return time.perf_counter()
+                        except trk.TrkError as e:
+                            if e.status != trk.TRK_ERR_NO_CAPACITY:
+                                raise
+                    lock.wait(0.005)
+
+        def stream(b, t0):
+            if need[b] > budget:  # never admissible
+                waits[b] = float("nan")
+                return
+            dt = t0 + starts[b] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            t_arrive = time.perf_counter()
+            t_adm = admit(b, t0)
+            waits[b] = t_adm - t_arrive
+            tickets, t = [], t_adm
+            for k in range(K):
+                t += gaps[b][k]
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(sv.submit(sess[b], frames[b][k % 4]))
+            for tk in tickets:
+                sv.wait(sess[b], tk, timeout_us=60_000_000, want_offsets=True)
+                served[b] += 1
+            with lock:
+                sv.detach(sess[b])
+                used[0] -= need[b]
+                lock.notify_all()
+
+        t0 = time.perf_counter()
+        th = [threading.Thread(target=stream, args=(b, t0)) for b in range(N)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        wall = time.perf_counter() - t0
+        st = sv.stats()
+    for s in sess:
+        s.close()
+    w = np.array([x for x in waits if x == x]) * 1e3
+    return {"streams": N, "frames_per_stream": K, "fps_per_stream": fps, "budget_bytes": budget,
+            "sum_of_session_bytes": int(sum(need)), "peak_admitted_bytes": int(peak[0]),
+            "streams_that_waited": int((w > 1.0).sum()), "streams_over_budget": int(N - len(w)),
+            "admission_wait_ms": {"p50": float(np.percentile(w, 50)), "p99": float(np.percentile(w, 99)),
+                                  "max": float(w.max())},
+            "frames": int(sum(served)), "seconds": round(wall, 3), "achieved_fps": sum(served) / wall,
+            "latency_ms": {"p50": st["latency_p50_us"] / 1000, "p99": st["latency_p99_us"] / 1000,
+                           "max": st["latency_max_us"] / 1000}}
 
 
 def run_uneven(args, rank, flush):
@@ -726,10 +850,13 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and args.cpu_frames > 0:
         cpu, frames_o, states_o = cpu_baseline(model, args.cpu_frames)
         sample = (frames_o, states_o)
+        if args.cpu_all_cores_frames > 0:
+            cpu["all_cores"] = cpu_baseline_all_cores(args.cpu_all_cores_frames)
     precision = None
     if args.precision_modes and B > 1:
         precision = run_precision_modes(args, model, rank, dev, n_seq, flush, nA, NP, sample)
     uneven = run_uneven(args, rank, flush) if args.uneven_sessions > 0 else None
+    admission = run_admission_serving(args, rank) if args.admission_streams > 0 else None
     experiments = run_experiments(args, rank) if (args.experiment_frames > 0 and rank == 0) else None
     if rank == 0:
         plain = {"value": value, "ms_per_step": max_ms / args.steps,
@@ -754,6 +881,7 @@ def run_ours(args, rank, world, local_rank):
             "batched": batched,
             "precision": precision,
             "uneven": uneven,
+            "admission_serving": admission,
             "experiments": experiments,
             "gpu_launches": info["kernels_per_frame"] * args.steps * (B if batched is not None else 1),
             "roofline": roof,
@@ -775,6 +903,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=150, help="length of the pre-rendered sequence")
     ap.add_argument("--cpu-frames", type=int, default=4, help="oracle frames of the CPU baseline sample")
+    ap.add_argument("--cpu-all-cores-frames", type=int, default=2,
+                    help="frames per core of the all-cores oracle baseline (0: skip)")
     ap.add_argument("--profile-reps", type=int, default=20)
     ap.add_argument("--sessions", type=int, default=16, help="concurrent sessions of the batched measurement")
     ap.add_argument("--serve-streams", type=int, default=32, help="Poisson streams (30 fps each) of the serving run")
@@ -784,6 +914,10 @@ def main():
     ap.add_argument("--only", choices=["all", "plain", "uneven"], default="all",
                     help="plain: the one-session and batched measurements only; uneven: the uneven batch only")
     ap.add_argument("--uneven-modes", default="one_by_one,streams,fused,schedule")
+    ap.add_argument("--admission-streams", type=int, default=32,
+                    help="streams of uneven sessions arriving under an HBM budget (0: skip)")
+    ap.add_argument("--admission-frames", type=int, default=30)
+    ap.add_argument("--admission-budget-gib", type=float, default=1.0)
     ap.add_argument("--experiment-frames", type=int, default=30,
                     help="frames of the sequence tracked in each of the paper's experiment conditions")
     ap.add_argument("--uneven-sessions", type=int, default=64,
@@ -793,7 +927,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.only == "plain":
-        args.uneven_sessions, args.precision_modes, args.experiment_frames = 0, 0, 0
+        args.uneven_sessions, args.precision_modes, args.experiment_frames, args.admission_streams = 0, 0, 0, 0
     rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         run_reference(args, rank, world)
