@@ -146,34 +146,48 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
   float r2;
   jacobian_row(d, rs, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, r2);
   __syncthreads();
-  const int ty = tid >> 4, tx = tid & 15;
-  float acc[T][T];
-#pragma unroll
-  for (int a = 0; a < T; ++a)
-#pragma unroll
-    for (int b = 0; b < T; ++b) acc[a][b] = 0.f;
-  for (int s = 0; s < total; ++s) {
-    const float* row = Js + s * ROW;
-    float ra[T], rb[T];
-#pragma unroll
-    for (int a = 0; a < T; ++a) {
-      ra[a] = row[ty * T + a];
-      rb[a] = row[tx * T + a];
-    }
+  // the symmetric product needs only the tiles (ty, tx) with ty <= tx among the nt x nt tiles that hold
+  // columns < NP: thread k < nt (nt + 1) / 2 takes the k-th of them (row-major), the others idle; each
+  // tile is written with its mirror (the mirrored products are the same products in the same order)
+  const int NP = d.NP;
+  const int nt = (NP + T - 1) / T;
+  int ty = 0, k = tid;
+  while (ty < nt && k >= nt - ty) {
+    k -= nt - ty;
+    ++ty;
+  }
+  const int tx = ty + k;
+  if (ty < nt) {
+    float acc[T][T];
 #pragma unroll
     for (int a = 0; a < T; ++a)
 #pragma unroll
-      for (int b = 0; b < T; ++b) acc[a][b] = fmaf(ra[a], rb[b], acc[a][b]);
-  }
-  const int NP = d.NP;
-  float* out = d.partial + (size_t)bp.x * NP * NP;
+      for (int b = 0; b < T; ++b) acc[a][b] = 0.f;
+    for (int s = 0; s < total; ++s) {
+      const float* row = Js + s * ROW;
+      float ra[T], rb[T];
 #pragma unroll
-  for (int a = 0; a < T; ++a)
+      for (int a = 0; a < T; ++a) {
+        ra[a] = row[ty * T + a];
+        rb[a] = row[tx * T + a];
+      }
 #pragma unroll
-    for (int b = 0; b < T; ++b) {
-      const int r = ty * T + a, c = tx * T + b;
-      if (r < NP && c < NP) out[r * NP + c] = acc[a][b];
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T; ++b) acc[a][b] = fmaf(ra[a], rb[b], acc[a][b]);
     }
+    float* out = d.partial + (size_t)bp.x * NP * NP;
+#pragma unroll
+    for (int a = 0; a < T; ++a)
+#pragma unroll
+      for (int b = 0; b < T; ++b) {
+        const int r = ty * T + a, c = tx * T + b;
+        if (r < NP && c < NP) {
+          out[r * NP + c] = acc[a][b];
+          out[c * NP + r] = acc[a][b];
+        }
+      }
+  }
   if (tid == 0) {
     d.jtj_rows[bp.x] = total;
     atomicAdd(&d.stats[1], total);
@@ -720,13 +734,22 @@ __global__ void __launch_bounds__(kSolveThreads) k_lm_solve(BatchGrid g, Dev d0)
 // Energy of each candidate at the fixed association (normals and p~ held), then the accept step:
 // the first candidate with E_c <= E wins (lambda <- lambda_c / 10); if none, Theta stays and
 // lambda <- min(lambda_5 * 10, 1e7).  The last block to finish does the selection.
-__device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_buf) {
+//
+// In two passes, so that the common case costs a third of the work: the first pass scores candidates
+// 0 and 1 (the damping that almost always succeeds) and accepts one if it can; otherwise it records
+// their energies and marks the step pending (lm_trials[7] = -2), and the second pass scores candidates
+// 2-5 and decides over all six.  The decision sequence and every energy are those of scoring all six at
+// once (each candidate's sum has the same blocks in the same order).  Candidates not scored report +inf.
+constexpr double kPending = -2.0;
+
+__device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_buf, int c0, int c1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DQ* sH = reinterpret_cast<DQ*>(smem_raw);  // [kCandidates][L]
   __shared__ int sok[kCandidates];
   __shared__ double swarp[kBlock / 32][kCandidates];
   __shared__ bool last;
   const int L = d.L, tid = threadIdx.x;
+  if (c0 > 0 && d.lm_trials[7] != kPending) return;  // the first pass decided
   const int i = bp.x * kBlock + tid;
   Acc4 a4 = Acc4{0, 0, 0, 0};
   float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -737,29 +760,27 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
   const bool inA = i < d.V && a4.w >= 1 && nn.w > 0.f;
   if (tid < kCandidates) sok[tid] = d.lm_ok[tid];
   if (__syncthreads_or(inA)) {  // the candidates' tables are needed only where a vertex of A is
-    for (int t = tid; t < kCandidates * L; t += kBlock) sH[t] = d.Hd_c[t];
+    for (int t = c0 * L + tid; t < c1 * L; t += kBlock) sH[t] = d.Hd_c[t];
     __syncthreads();
   }
   float e[kCandidates];
 #pragma unroll
   for (int c = 0; c < kCandidates; ++c) e[c] = 0.f;
-  {
-    if (inA) {
-      const float inv = 1.f / ((float)a4.w * kFix);
-      const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
-      const float4 v = d.v[i], x0 = d.v0[i], ph = d.phi[phi_buf][i];
-      const float3 x = make_float3(x0.x + ph.x, x0.y + ph.y, x0.z + ph.z);
-      const uchar4 bi = d.bidx[i];
-      const float4 bw = d.bw[i];
+  if (inA) {
+    const float inv = 1.f / ((float)a4.w * kFix);
+    const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
+    const float4 v = d.v[i], x0 = d.v0[i], ph = d.phi[phi_buf][i];
+    const float3 x = make_float3(x0.x + ph.x, x0.y + ph.y, x0.z + ph.z);
+    const uchar4 bi = d.bidx[i];
+    const float4 bw = d.bw[i];
 #pragma unroll
-      for (int c = 0; c < kCandidates; ++c) {
-        if (!sok[c]) continue;
-        float sg[4];
-        const DQ H = blend_bones(sH + c * L, bi, bw, sg);
-        const float3 vc = dq_point(H, x);
-        const float r = nn.x * (v.x - vc.x + pm.x) + nn.y * (v.y - vc.y + pm.y) + nn.z * (v.z - vc.z + pm.z);
-        e[c] = r * r;
-      }
+    for (int c = 0; c < kCandidates; ++c) {
+      if (c < c0 || c >= c1 || !sok[c]) continue;
+      float sg[4];
+      const DQ H = blend_bones(sH + c * L, bi, bw, sg);
+      const float3 vc = dq_point(H, x);
+      const float r = nn.x * (v.x - vc.x + pm.x) + nn.y * (v.y - vc.y + pm.y) + nn.z * (v.z - vc.z + pm.z);
+      e[c] = r * r;
     }
   }
 #pragma unroll
@@ -768,7 +789,7 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
   if ((tid & 31) == 0)
     for (int c = 0; c < kCandidates; ++c) swarp[tid >> 5][c] = e[c];
   __syncthreads();
-  if (tid < kCandidates) {
+  if (tid >= c0 && tid < c1) {
     double s = 0.0;
     for (int w = 0; w < kBlock / 32; ++w) s += swarp[w][tid];
     d.epart[(size_t)bp.x * 8 + tid] = s;
@@ -784,20 +805,25 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
   {
     double s6[kCandidates] = {0, 0, 0, 0, 0, 0};
     for (int b = tid; b < bp.gx; b += kBlock)
-      for (int c = 0; c < kCandidates; ++c) s6[c] += __ldcg(d.epart + (size_t)b * 8 + c);
+      for (int c = c0; c < c1; ++c) s6[c] += __ldcg(d.epart + (size_t)b * 8 + c);
     for (int c = 0; c < kCandidates; ++c) red[tid][c] = s6[c];
   }
   __syncthreads();
   for (int h = kBlock / 2; h > 0; h >>= 1) {
     if (tid < h)
-      for (int c = 0; c < kCandidates; ++c) red[tid][c] += red[tid + h][c];
+      for (int c = c0; c < c1; ++c) red[tid][c] += red[tid + h][c];
     __syncthreads();
   }
+  const double inf = __longlong_as_double(0x7ff0000000000000ll);
   if (tid < kCandidates) {
-    double s = red[0][tid];
-    const double* thc = d.theta_c + (size_t)tid * L;
-    for (int k = 0; k < L; ++k) s += d.prior2[k] * thc[k] * thc[k];
-    Ec[tid] = sok[tid] ? s : __longlong_as_double(0x7ff0000000000000ll);
+    if (tid >= c0 && tid < c1) {
+      double s = red[0][tid];
+      const double* thc = d.theta_c + (size_t)tid * L;
+      for (int k = 0; k < L; ++k) s += d.prior2[k] * thc[k] * thc[k];
+      Ec[tid] = sok[tid] ? s : inf;
+    } else {
+      Ec[tid] = tid < c0 ? d.lm_trials[tid] : inf;  // the first pass's energies; later ones unscored
+    }
   }
   __syncthreads();
   __shared__ int acc_c;
@@ -805,18 +831,23 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
     const double E = d.lm_trials[6];
     double lam = *d.lam;
     int a = -1;
-    for (int c = 0; c < kCandidates; ++c) {
+    for (int c = 0; c < c1; ++c) {
       d.lm_trials[c] = Ec[c];
       if (a < 0 && sok[c] && Ec[c] <= E) a = c;
     }
-    if (a >= 0) {
-      for (int t = 0; t < a; ++t) lam = fmin(lam * 10.0, 1e7);
-      lam = fmax(lam / 10.0, 1e-7);
+    for (int c = c1; c < kCandidates; ++c) d.lm_trials[c] = inf;
+    if (a >= 0 || c1 == kCandidates) {
+      if (a >= 0) {
+        for (int t = 0; t < a; ++t) lam = fmin(lam * 10.0, 1e7);
+        lam = fmax(lam / 10.0, 1e-7);
+      } else {
+        for (int t = 0; t < kCandidates; ++t) lam = fmin(lam * 10.0, 1e7);
+      }
+      *d.lam = lam;
+      d.lm_trials[7] = (double)a;
     } else {
-      for (int t = 0; t < kCandidates; ++t) lam = fmin(lam * 10.0, 1e7);
+      d.lm_trials[7] = kPending;
     }
-    *d.lam = lam;
-    d.lm_trials[7] = (double)a;
     acc_c = a;
     d.counter[0] = 0;
   }
@@ -831,13 +862,15 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_lm_eval(BatchGrid g, Dev d0, int phi_buf) {
+constexpr int kFirstPass = 2;  // candidates scored by the first pass
+
+__global__ void __launch_bounds__(kBlock) k_lm_eval(BatchGrid g, Dev d0, int phi_buf, int c0, int c1) {
   if (g.map == nullptr) {
-    lm_eval_impl(d0, grid_pos(), phi_buf);
+    lm_eval_impl(d0, grid_pos(), phi_buf, c0, c1);
     return;
   }
   __shared__ Dev sd;
-  lm_eval_impl(sd, batch_block(g, sd), phi_buf);
+  lm_eval_impl(sd, batch_block(g, sd), phi_buf, c0, c1);
 }
 
 static int lm_solve_smem(int L) {
@@ -850,7 +883,9 @@ void launch_lm_solve(const Dev& d, cudaStream_t st) {
 }
 
 void launch_lm_eval(const Dev& d, int phi_buf, cudaStream_t st) {
-  k_lm_eval<<<d.nblk_v, kBlock, kCandidates * d.L * sizeof(DQ), st>>>(kSingle, d, phi_buf);
+  const size_t sm = kCandidates * d.L * sizeof(DQ);
+  k_lm_eval<<<d.nblk_v, kBlock, sm, st>>>(kSingle, d, phi_buf, 0, kFirstPass);
+  k_lm_eval<<<d.nblk_v, kBlock, sm, st>>>(kSingle, d, phi_buf, kFirstPass, kCandidates);
 }
 
 void launch_lm(const Dev& d, int phi_buf, cudaStream_t st) {
@@ -1291,7 +1326,11 @@ void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGr
 void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int max_links, int phi_buf,
                  cudaStream_t st) {
   if (nlm > 0) k_lm_solve<<<nlm, kSolveThreads, lm_solve_smem(max_links), st>>>(glm, Dev{});
-  if (nv > 0) k_lm_eval<<<nv, kBlock, kCandidates * max_links * sizeof(DQ), st>>>(gv, Dev{}, phi_buf);
+  if (nv > 0) {
+    const size_t sm = kCandidates * max_links * sizeof(DQ);
+    k_lm_eval<<<nv, kBlock, sm, st>>>(gv, Dev{}, phi_buf, 0, kFirstPass);
+    k_lm_eval<<<nv, kBlock, sm, st>>>(gv, Dev{}, phi_buf, kFirstPass, kCandidates);
+  }
 }
 
 int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int solver, int phi_src, int slot,

@@ -762,7 +762,7 @@ trk_status trk_get_info(trk_session* s, trk_info* out) {
   out->height = d.cam.H;
   const int per_assoc = (d.F > 0 ? 5 : 4);  // skin, raster, visibility, associate (2 kernels)
   const int shape_k = s->prm.shape_solver == 1 ? 3 * s->prm.shape_sweeps + 1 : s->prm.shape_sweeps;
-  out->kernels_per_frame = s->prm.pose_iters * (per_assoc + 4) + s->prm.shape_iters * (per_assoc + shape_k);
+  out->kernels_per_frame = s->prm.pose_iters * (per_assoc + 5) + s->prm.shape_iters * (per_assoc + shape_k);
   out->device_bytes = s->device_bytes;
   return TRK_OK;
 }
