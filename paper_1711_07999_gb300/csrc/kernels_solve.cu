@@ -3,10 +3,11 @@
 // energy test (Sec. 4.2), and the per-vertex shape step (Eq. r_warp, Sec. 4.3).
 //
 // Reductions are deterministic: per-block partial sums over fixed vertex ranges, then a second pass
-// that adds the partials in block order in FP64.  The LM retries of one iteration (damping lambda,
-// 10 lambda, ..., 10^5 lambda) are solved side by side, one CTA each, and their energies evaluated in
-// one pass over the vertices; the first candidate that does not raise the energy is taken on the device,
-// which gives the same result as trying them one after the other without any host round trip.
+// that adds the partials in a fixed order (error-free FP32 within a warp, FP64 across warps).  The LM
+// retries of one iteration (damping lambda, 10 lambda, ..., 10^5 lambda) are solved side by side, one CTA
+// each, and their energies evaluated over the vertices; the first candidate that does not raise the
+// energy is taken on the device, which gives the same result as trying them one after the other without
+// any host round trip.
 #include <mutex>
 
 #include "tcgen05.cuh"
@@ -321,22 +322,34 @@ __global__ void __launch_bounds__(kBlock) k_resid_jtj_tc(BatchGrid g, Dev d0, in
   resid_jtj_tc_impl<PREC, NB>(sd, batch_block(g, sd), phi_buf);
 }
 
-// Fixed-order FP64 sum of the block partials -> [J r]^T [J r]; the last entry gives E_pose (with the
-// prior sum_k (lambda_s S_kk theta_k)^2), recorded as this iteration's energy and as the LM reference.
-// A CTA owns 32 consecutive entries (coalesced lanes); its 32 warps take every 32nd partial, then warp 0
-// adds the 32 warp sums in order.
+// Fixed-order sum of the block partials -> [J r]^T [J r]; the last entry gives E_pose (with the prior
+// sum_k (lambda_s S_kk theta_k)^2), recorded as this iteration's energy and as the LM reference.
+// A CTA owns 32 consecutive entries (coalesced lanes); its 32 warps take every 32nd partial and add them
+// in FP32 with an error-free transformation (each addition's rounding error, from Knuth's TwoSum, is
+// carried in a second FP32 accumulator: the compensated sum of Ogita, Rump and Oishi, accurate to about
+// u |S| + (n u)^2 sum |x| in FP32 unit roundoff u, i.e. as if added in twice the precision).  The FP64
+// pipe issues a small fraction of the FP32 rate on this GPU, so it is left to warp 0, which adds the 32
+// warp sums (hi + lo) in FP64 in warp order.
 constexpr int kReduceThreads = 1024;
+
+__device__ __forceinline__ void sum2_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (x - bb);  // exact: hi + x = s + e
+  hi = s;
+  lo += e;
+}
 
 __device__ __forceinline__ void reduce_jtj_impl(const Dev& d, BlockPos bp, int slot) {
   __shared__ double sm[kReduceThreads / 32][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int NP = d.NP, n2 = NP * NP;
   const int e = bp.x * 32 + lane;
-  // warp w takes blocks w, w + 32, ... (four at a time, loads in flight together); blocks that added no
-  // rows wrote no partial and count as zero
+  // warp w takes blocks w, w + 32, ... (four loads in flight together); blocks that added no rows wrote
+  // no partial and count as zero
   constexpr int S = kReduceThreads / 32;
   const int nb = d.nblk_jtj;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  float hi = 0.f, lo = 0.f;
   if (e < n2) {
     int b = w;
     for (; b + 3 * S < nb; b += 4 * S) {
@@ -345,16 +358,15 @@ __device__ __forceinline__ void reduce_jtj_impl(const Dev& d, BlockPos bp, int s
       const float p1 = r1 > 0 ? d.partial[(size_t)(b + S) * n2 + e] : 0.f;
       const float p2 = r2 > 0 ? d.partial[(size_t)(b + 2 * S) * n2 + e] : 0.f;
       const float p3 = r3 > 0 ? d.partial[(size_t)(b + 3 * S) * n2 + e] : 0.f;
-      s0 += (double)p0;
-      s1 += (double)p1;
-      s2 += (double)p2;
-      s3 += (double)p3;
+      sum2_add(hi, lo, p0);
+      sum2_add(hi, lo, p1);
+      sum2_add(hi, lo, p2);
+      sum2_add(hi, lo, p3);
     }
     for (; b < nb; b += S)
-      if (d.jtj_rows[b] > 0) s0 += (double)d.partial[(size_t)b * n2 + e];
+      if (d.jtj_rows[b] > 0) sum2_add(hi, lo, d.partial[(size_t)b * n2 + e]);
   }
-  const double s = (s0 + s1) + (s2 + s3);
-  sm[w][lane] = s;
+  sm[w][lane] = (double)hi + (double)lo;
   __syncthreads();
   if (w != 0 || e >= n2) return;
   double t = 0.0;
@@ -439,12 +451,13 @@ void launch_normal_equations(const Dev& d, int phi_buf, int slot, cudaStream_t s
 // b = J^T r + (lambda_s S)^2 Theta and lambda_c = min(lambda 10^c, 1e7); a parameter whose diagonal is
 // zero is frozen (x_k = 0).  Theta_c = Theta - x and its FK tables follow.
 //
-// On this GPU a dependent FP64 FMA costs ~70 cycles and an FP64 rsqrt ~440 (FP32: ~4 and ~20), so the
-// P sequential pivot steps of an FP64 Cholesky are latency-bound (~80 us at P = 55).  The solve therefore
-// factors the Jacobi-scaled matrix D M D (unit diagonal) in FP32 and reaches FP64 accuracy by iterative
-// refinement: x += D (D M D)^-1 D (b - M x) with the residual in FP64, until the scaled residual is below
-// 1e-10 of the scaled right-hand side.  If the FP32 factorisation breaks down or the refinement stalls,
-// the FP64 Cholesky factorisation of M is used instead.
+// On this GPU a dependent FP64 FMA costs ~70 cycles and an FP64 rsqrt ~440 (FP32: ~4 and ~20), and the
+// FP64 pipe issues ~2 operations per cycle per SM, so the P sequential pivot steps of an FP64 Cholesky
+// are latency-bound (~80 us at P = 55).  The solve therefore factors the Jacobi-scaled matrix D M D
+// (unit diagonal) in FP32 (blocked Cholesky) and reaches FP64 accuracy by iterative refinement:
+// x += D (D M D)^-1 D (b - M x) with the residual in FP64, until the scaled residual is below 1e-10 of
+// the scaled right-hand side.  If the FP32 factorisation breaks down or the refinement stalls, the FP64
+// Cholesky factorisation of M is used instead.
 // ---------------------------------------------------------------------------------------------
 constexpr int kSolveThreads = 256;
 constexpr int kMaxRefine = 8;
@@ -631,50 +644,55 @@ __device__ __forceinline__ void lm_solve_impl(const Dev& d, BlockPos bp) {
   double* res = x + P;
   double* b = res + P;
   double* dg = b + P;
-  LinkTable* lt = reinterpret_cast<LinkTable*>(smem_raw + ((((size_t)P * P + 4 * P) * 8 + 15) & ~(size_t)15));
+  double* p2 = dg + P;  // (lambda_s S_kk)^2
+  double* th = p2 + P;  // Theta
+  LinkTable* lt = reinterpret_cast<LinkTable*>(smem_raw + ((((size_t)P * P + 6 * P) * 8 + 15) & ~(size_t)15));
   DQ* H0 = reinterpret_cast<DQ*>(reinterpret_cast<unsigned char*>(lt) + ((sizeof(LinkTable) + 15) & ~(size_t)15));
   __shared__ unsigned rmax_bits, bmax_bits;
-  for (int t = tid; t < (int)(sizeof(LinkTable) / 4); t += nt)
-    reinterpret_cast<int*>(lt)[t] = reinterpret_cast<const int*>(d.links)[t];
+  __shared__ unsigned char frz[kMaxPad];
+  // ---- inputs in one round trip: the link table, A (P x P at row stride NP), its diagonal and last column
+  for (int t = tid; t < (int)(sizeof(LinkTable) / 16); t += nt)
+    cp_async16(reinterpret_cast<char*>(lt) + 16 * t, reinterpret_cast<const char*>(d.links) + 16 * t);
+  for (int e = tid; e < P * P; e += nt) cp_async8(M + e, d.A + (size_t)(e / P) * NP + e % P);
+  for (int r = tid; r < P; r += nt) {
+    cp_async8(dg + r, d.A + (size_t)r * NP + r);
+    cp_async8(b + r, d.A + (size_t)r * NP + P);
+    cp_async8(p2 + r, d.prior2 + r);
+    cp_async8(th + r, d.theta + r);
+  }
   double lam = *d.lam;
   for (int t = 0; t < c; ++t) lam = fmin(lam * 10.0, 1e7);
-  for (int r = tid; r < P; r += nt) dg[r] = d.A[r * NP + r] + d.prior2[r];
   if (tid == 0) bmax_bits = 0u;
+  cp_async_wait_all();
   __syncthreads();
   // ---- setup: M = A + diag(prior + lambda dg) (FP64), frozen rows/columns -> identity; scale D in FP32
-  for (int r = tid; r < Pp; r += nt) {
-    if (r >= P) { sc[r] = 1.f; continue; }
-    const bool fr = dg[r] == 0.0;
-    sc[r] = fr ? 1.f : rsqrtf((float)(dg[r] * (1.0 + lam)));
-    b[r] = fr ? 0.0 : d.A[r * NP + P] + d.prior2[r] * d.theta[r];
+  for (int r = tid; r < P; r += nt) {  // each thread reads and writes only its own rows here
+    const double dgr = dg[r] + p2[r];
+    const bool fr = dgr == 0.0;
+    dg[r] = dgr;
+    frz[r] = fr;
+    sc[r] = fr ? 1.f : rsqrtf((float)(dgr * (1.0 + lam)));
+    b[r] = fr ? 0.0 : b[r] + p2[r] * th[r];
     x[r] = 0.0;
     res[r] = b[r];
     atomicMax(&bmax_bits, __float_as_uint(fabsf((float)b[r] * sc[r])));
   }
-  for (int e0 = tid; e0 < P * P; e0 += 4 * nt) {
-    double a[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = e0 + u * nt;
-      a[u] = e < P * P ? d.A[(e / P) * NP + e % P] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = e0 + u * nt;
-      if (e >= P * P) continue;
-      const int r = e / P, q = e % P;
-      const bool frozen = dg[r] == 0.0 || dg[q] == 0.0;
-      M[e] = frozen ? (r == q ? 1.0 : 0.0) : a[u] + (r == q ? d.prior2[r] + lam * dg[r] : 0.0);
-    }
+  __syncthreads();
+  // M and, in the same pass, the FP32 lower triangle of D M D (FP64 arithmetic only on the diagonal)
+  for (int e = tid; e < P * P; e += nt) {
+    const int r = e / P, q = e % P;
+    double m = M[e];
+    if (frz[r] | frz[q]) m = r == q ? 1.0 : 0.0;
+    else if (r == q) m = m + (p2[r] + lam * dg[r]);
+    M[e] = m;
+    if (q <= r) F[r][q] = (float)m * sc[r] * sc[q];
+  }
+  for (int e = tid; e < (Pp - P) * Pp; e += nt) {  // identity rows padding P to a multiple of the block
+    const int r = P + e / Pp, q = e % Pp;
+    if (q <= r) F[r][q] = r == q ? 1.f : 0.f;
   }
   __syncthreads();
   // ---- FP32 factor of D M D, padded with identity rows to a multiple of the block size
-  for (int e = tid; e < Pp * Pp; e += nt) {
-    const int r = e / Pp, q = e % Pp;
-    if (q > r) continue;
-    F[r][q] = (r < P && q < P) ? (float)M[r * P + q] * sc[r] * sc[q] : (r == q ? 1.f : 0.f);
-  }
-  __syncthreads();
   const bool ok32 = chol_blocked(F, ivd, Pp);
   // ---- iterative refinement: x += D (D M D)^-1 D (b - M x), residual in FP64
   int iters = 0;
@@ -687,20 +705,28 @@ __device__ __forceinline__ void lm_solve_impl(const Dev& d, BlockPos bp) {
     for (int r = tid; r < P; r += nt) x[r] += (double)sc[r] * (double)ys[r];
     if (tid == 0) rmax_bits = 0u;
     __syncthreads();
-    for (int r = tid; r < P; r += nt) {  // res = b - M x, four independent FP64 accumulators
-      const double* mr = M + (size_t)r * P;
-      double s0 = b[r], s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int q = 0;
-      for (; q + 3 < P; q += 4) {
-        s0 = fma(-mr[q], x[q], s0);
-        s1 = fma(-mr[q + 1], x[q + 1], s1);
-        s2 = fma(-mr[q + 2], x[q + 2], s2);
-        s3 = fma(-mr[q + 3], x[q + 3], s3);
+    // res = b - M x in FP64: four threads per row (columns q = part mod 4, two accumulators each), the
+    // four sums combined by shuffles in a fixed pairing
+    for (int r0 = 0; r0 < P; r0 += nt / 4) {
+      const int r = r0 + (tid >> 2), part = tid & 3;
+      double s0 = 0.0, s1 = 0.0;
+      if (r < P) {
+        const double* mr = M + (size_t)r * P;
+        int q = part;
+        for (; q + 4 < P; q += 8) {
+          s0 = fma(-mr[q], x[q], s0);
+          s1 = fma(-mr[q + 4], x[q + 4], s1);
+        }
+        if (q < P) s0 = fma(-mr[q], x[q], s0);
       }
-      for (; q < P; ++q) s0 = fma(-mr[q], x[q], s0);
-      const double rres = (s0 + s1) + (s2 + s3);
-      res[r] = rres;
-      atomicMax(&rmax_bits, __float_as_uint(fabsf((float)rres * sc[r])));
+      double sum = s0 + s1;
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+      if (r < P && part == 0) {
+        const double rres = b[r] + sum;
+        res[r] = rres;
+        atomicMax(&rmax_bits, __float_as_uint(fabsf((float)rres * sc[r])));
+      }
     }
     __syncthreads();
     iters = it + 1;
@@ -713,13 +739,17 @@ __device__ __forceinline__ void lm_solve_impl(const Dev& d, BlockPos bp) {
     chol_solve_fp64(M, x, P, fail);
   }
   double* thc = d.theta_c + (size_t)c * P;
-  for (int j = tid; j < P; j += nt) thc[j] = fail ? d.theta[j] : d.theta[j] - x[j];
+  for (int j = tid; j < P; j += nt) {  // the candidate, also kept in shared memory (res is free now) for FK
+    const double tj = fail ? th[j] : th[j] - x[j];
+    thc[j] = tj;
+    res[j] = tj;
+  }
   if (tid == 0) {
     d.lm_ok[c] = !fail;
     d.lm_ok[kCandidates + c] = converged ? iters : (fail ? -2 : -1);
   }
   __syncthreads();
-  fk_all(*lt, thc, H0, d.Hd_c + (size_t)c * P, d.xi_c + (size_t)c * P * 8, 8);
+  fk_all(*lt, res, H0, d.Hd_c + (size_t)c * P, d.xi_c + (size_t)c * P * 8, 8);
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_lm_solve(BatchGrid g, Dev d0) {
@@ -874,7 +904,7 @@ __global__ void __launch_bounds__(kBlock) k_lm_eval(BatchGrid g, Dev d0, int phi
 }
 
 static int lm_solve_smem(int L) {
-  return (int)(((((size_t)L * L + 4 * L) * 8 + 15) & ~(size_t)15) + ((sizeof(LinkTable) + 15) & ~(size_t)15) +
+  return (int)(((((size_t)L * L + 6 * L) * 8 + 15) & ~(size_t)15) + ((sizeof(LinkTable) + 15) & ~(size_t)15) +
                (size_t)L * sizeof(DQ));
 }
 

@@ -397,6 +397,43 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
     lt.depth[j] = sk->parent[j] < 0 ? 0 : lt.depth[sk->parent[j]] + 1;
     lt.max_depth = std::max(lt.max_depth, lt.depth[j]);
   }
+  {  // chains of single-child links (parents precede their children), grouped in rounds
+    std::vector<int> nchild(L, 0), only_child(L, -1), chain_of(L, -1), round_of_chain;
+    for (int j = 0; j < L; ++j)
+      if (sk->parent[j] >= 0) {
+        ++nchild[sk->parent[j]];
+        only_child[sk->parent[j]] = j;
+      }
+    std::vector<std::vector<int>> chains;
+    for (int h = 0; h < L; ++h) {
+      const int p = sk->parent[h];
+      if (p >= 0 && nchild[p] == 1) continue;  // continues its parent's chain
+      const int c = (int)chains.size();
+      chains.emplace_back();
+      round_of_chain.push_back(p < 0 ? 0 : round_of_chain[chain_of[p]] + 1);
+      for (int j = h;; j = only_child[j]) {
+        chains[c].push_back(j);
+        chain_of[j] = c;
+        if (nchild[j] != 1) break;
+      }
+    }
+    const int nc = (int)chains.size();
+    int nr = 0;
+    for (int c = 0; c < nc; ++c) nr = std::max(nr, round_of_chain[c] + 1);
+    lt.n_chains = nc;
+    lt.n_rounds = nr;
+    int t = 0, k = 0;
+    for (int r = 0; r < nr; ++r) {
+      lt.round_start[r] = k;
+      for (int c = 0; c < nc; ++c) {
+        if (round_of_chain[c] != r) continue;
+        lt.chain_start[k++] = t;
+        for (int j : chains[c]) lt.chain[t++] = j;
+      }
+    }
+    lt.round_start[nr] = k;
+    lt.chain_start[k] = t;
+  }
   lt.pre.r = make_float4(1.f, 0.f, 0.f, 0.f);
   lt.pre.d = make_float4(0.f, (float)pre.d.x, (float)pre.d.y, (float)pre.d.z);
   std::vector<HDQ> bind(L);

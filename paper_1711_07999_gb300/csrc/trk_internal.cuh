@@ -33,15 +33,25 @@ struct __align__(32) Acc4 {
 // FK starts from pre = T(-c); the bind pose is stored in the same frame.
 struct LinkTable {
   int L;
-  int max_depth;           // links are grouped by depth (root links: 0) for level-synchronous FK
+  int max_depth;  // largest link depth (root links: 0)
   int depth[kMaxLinks];
   int parent[kMaxLinks];
   int type[kMaxLinks];
   float axis[kMaxLinks][3];
+  // The links split into chains: a link continues its parent's chain when it is the parent's only
+  // child, else it starts a chain.  chain[] lists the links chain by chain, each from its head down;
+  // chain c is chain[chain_start[c] .. chain_start[c + 1]).  Chains are grouped in rounds: a chain's
+  // round is one more than the round of the chain holding its head's parent (root chains: round 0), and
+  // round r holds chains round_start[r] .. round_start[r + 1] - 1.
+  int n_chains, n_rounds;
+  int chain[kMaxLinks];
+  int chain_start[kMaxLinks + 1];
+  int round_start[kMaxLinks + 1];
   DQ pre;               // T(-c)
   DQ off[kMaxLinks];
   DQ bindc[kMaxLinks];  // conjugate of the bind-pose DQ T(-c) H^0_{0,j}
 };
+static_assert(sizeof(LinkTable) % 16 == 0, "LinkTable is copied in 16-byte units");
 
 // Per-session constants passed by value to the kernels.
 struct Cam {
@@ -100,50 +110,43 @@ __device__ __forceinline__ DQ joint_dq(int type, const float* z, float th) {
   return h;
 }
 
-// Forward kinematics of link j by walking its chain from the root: H_{0,j} = prod (off_m J_m(theta_m)).
-// Writes H_{j,Delta} = H_{0,j} conj(H^0_{0,j}) and the twist Xi_j = H_{0,j} G_j conj(H_{0,j}) with
-// G_j = (0, z/2 | 0) for a hinge and (0 | 0, z/2) for a prismatic joint (the joint's generator
-// H_j^{-1} dH_j/dtheta_j): dH_{k,Delta}/dtheta_j = Xi_j H_{k,Delta} for every k below j.
-template <typename ThetaT>
-__device__ __forceinline__ void fk_link(const LinkTable& lt, const ThetaT* theta, int j, DQ* Hd_out,
-                                        float* xi_out /*6*/) {
-  int chain[kMaxLinks];
-  int n = 0;
-  for (int k = j; k >= 0; k = lt.parent[k]) chain[n++] = k;
-  DQ H = lt.pre;
-  for (int t = n - 1; t >= 0; --t) {
-    int m = chain[t];
-    H = dqmul(dqmul(H, lt.off[m]), joint_dq(lt.type[m], lt.axis[m], (float)theta[m]));
-  }
-  *Hd_out = dqmul(H, lt.bindc[j]);
-  DQ G;
-  const float* z = lt.axis[j];
-  if (lt.type[j] == 0) {
-    G.r = make_float4(0.f, 0.5f * z[0], 0.5f * z[1], 0.5f * z[2]);
-    G.d = make_float4(0.f, 0.f, 0.f, 0.f);
-  } else {
-    G.r = make_float4(0.f, 0.f, 0.f, 0.f);
-    G.d = make_float4(0.f, 0.5f * z[0], 0.5f * z[1], 0.5f * z[2]);
-  }
-  DQ X = dqmul(dqmul(H, G), dqconj(H));
-  xi_out[0] = X.r.y; xi_out[1] = X.r.z; xi_out[2] = X.r.w;
-  xi_out[3] = X.d.y; xi_out[4] = X.d.z; xi_out[5] = X.d.w;
+// Asynchronous global -> shared copies (cp.async); cp_async_wait_all() waits for all of this thread's.
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((uint32_t)__cvta_generic_to_shared(s)),
+               "l"(__cvta_generic_to_global(g))
+               : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(s)),
+               "l"(__cvta_generic_to_global(g))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Block-level FK of all links, level by level (every link of one depth in parallel, a barrier between
-// levels), with the joint transforms' sines and cosines computed up front in parallel.  Same products
-// in the same order as fk_link.  H0 (shared, [L]) is scratch; all threads of the block must call it.
+// Forward kinematics of all links (Sec. 3.1): H_{0,j} = H_{0,parent(j)} off_j J_j(theta_j) (H_{0,-1} = the
+// root transform pre), formed as (H_{0,parent} off_j) J_j.  Writes H_{j,Delta} = H_{0,j} conj(H^0_{0,j})
+// and the twist Xi_j = H_{0,j} G_j conj(H_{0,j}) with G_j = (0, z/2 | 0) for a hinge and (0 | 0, z/2) for
+// a prismatic joint (the joint's generator H_j^{-1} dH_j/dtheta_j): dH_{k,Delta}/dtheta_j = Xi_j H_{k,Delta}
+// for every k below j.
+//
+// One thread walks each chain of single-child links (a 3-DoF joint is three such links), the chains of a
+// round in parallel, one barrier per round: the products are those of a link-by-link walk from the root,
+// with ~3x fewer barriers.  H0 (shared, [L]) is scratch; all threads of the block must call it.
 template <typename ThetaT>
 __device__ __forceinline__ void fk_all(const LinkTable& lt, const ThetaT* theta, DQ* H0, DQ* Hd_out, float* xi_out,
                                        int xi_stride) {
   const int L = lt.L;
   for (int j = threadIdx.x; j < L; j += blockDim.x) H0[j] = joint_dq(lt.type[j], lt.axis[j], (float)theta[j]);
   __syncthreads();
-  for (int lev = 0; lev <= lt.max_depth; ++lev) {
-    for (int j = threadIdx.x; j < L; j += blockDim.x) {
-      if (lt.depth[j] != lev) continue;
-      const DQ par = lt.parent[j] < 0 ? lt.pre : H0[lt.parent[j]];
-      H0[j] = dqmul(dqmul(par, lt.off[j]), H0[j]);
+  for (int r = 0; r < lt.n_rounds; ++r) {
+    for (int c = lt.round_start[r] + threadIdx.x; c < lt.round_start[r + 1]; c += blockDim.x) {
+      const int head = lt.chain[lt.chain_start[c]];
+      DQ H = lt.parent[head] < 0 ? lt.pre : H0[lt.parent[head]];
+      for (int t = lt.chain_start[c]; t < lt.chain_start[c + 1]; ++t) {
+        const int j = lt.chain[t];
+        H = dqmul(dqmul(H, lt.off[j]), H0[j]);
+        H0[j] = H;
+      }
     }
     __syncthreads();
   }
