@@ -150,17 +150,29 @@ __device__ __forceinline__ void visibility_impl(const Dev& d, BlockPos bp) {
   const int i = bp.x * blockDim.x + threadIdx.x;
   if (i >= d.V) return;
   float3 s = make_float3(0.f, 0.f, 0.f);
-  const int e = d.csr_off[i + 1];
-  for (int t = d.csr_off[i]; t < e; ++t) {
-    const float4 fn = d.fn[d.csr_face[t]];
-    s.x += fn.x; s.y += fn.y; s.z += fn.z;
+  const int b = d.csr_off[i], e = d.csr_off[i + 1];
+  const float4 pl = d.v[i];
+  // incident faces in groups of 8: all indices, then all normals in flight, then added in order
+  for (int t0 = b; t0 < e; t0 += 8) {
+    int f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = t0 + k < e ? d.csr_face[t0 + k] : -1;
+    float4 fn[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fn[k] = f[k] >= 0 ? d.fn[f[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (f[k] >= 0) {
+        s.x += fn[k].x;
+        s.y += fn[k].y;
+        s.z += fn[k].z;
+      }
   }
   const float len = sqrtf(dot3(s, s));
   const bool valid = len >= 1e-12f;
   const float3 n = valid ? make_float3(s.x / len, s.y / len, s.z / len) : make_float3(0.f, 0.f, 0.f);
   d.n[i] = make_float4(n.x, n.y, n.z, valid ? 1.f : 0.f);
   int vp = -1;
-  const float4 pl = d.v[i];
   const Cam c = d.cam;
   const float3 p = make_float3(pl.x + c.ox, pl.y + c.oy, pl.z + c.oz);  // camera frame
   if (valid && p.z > c.z_near) {

@@ -51,22 +51,32 @@ __device__ __forceinline__ void load_link_tables(const Dev& d, DQ* sHd, float* s
 }
 
 // This block's vertices in A (c_i >= 1 and a valid normal) and each one's row slot, compacted in vertex
-// order.  Contains a __syncthreads; returns the number of rows (the same in every thread).
+// order, with every input of the vertex's row (all loaded at once: one round trip, the point data of
+// vertices outside A read and dropped).  Contains a __syncthreads; returns the number of rows (the same
+// in every thread).
 struct RowSlot {
   int i, slot;
   bool inA;
   Acc4 a4;
-  float4 nn;
+  float4 nn, v, x0, ph, bw;
+  uchar4 bi;
 };
-__device__ __forceinline__ int block_rows(const Dev& d, int blk, int* s_warp, RowSlot& rs) {
+__device__ __forceinline__ int block_rows(const Dev& d, int blk, int phi_buf, int* s_warp, RowSlot& rs) {
   const int tid = threadIdx.x;
   rs.i = blk * kBlock + tid;
   rs.inA = false;
   rs.a4 = Acc4{0, 0, 0, 0};
   rs.nn = make_float4(0.f, 0.f, 0.f, 0.f);
+  rs.v = rs.x0 = rs.ph = rs.bw = rs.nn;
+  rs.bi = make_uchar4(0, 0, 0, 0);
   if (rs.i < d.V) {
     rs.a4 = d.acc[rs.i];
     rs.nn = d.n[rs.i];
+    rs.v = d.v[rs.i];
+    rs.x0 = d.v0[rs.i];
+    rs.ph = d.phi[phi_buf][rs.i];
+    rs.bi = d.bidx[rs.i];
+    rs.bw = d.bw[rs.i];
     rs.inA = rs.a4.w >= 1 && rs.nn.w > 0.f;
   }
   const unsigned m = __ballot_sync(0xffffffffu, rs.inA);
@@ -89,7 +99,6 @@ __device__ __forceinline__ void jacobian_row(const Dev& d, const RowSlot& rs, in
                                              int width, const DQ* sHd, const float* sXi, const int* sPar, float& r2) {
   r2 = 0.f;
   if (!rs.inA) return;
-  const int i = rs.i;
   const Acc4 a4 = rs.a4;
   float* row = Js + rs.slot * ROW;
   for (int k = 0; k < width; ++k) row[k] = 0.f;
@@ -100,10 +109,10 @@ __device__ __forceinline__ void jacobian_row(const Dev& d, const RowSlot& rs, in
   row[d.L] = r;
   r2 = r * r;
   float sg[4];
-  const uchar4 bi = d.bidx[i];
-  const float4 bw = d.bw[i];
+  const uchar4 bi = rs.bi;
+  const float4 bw = rs.bw;
   const DQ H = blend_bones(sHd, bi, bw, sg);
-  const float4 x0 = d.v0[i], ph = d.phi[phi_buf][i], v = d.v[i];
+  const float4 x0 = rs.x0, ph = rs.ph, v = rs.v;
   const float4 X = make_float4(0.f, x0.x + ph.x, x0.y + ph.y, x0.z + ph.z);
   const float4 Np = make_float4(0.f, n.x, n.y, n.z);
   const float invN = 1.f / qdot(H.r, H.r);
@@ -112,16 +121,75 @@ __device__ __forceinline__ void jacobian_row(const Dev& d, const RowSlot& rs, in
   const float4 cd = qscale(Na, 2.f * invN);
   const int idx[4] = {bi.x, bi.y, bi.z, bi.w};
   const float ws[4] = {bw.x, bw.y, bw.z, bw.w};
+  // e_b of every weighted bone, keyed by its link (-1: no weight)
+  int key[4];
+  float es[4][6];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
+    key[s] = -1;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) es[s][c] = 0.f;
     if (!(ws[s] > 0.f)) continue;
+    key[s] = idx[s];
     const DQ h = sHd[idx[s]];
     const float sc = ws[s] * sg[s];
     const float3 e1 = Lfun(cr, h.r), e2 = Lfun(cd, h.d), e3 = Lfun(cd, h.r);
-    const float e[6] = {sc * (e1.x + e2.x), sc * (e1.y + e2.y), sc * (e1.z + e2.z), sc * e3.x, sc * e3.y, sc * e3.z};
-    for (int k = idx[s]; k >= 0; k = sPar[k]) {
+    es[s][0] = sc * (e1.x + e2.x);
+    es[s][1] = sc * (e1.y + e2.y);
+    es[s][2] = sc * (e1.z + e2.z);
+    es[s][3] = sc * e3.x;
+    es[s][4] = sc * e3.y;
+    es[s][5] = sc * e3.z;
+  }
+  // J_ik = -Xi_k . (sum of e_b over the bones b at or below k).  The bones, sorted by link (parents
+  // precede their children), are walked to the root from the deepest one; a bone met on the way joins
+  // the running sum, so a link shared by several bones' chains is visited once.  A bone on another
+  // branch is not met and starts its own walk afterwards (sums are linear, so every bone still reaches
+  // each of its ancestors exactly once).
+  auto cswap = [&](int a, int b) {
+    if (key[a] < key[b]) {
+      const int t = key[a];
+      key[a] = key[b];
+      key[b] = t;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const float u = es[a][c];
+        es[a][c] = es[b][c];
+        es[b][c] = u;
+      }
+    }
+  };
+  cswap(0, 1);
+  cswap(2, 3);
+  cswap(0, 2);
+  cswap(1, 3);
+  cswap(1, 2);
+  auto pop = [&]() {  // drops the head of the sorted queue
+    key[0] = key[1];
+    key[1] = key[2];
+    key[2] = key[3];
+    key[3] = -1;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      es[0][c] = es[1][c];
+      es[1][c] = es[2][c];
+      es[2][c] = es[3][c];
+    }
+  };
+  while (key[0] >= 0) {
+    int k = key[0];
+    float E[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) E[c] = es[0][c];
+    pop();
+    for (; k >= 0; k = sPar[k]) {
+      while (key[0] == k) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) E[c] += es[0][c];
+        pop();
+      }
       const float* xk = sXi + 6 * k;
-      row[k] -= xk[0] * e[0] + xk[1] * e[1] + xk[2] * e[2] + xk[3] * e[3] + xk[4] * e[4] + xk[5] * e[5];
+      row[k] -= xk[0] * E[0] + xk[1] * E[1] + xk[2] * E[2] + xk[3] * E[3] + xk[4] * E[4] + xk[5] * E[5];
     }
   }
 }
@@ -137,7 +205,7 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
   __shared__ int s_warp[kBlock / 32];
   const int tid = threadIdx.x;
   RowSlot rs;
-  const int total = block_rows(d, bp.x, s_warp, rs);
+  const int total = block_rows(d, bp.x, phi_buf, s_warp, rs);
   if (total == 0) {  // nothing to add: the reduction skips this block's (unwritten) partial
     if (tid == 0) d.jtj_rows[bp.x] = 0;
     return;
@@ -231,7 +299,7 @@ __device__ __forceinline__ void resid_jtj_tc_impl(const Dev& d, BlockPos bp, int
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int NP = d.NP;
   RowSlot rs;
-  const int total = block_rows(d, bp.x, s_warp, rs);
+  const int total = block_rows(d, bp.x, phi_buf, s_warp, rs);
   if (total == 0) {  // nothing to add: no TMEM is taken and the reduction skips this block
     if (tid == 0) d.jtj_rows[bp.x] = 0;
     return;
@@ -778,31 +846,34 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
   __shared__ int sok[kCandidates];
   __shared__ double swarp[kBlock / 32][kCandidates];
   __shared__ bool last;
-  const int L = d.L, tid = threadIdx.x;
+  const int L = d.L, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (c0 > 0 && d.lm_trials[7] != kPending) return;  // the first pass decided
+  // every input of the vertex is loaded at once (one round trip; the point data of vertices outside A is
+  // read and dropped), together with the candidates' tables
   const int i = bp.x * kBlock + tid;
   Acc4 a4 = Acc4{0, 0, 0, 0};
-  float4 nn = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 nn = make_float4(0.f, 0.f, 0.f, 0.f), v = nn, x0 = nn, ph = nn, bw = nn;
+  uchar4 bi = make_uchar4(0, 0, 0, 0);
   if (i < d.V) {
     a4 = d.acc[i];
     nn = d.n[i];
+    v = d.v[i];
+    x0 = d.v0[i];
+    ph = d.phi[phi_buf][i];
+    bi = d.bidx[i];
+    bw = d.bw[i];
   }
-  const bool inA = i < d.V && a4.w >= 1 && nn.w > 0.f;
+  for (int t = c0 * L + tid; t < c1 * L; t += kBlock) sH[t] = d.Hd_c[t];
   if (tid < kCandidates) sok[tid] = d.lm_ok[tid];
-  if (__syncthreads_or(inA)) {  // the candidates' tables are needed only where a vertex of A is
-    for (int t = c0 * L + tid; t < c1 * L; t += kBlock) sH[t] = d.Hd_c[t];
-    __syncthreads();
-  }
+  __syncthreads();
+  const bool inA = i < d.V && a4.w >= 1 && nn.w > 0.f;
   float e[kCandidates];
 #pragma unroll
   for (int c = 0; c < kCandidates; ++c) e[c] = 0.f;
   if (inA) {
     const float inv = 1.f / ((float)a4.w * kFix);
     const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
-    const float4 v = d.v[i], x0 = d.v0[i], ph = d.phi[phi_buf][i];
     const float3 x = make_float3(x0.x + ph.x, x0.y + ph.y, x0.z + ph.z);
-    const uchar4 bi = d.bidx[i];
-    const float4 bw = d.bw[i];
 #pragma unroll
     for (int c = 0; c < kCandidates; ++c) {
       if (c < c0 || c >= c1 || !sok[c]) continue;
@@ -816,12 +887,14 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
 #pragma unroll
   for (int c = 0; c < kCandidates; ++c)
     for (int o = 16; o > 0; o >>= 1) e[c] += __shfl_xor_sync(0xffffffffu, e[c], o);
-  if ((tid & 31) == 0)
-    for (int c = 0; c < kCandidates; ++c) swarp[tid >> 5][c] = e[c];
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < kCandidates; ++c) swarp[w][c] = e[c];
+  }
   __syncthreads();
   if (tid >= c0 && tid < c1) {
     double s = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) s += swarp[w][tid];
+    for (int k = 0; k < kBlock / 32; ++k) s += swarp[k][tid];
     d.epart[(size_t)bp.x * 8 + tid] = s;
   }
   __threadfence();
@@ -830,27 +903,39 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
   __syncthreads();
   if (!last) return;
   __threadfence();
-  __shared__ double red[kBlock][kCandidates];
-  __shared__ double Ec[kCandidates];
+  // the session's last block: sum of the block energies (strided over the threads, then a shuffle tree
+  // and the 8 warp sums in order) plus each candidate's prior term (warp c, lanes over the links)
+  __shared__ double Ec[kCandidates], pri[kCandidates];
   {
     double s6[kCandidates] = {0, 0, 0, 0, 0, 0};
-    for (int b = tid; b < bp.gx; b += kBlock)
-      for (int c = c0; c < c1; ++c) s6[c] += __ldcg(d.epart + (size_t)b * 8 + c);
-    for (int c = 0; c < kCandidates; ++c) red[tid][c] = s6[c];
+    for (int b = tid; b < bp.gx; b += kBlock) {
+#pragma unroll
+      for (int c = 0; c < kCandidates; ++c)
+        if (c >= c0 && c < c1) s6[c] += __ldcg(d.epart + (size_t)b * 8 + c);
+    }
+#pragma unroll
+    for (int c = 0; c < kCandidates; ++c)
+      for (int o = 16; o > 0; o >>= 1) s6[c] += __shfl_xor_sync(0xffffffffu, s6[c], o);
+    __syncthreads();  // swarp is reused
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < kCandidates; ++c) swarp[w][c] = s6[c];
+    }
+    if (w >= c0 && w < c1) {
+      const double* thc = d.theta_c + (size_t)w * L;
+      double p = 0.0;
+      for (int k = lane; k < L; k += 32) p += d.prior2[k] * thc[k] * thc[k];
+      for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+      if (lane == 0) pri[w] = p;
+    }
   }
   __syncthreads();
-  for (int h = kBlock / 2; h > 0; h >>= 1) {
-    if (tid < h)
-      for (int c = c0; c < c1; ++c) red[tid][c] += red[tid + h][c];
-    __syncthreads();
-  }
   const double inf = __longlong_as_double(0x7ff0000000000000ll);
   if (tid < kCandidates) {
     if (tid >= c0 && tid < c1) {
-      double s = red[0][tid];
-      const double* thc = d.theta_c + (size_t)tid * L;
-      for (int k = 0; k < L; ++k) s += d.prior2[k] * thc[k] * thc[k];
-      Ec[tid] = sok[tid] ? s : inf;
+      double s = 0.0;
+      for (int k = 0; k < kBlock / 32; ++k) s += swarp[k][tid];
+      Ec[tid] = sok[tid] ? s + pri[tid] : inf;
     } else {
       Ec[tid] = tid < c0 ? d.lm_trials[tid] : inf;  // the first pass's energies; later ones unscored
     }
@@ -974,12 +1059,12 @@ __device__ __forceinline__ void block_energy_to_slot(const Dev& d, BlockPos bp, 
 }
 
 // r_i (the mean offset of the associated pixels along n_i) and g_i = dr_i/dphi_i = -R(a^_i)^T n_i.
-__device__ __forceinline__ void vertex_r_g(const Dev& d, const DQ* sHd, int i, const Acc4& a4, const float4& nn,
+__device__ __forceinline__ void vertex_r_g(const DQ* sHd, uchar4 bi, float4 bw, const Acc4& a4, const float4& nn,
                                            float& r, float3& g) {
   const float inv = 1.f / ((float)a4.w * kFix);
   r = nn.x * (float)a4.x * inv + nn.y * (float)a4.y * inv + nn.z * (float)a4.z * inv;
   float sg[4];
-  const DQ H = blend_bones(sHd, d.bidx[i], d.bw[i], sg);
+  const DQ H = blend_bones(sHd, bi, bw, sg);
   const float4 ah = qscale(H.r, rsqrtf(qdot(H.r, H.r)));
   const float4 q = qmul(qmul(qconj(ah), make_float4(0.f, nn.x, nn.y, nn.z)), ah);  // R^T n
   g = make_float3(-q.y, -q.z, -q.w);
@@ -989,35 +1074,42 @@ __device__ __forceinline__ void shape_impl(const Dev& d, BlockPos bp, int src, i
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DQ* sHd = reinterpret_cast<DQ*>(smem_raw);
   const int i = bp.x * kBlock + threadIdx.x;
-  bool anyA = false;
-  if (i < d.V) anyA = d.acc[i].w >= 1 && d.n[i].w > 0.f;
-  if (__syncthreads_or(anyA)) {  // the pose tables are needed only where a vertex of A is
-    for (int j = threadIdx.x; j < d.L; j += kBlock) sHd[j] = d.Hd[j];
-    __syncthreads();
+  // the vertex's own inputs in one round trip, with the pose tables; the neighbours' offsets (and the
+  // skinning weights of a vertex of A) follow in a second
+  const float4* phi = d.phi[src];
+  float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f), nn = p4;
+  Acc4 a4 = Acc4{0, 0, 0, 0};
+  int4 nb = make_int4(-1, -1, -1, -1);
+  if (i < d.V) {
+    p4 = phi[i];
+    a4 = d.acc[i];
+    nn = d.n[i];
+    nb = d.nbr[i];
   }
+  for (int j = threadIdx.x; j < d.L; j += kBlock) sHd[j] = d.Hd[j];
+  __syncthreads();
+  const int nbs[4] = {nb.x, nb.y, nb.z, nb.w};
+  float4 qn[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) qn[t] = t < d.knn && nbs[t] >= 0 ? phi[nbs[t]] : make_float4(0.f, 0.f, 0.f, 0.f);
   float e = 0.f;
   int inA_count = 0;
   if (i < d.V) {
-    const float4* phi = d.phi[src];
-    const float4 p4 = phi[i];
     const float3 pi = f3(p4);
-    const Acc4 a4 = d.acc[i];
-    const float4 nn = d.n[i];
     const bool inA = a4.w >= 1 && nn.w > 0.f;
     float r = 0.f;
     float3 g = make_float3(0.f, 0.f, 0.f);
     if (inA) {
       inA_count = 1;
-      vertex_r_g(d, sHd, i, a4, nn, r, g);
+      vertex_r_g(sHd, d.bidx[i], d.bw[i], a4, nn, r, g);
     }
     e = r * r + d.lambda_phi * dot3(pi, pi);
     float3 sd = make_float3(0.f, 0.f, 0.f);
     int nn_count = 0;
-    const int4 nb = d.nbr[i];
-    const int nbs[4] = {nb.x, nb.y, nb.z, nb.w};
-    for (int t = 0; t < d.knn; ++t) {
-      if (nbs[t] < 0) continue;
-      const float3 q = f3(phi[nbs[t]]);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (t >= d.knn || nbs[t] < 0) continue;
+      const float3 q = f3(qn[t]);
       const float3 df = make_float3(pi.x - q.x, pi.y - q.y, pi.z - q.z);
       e += d.lambda_N * dot3(df, df);
       sd.x += df.x; sd.y += df.y; sd.z += df.z;
@@ -1152,7 +1244,7 @@ __device__ __forceinline__ void cg_init_impl(const Dev& d, BlockPos bp, int src,
     float3 g = make_float3(0.f, 0.f, 0.f);
     if (a4.w >= 1 && nn.w > 0.f) {
       inA_count = 1;
-      vertex_r_g(d, sHd, i, a4, nn, r, g);
+      vertex_r_g(sHd, d.bidx[i], d.bw[i], a4, nn, r, g);
     }
     e = r * r + d.lambda_phi * dot3(pi, pi);
     const int4 nb = d.nbr[i];

