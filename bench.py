@@ -129,7 +129,7 @@ class ClockSampler:
 def algorithmic(stage, V, F, npx, NP, nvis, nassoc_px, nA, n_valid_px, nblk):
     """Minimum bytes (or FP64 flops) a stage must move for one session: V vertices, F triangles, npx
     pixels, NP = links + 1, nvis visible vertices, nassoc_px associated pixels, nA vertices in A,
-    n_valid_px valid depth pixels, nblk [J r] blocks that hold rows."""
+    n_valid_px valid depth pixels, nblk [J r] blocks (256 jtj_group vertices each) that hold rows."""
     if stage == "skin":  # v0, phi, bone idx, bone w in; v out; sums cleared; z-buffer, heads, corr cleared
         return "hbm", V * (16 + 16 + 4 + 16 + 16 + 32) + npx * (8 + 4 + 4)
     if stage == "raster":  # triangles, posed vertices, face normals out, covered z-buffer words
@@ -138,12 +138,13 @@ def algorithmic(stage, V, F, npx, NP, nvis, nassoc_px, nA, n_valid_px, nblk):
         return "hbm", V * (4 + 16 + 16 + 4) + 3 * F * 4 + F * 16 + nvis * (8 + 4 + 16)
     if stage == "associate":  # depth in, corr out, bucket heads, visible records, per-vertex sums
         return "hbm", n_valid_px * (4 + 4 + 4) + nvis * 16 + nassoc_px * 32
-    if stage == "resid_jtj":  # sums and normals of every vertex; streams of A; partials of blocks with rows
-        return "hbm", V * (32 + 16) + nA * (4 + 16 + 16 + 16 + 16) + nblk * NP * NP * 4
+    if stage == "resid_jtj":  # sums and normals of every vertex; streams of A; partials of blocks with rows;
+        # the 64-byte record of every row for the candidate energies
+        return "hbm", V * (32 + 16) + nA * (4 + 16 + 16 + 16 + 16) + nblk * NP * NP * 4 + nA * 64
     if stage == "reduce":
         return "hbm", nblk * NP * NP * 4 + NP * NP * 8
-    if stage == "lm_eval":  # sums and normals of every vertex; the streams of A for six candidates
-        return "hbm", V * (32 + 16) + nA * (16 + 16 + 16 + 4 + 16)
+    if stage == "lm_eval":  # the rows' records and row counts (the first pass: candidates 0 and 1)
+        return "hbm", nA * 64 + nblk * 4
     if stage == "shape":  # phi, neighbours, sums, normals in; phi, r/g, phi0 out; bones of A
         return "hbm", V * (16 + 16 + 32 + 16 + 16 + 16 + 16) + nA * (4 + 16)
     if stage == "lm_solve":  # 6 FP64 Cholesky factorisations + solves of the P x P system
@@ -158,7 +159,7 @@ def session_counts(sess, depth):
     acc = sess.read("ACC")
     NP = info["n_links"] + 1
     nA = int((acc[:, 3] > 0).sum())
-    blocks = (np.nonzero(acc[:, 3] > 0)[0] // 256)
+    blocks = (np.nonzero(acc[:, 3] > 0)[0] // (256 * info["jtj_group"]))
     return dict(V=info["n_verts"], F=info["n_tris"], npx=info["width"] * info["height"], NP=NP,
                 nvis=int((sess.read("VISPIX") >= 0).sum()), nassoc_px=int(acc[:, 3].sum()), nA=nA,
                 n_valid_px=int((np.asarray(depth) > 0).sum()), nblk=int(len(np.unique(blocks))))

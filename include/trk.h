@@ -90,6 +90,9 @@ typedef struct {
                            conditions, Sec. 5)                                                       */
   int32_t association;  /* 0: the closest visible vertex in the window (Sec. 4.1); 1: the nearest
                            corner of the triangle the z-buffer holds at the pixel (O(1) per pixel)   */
+  int32_t jtj_group;    /* vertices per block of the [J r]^T [J r] contraction, in units of 256: 1, 2
+                           or 4 (fewer block partials to add; FP32 precision only), 0: chosen from the
+                           mesh size (1 up to 304 units, 2 up to 608, else 4)                         */
 } trk_params;
 
 /* TRACK: every frame estimates the shape (the full method).  SHAPE_MATCH: only the first frame after
@@ -231,6 +234,7 @@ typedef struct {
   int32_t n_links, n_verts, n_tris, width, height;
   int32_t kernels_per_frame; /* kernel launches in one trk_track_frame                          */
   size_t device_bytes;       /* device memory the session holds                                  */
+  int32_t jtj_group;         /* the [J r] contraction's vertices per block / 256 (trk_params)     */
 } trk_info;
 trk_status trk_get_info(trk_session* s, trk_info* out);
 

@@ -25,8 +25,9 @@ using namespace trk;
 
 namespace {
 
-// kJtj1..kJtj5: the [J r] blocks of the sessions with tile width class ceil(NP / 16) = 1..5
-enum Kind { kSkin, kTris, kVerts, kAssoc, kJtj1, kJtj2, kJtj3, kJtj4, kJtj5, kReduce, kLm, kKinds };
+// kJtj1..kJtj5: the [J r] blocks of the sessions with tile width class ceil(NP / 16) = 1..5; kRows: the
+// [J r] blocks of every session (the candidate energies read their rows)
+enum Kind { kSkin, kTris, kVerts, kAssoc, kJtj1, kJtj2, kJtj3, kJtj4, kJtj5, kReduce, kLm, kRows, kKinds };
 constexpr int kSrcSlots = 4;
 constexpr int kMaxBatch = 4096;  // the tail's prefix kernel scans up to 1024 x 4 sessions
 
@@ -71,9 +72,10 @@ void blocks_of(const Dev& d, Kind k, int& gx, int& gy) {
     case kVerts: gx = d.nblk_v; break;
     case kAssoc: gx = (d.cam.W + 15) / 16; gy = (d.cam.H + 15) / 16; break;
     case kJtj1: case kJtj2: case kJtj3: case kJtj4: case kJtj5:
-      gx = (d.NP + 15) / 16 == k - kJtj1 + 1 ? d.nblk_jtj : 0;
+      gx = (d.NP + 15) / 16 == k - kJtj1 + 1 ? d.nblk_rows : 0;
       break;
     case kReduce: gx = (d.NP * d.NP + 31) / 32; break;
+    case kRows: gx = d.nblk_rows; break;
     default: gx = kCandidates; break;  // kLm
   }
 }
@@ -100,7 +102,7 @@ void enqueue_batch_frame(trk_batch* b, cudaStream_t st) {
       nj[t] = b->tables[kJtj1 + t].n;
     }
     launch_normal_equations_b(gj, nj, grid_of(b, kReduce), b->tables[kReduce].n, L, b->precision, cur, it, st);
-    launch_lm_b(grid_of(b, kLm), b->tables[kLm].n, grid_of(b, kVerts), b->tables[kVerts].n, L, cur, st);
+    launch_lm_b(grid_of(b, kLm), b->tables[kLm].n, grid_of(b, kRows), b->tables[kRows].n, L, cur, st);
   }
   for (int it = 0; it < S; ++it) {
     geometry();
@@ -319,8 +321,8 @@ trk_status trk_batch_profile(trk_batch* b, const float* const* d_depths, int32_t
       err = timed(TRK_STAGE_REDUCE, [&] {
         launch_normal_equations_b(gj, nz, grid_of(b, kReduce), b->tables[kReduce].n, L, b->precision, 0, -1, st);
       });
-    if (!err) err = timed(TRK_STAGE_LM_SOLVE, [&] { launch_lm_b(grid_of(b, kLm), b->tables[kLm].n, grid_of(b, kVerts), 0, L, 0, st); });
-    if (!err) err = timed(TRK_STAGE_LM_EVAL, [&] { launch_lm_b(grid_of(b, kLm), 0, grid_of(b, kVerts), b->tables[kVerts].n, L, 0, st); });
+    if (!err) err = timed(TRK_STAGE_LM_SOLVE, [&] { launch_lm_b(grid_of(b, kLm), b->tables[kLm].n, grid_of(b, kRows), 0, L, 0, st); });
+    if (!err) err = timed(TRK_STAGE_LM_EVAL, [&] { launch_lm_b(grid_of(b, kLm), 0, grid_of(b, kRows), b->tables[kRows].n, L, 0, st); });
   }
   for (int r = 0; r < reps && err == cudaSuccess; ++r) {
     launch_skin_b(grid_of(b, kSkin), b->tables[kSkin].n, L, 0, b->d_ctl, st);

@@ -55,15 +55,17 @@ __device__ __forceinline__ void load_link_tables(const Dev& d, DQ* sHd, float* s
 // vertices outside A read and dropped).  Contains a __syncthreads; returns the number of rows (the same
 // in every thread).
 struct RowSlot {
-  int i, slot;
+  int i, slot, base;  // vertex, its row among the vertex block's rows, the record index of row 0
   bool inA;
   Acc4 a4;
   float4 nn, v, x0, ph, bw;
   uchar4 bi;
 };
-__device__ __forceinline__ int block_rows(const Dev& d, int blk, int phi_buf, int* s_warp, RowSlot& rs) {
+__device__ __forceinline__ int block_rows(const Dev& d, int blk, int row_base, int phi_buf, int* s_warp,
+                                         RowSlot& rs) {
   const int tid = threadIdx.x;
   rs.i = blk * kBlock + tid;
+  rs.base = row_base;
   rs.inA = false;
   rs.a4 = Acc4{0, 0, 0, 0};
   rs.nn = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -114,6 +116,15 @@ __device__ __forceinline__ void jacobian_row(const Dev& d, const RowSlot& rs, in
   const DQ H = blend_bones(sHd, bi, bw, sg);
   const float4 x0 = rs.x0, ph = rs.ph, v = rs.v;
   const float4 X = make_float4(0.f, x0.x + ph.x, x0.y + ph.y, x0.z + ph.z);
+  {  // the row's record for the candidate energies: p~ = v + pm, n, x = x0 + phi, bones and weights
+    float4* rec = d.arec + (size_t)(rs.base + rs.slot) * 4;
+    unsigned bits;
+    memcpy(&bits, &bi, 4);
+    rec[0] = make_float4(v.x + pm.x, v.y + pm.y, v.z + pm.z, n.x);
+    rec[1] = make_float4(n.y, n.z, X.y, X.z);
+    rec[2] = make_float4(X.w, bw.x, bw.y, bw.z);
+    rec[3] = make_float4(bw.w, __uint_as_float(bits), 0.f, 0.f);
+  }
   const float4 Np = make_float4(0.f, n.x, n.y, n.z);
   const float invN = 1.f / qdot(H.r, H.r);
   const float4 Na = qmul(Np, H.r);
@@ -194,6 +205,8 @@ __device__ __forceinline__ void jacobian_row(const Dev& d, const RowSlot& rs, in
   }
 }
 
+// A [J r] block covers jtj_group consecutive blocks of 256 vertices: each one's rows are formed and
+// staged in turn and added to the same tiles, so the block writes one partial for up to 256 G rows.
 template <int T>
 __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int phi_buf) {
   constexpr int ROW = 16 * T + 1;
@@ -203,18 +216,7 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
   float* sXi = reinterpret_cast<float*>(sHd + d.L);
   int* sPar = reinterpret_cast<int*>(sXi + 6 * d.L);
   __shared__ int s_warp[kBlock / 32];
-  const int tid = threadIdx.x;
-  RowSlot rs;
-  const int total = block_rows(d, bp.x, phi_buf, s_warp, rs);
-  if (total == 0) {  // nothing to add: the reduction skips this block's (unwritten) partial
-    if (tid == 0) d.jtj_rows[bp.x] = 0;
-    return;
-  }
-  load_link_tables(d, sHd, sXi, sPar);
-  __syncthreads();
-  float r2;
-  jacobian_row(d, rs, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, r2);
-  __syncthreads();
+  const int tid = threadIdx.x, G = d.jtj_group;
   // the symmetric product needs only the tiles (ty, tx) with ty <= tx among the nt x nt tiles that hold
   // columns < NP: thread k < nt (nt + 1) / 2 takes the k-th of them (row-major), the others idle; each
   // tile is written with its mirror (the mirrored products are the same products in the same order)
@@ -226,25 +228,52 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
     ++ty;
   }
   const int tx = ty + k;
-  if (ty < nt) {
-    float acc[T][T];
+  float acc[T][T];
 #pragma unroll
-    for (int a = 0; a < T; ++a)
+  for (int a = 0; a < T; ++a)
 #pragma unroll
-      for (int b = 0; b < T; ++b) acc[a][b] = 0.f;
-    for (int s = 0; s < total; ++s) {
-      const float* row = Js + s * ROW;
-      float ra[T], rb[T];
-#pragma unroll
-      for (int a = 0; a < T; ++a) {
-        ra[a] = row[ty * T + a];
-        rb[a] = row[tx * T + a];
-      }
-#pragma unroll
-      for (int a = 0; a < T; ++a)
-#pragma unroll
-        for (int b = 0; b < T; ++b) acc[a][b] = fmaf(ra[a], rb[b], acc[a][b]);
+    for (int b = 0; b < T; ++b) acc[a][b] = 0.f;
+  int done = 0;  // rows added so far (the same in every thread)
+  bool tables = false;
+  for (int sub = 0; sub < G; ++sub) {
+    const int vb = bp.x * G + sub;
+    if (vb * kBlock >= d.V) break;
+    RowSlot rs;
+    const int total = block_rows(d, vb, bp.x * kBlock * G + done, phi_buf, s_warp, rs);
+    if (total == 0) {
+      __syncthreads();  // s_warp is rewritten by the next vertex block
+      continue;
     }
+    if (!tables) {
+      load_link_tables(d, sHd, sXi, sPar);
+      tables = true;
+    }
+    __syncthreads();
+    float r2;
+    jacobian_row(d, rs, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, r2);
+    __syncthreads();
+    if (ty < nt) {
+      for (int s = 0; s < total; ++s) {
+        const float* row = Js + s * ROW;
+        float ra[T], rb[T];
+#pragma unroll
+        for (int a = 0; a < T; ++a) {
+          ra[a] = row[ty * T + a];
+          rb[a] = row[tx * T + a];
+        }
+#pragma unroll
+        for (int a = 0; a < T; ++a)
+#pragma unroll
+          for (int b = 0; b < T; ++b) acc[a][b] = fmaf(ra[a], rb[b], acc[a][b]);
+      }
+    }
+    done += total;
+  }
+  if (done == 0) {  // nothing to add: the reduction skips this block's (unwritten) partial
+    if (tid == 0) d.jtj_rows[bp.x] = 0;
+    return;
+  }
+  if (ty < nt) {
     float* out = d.partial + (size_t)bp.x * NP * NP;
 #pragma unroll
     for (int a = 0; a < T; ++a)
@@ -258,8 +287,8 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
       }
   }
   if (tid == 0) {
-    d.jtj_rows[bp.x] = total;
-    atomicAdd(&d.stats[1], total);
+    d.jtj_rows[bp.x] = done;
+    atomicAdd(&d.stats[1], done);
   }
 }
 
@@ -299,7 +328,7 @@ __device__ __forceinline__ void resid_jtj_tc_impl(const Dev& d, BlockPos bp, int
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int NP = d.NP;
   RowSlot rs;
-  const int total = block_rows(d, bp.x, phi_buf, s_warp, rs);
+  const int total = block_rows(d, bp.x, bp.x * kBlock, phi_buf, s_warp, rs);  // jtj_group is 1 here
   if (total == 0) {  // nothing to add: no TMEM is taken and the reduction skips this block
     if (tid == 0) d.jtj_rows[bp.x] = 0;
     return;
@@ -416,7 +445,7 @@ __device__ __forceinline__ void reduce_jtj_impl(const Dev& d, BlockPos bp, int s
   // warp w takes blocks w, w + 32, ... (four loads in flight together); blocks that added no rows wrote
   // no partial and count as zero
   constexpr int S = kReduceThreads / 32;
-  const int nb = d.nblk_jtj;
+  const int nb = d.nblk_rows;
   float hi = 0.f, lo = 0.f;
   if (e < n2) {
     int b = w;
@@ -469,7 +498,7 @@ static int jtj_tc_smem_bytes(int NB, int L) {
 template <int PREC>
 static void launch_resid_jtj_tc(const Dev& d, int phi_buf, cudaStream_t st) {
   const int NB = (d.NP + 15) / 16;
-  const int g = d.nblk_jtj;
+  const int g = d.nblk_rows;
   const int sm = jtj_tc_smem_bytes<PREC>(NB, d.L);
   switch (NB) {
     case 1: k_resid_jtj_tc<PREC, 1><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
@@ -493,7 +522,7 @@ void launch_resid_jtj(const Dev& d, int phi_buf, cudaStream_t st) {
   if (d.precision == 1) return launch_resid_jtj_tc<1>(d, phi_buf, st);
   if (d.precision == 2) return launch_resid_jtj_tc<2>(d, phi_buf, st);
   const int T = (d.NP + 15) / 16;
-  const int g = d.nblk_jtj;
+  const int g = d.nblk_rows;
   const int sm = jtj_smem_bytes(T, d.L);
   switch (T) {
     case 1: k_resid_jtj<1><<<g, kBlock, sm, st>>>(kSingle, d, phi_buf); break;
@@ -848,40 +877,45 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
   __shared__ bool last;
   const int L = d.L, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (c0 > 0 && d.lm_trials[7] != kPending) return;  // the first pass decided
-  // every input of the vertex is loaded at once (one round trip; the point data of vertices outside A is
-  // read and dropped), together with the candidates' tables
-  const int i = bp.x * kBlock + tid;
-  Acc4 a4 = Acc4{0, 0, 0, 0};
-  float4 nn = make_float4(0.f, 0.f, 0.f, 0.f), v = nn, x0 = nn, ph = nn, bw = nn;
-  uchar4 bi = make_uchar4(0, 0, 0, 0);
-  if (i < d.V) {
-    a4 = d.acc[i];
-    nn = d.n[i];
-    v = d.v[i];
-    x0 = d.v0[i];
-    ph = d.phi[phi_buf][i];
-    bi = d.bidx[i];
-    bw = d.bw[i];
+  // the [J r] block's rows (written by the normal-equations pass of this iteration, one record per vertex
+  // of A: the mean data point p~, n, x = x0 + phi, bones and weights), with the candidates' tables
+  const int cnt = d.jtj_rows[bp.x];
+  const float4* recs = d.arec + (size_t)bp.x * kBlock * d.jtj_group * 4;
+  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+  if (tid < cnt) {
+    r0 = recs[4 * tid];
+    r1 = recs[4 * tid + 1];
+    r2 = recs[4 * tid + 2];
+    r3 = recs[4 * tid + 3];
   }
-  for (int t = c0 * L + tid; t < c1 * L; t += kBlock) sH[t] = d.Hd_c[t];
+  if (cnt > 0)  // the same in every thread of the block
+    for (int t = c0 * L + tid; t < c1 * L; t += kBlock) sH[t] = d.Hd_c[t];
   if (tid < kCandidates) sok[tid] = d.lm_ok[tid];
   __syncthreads();
-  const bool inA = i < d.V && a4.w >= 1 && nn.w > 0.f;
   float e[kCandidates];
 #pragma unroll
   for (int c = 0; c < kCandidates; ++c) e[c] = 0.f;
-  if (inA) {
-    const float inv = 1.f / ((float)a4.w * kFix);
-    const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
-    const float3 x = make_float3(x0.x + ph.x, x0.y + ph.y, x0.z + ph.z);
+  for (int q = tid; q < cnt; q += kBlock) {
+    if (q != tid) {
+      r0 = recs[4 * q];
+      r1 = recs[4 * q + 1];
+      r2 = recs[4 * q + 2];
+      r3 = recs[4 * q + 3];
+    }
+    const float3 pt = make_float3(r0.x, r0.y, r0.z), nn = make_float3(r0.w, r1.x, r1.y);
+    const float3 x = make_float3(r1.z, r1.w, r2.x);
+    const float4 bw = make_float4(r2.y, r2.z, r2.w, r3.x);
+    const unsigned bits = __float_as_uint(r3.y);
+    uchar4 bi;
+    memcpy(&bi, &bits, 4);
 #pragma unroll
     for (int c = 0; c < kCandidates; ++c) {
       if (c < c0 || c >= c1 || !sok[c]) continue;
       float sg[4];
       const DQ H = blend_bones(sH + c * L, bi, bw, sg);
       const float3 vc = dq_point(H, x);
-      const float r = nn.x * (v.x - vc.x + pm.x) + nn.y * (v.y - vc.y + pm.y) + nn.z * (v.z - vc.z + pm.z);
-      e[c] = r * r;
+      const float r = nn.x * (pt.x - vc.x) + nn.y * (pt.y - vc.y) + nn.z * (pt.z - vc.z);
+      e[c] += r * r;
     }
   }
 #pragma unroll
@@ -999,8 +1033,8 @@ void launch_lm_solve(const Dev& d, cudaStream_t st) {
 
 void launch_lm_eval(const Dev& d, int phi_buf, cudaStream_t st) {
   const size_t sm = kCandidates * d.L * sizeof(DQ);
-  k_lm_eval<<<d.nblk_v, kBlock, sm, st>>>(kSingle, d, phi_buf, 0, kFirstPass);
-  k_lm_eval<<<d.nblk_v, kBlock, sm, st>>>(kSingle, d, phi_buf, kFirstPass, kCandidates);
+  k_lm_eval<<<d.nblk_rows, kBlock, sm, st>>>(kSingle, d, phi_buf, 0, kFirstPass);
+  k_lm_eval<<<d.nblk_rows, kBlock, sm, st>>>(kSingle, d, phi_buf, kFirstPass, kCandidates);
 }
 
 void launch_lm(const Dev& d, int phi_buf, cudaStream_t st) {
@@ -1074,28 +1108,20 @@ __device__ __forceinline__ void shape_impl(const Dev& d, BlockPos bp, int src, i
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DQ* sHd = reinterpret_cast<DQ*>(smem_raw);
   const int i = bp.x * kBlock + threadIdx.x;
-  // the vertex's own inputs in one round trip, with the pose tables; the neighbours' offsets (and the
-  // skinning weights of a vertex of A) follow in a second
-  const float4* phi = d.phi[src];
-  float4 p4 = make_float4(0.f, 0.f, 0.f, 0.f), nn = p4;
-  Acc4 a4 = Acc4{0, 0, 0, 0};
-  int4 nb = make_int4(-1, -1, -1, -1);
-  if (i < d.V) {
-    p4 = phi[i];
-    a4 = d.acc[i];
-    nn = d.n[i];
-    nb = d.nbr[i];
+  bool anyA = false;
+  if (i < d.V) anyA = d.acc[i].w >= 1 && d.n[i].w > 0.f;
+  if (__syncthreads_or(anyA)) {  // the pose tables are needed only where a vertex of A is
+    for (int j = threadIdx.x; j < d.L; j += kBlock) sHd[j] = d.Hd[j];
+    __syncthreads();
   }
-  for (int j = threadIdx.x; j < d.L; j += kBlock) sHd[j] = d.Hd[j];
-  __syncthreads();
-  const int nbs[4] = {nb.x, nb.y, nb.z, nb.w};
-  float4 qn[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) qn[t] = t < d.knn && nbs[t] >= 0 ? phi[nbs[t]] : make_float4(0.f, 0.f, 0.f, 0.f);
   float e = 0.f;
   int inA_count = 0;
   if (i < d.V) {
+    const float4* phi = d.phi[src];
+    const float4 p4 = phi[i];
     const float3 pi = f3(p4);
+    const Acc4 a4 = d.acc[i];
+    const float4 nn = d.n[i];
     const bool inA = a4.w >= 1 && nn.w > 0.f;
     float r = 0.f;
     float3 g = make_float3(0.f, 0.f, 0.f);
@@ -1106,10 +1132,11 @@ __device__ __forceinline__ void shape_impl(const Dev& d, BlockPos bp, int src, i
     e = r * r + d.lambda_phi * dot3(pi, pi);
     float3 sd = make_float3(0.f, 0.f, 0.f);
     int nn_count = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (t >= d.knn || nbs[t] < 0) continue;
-      const float3 q = f3(qn[t]);
+    const int4 nb = d.nbr[i];
+    const int nbs[4] = {nb.x, nb.y, nb.z, nb.w};
+    for (int t = 0; t < d.knn; ++t) {
+      if (nbs[t] < 0) continue;
+      const float3 q = f3(phi[nbs[t]]);
       const float3 df = make_float3(pi.x - q.x, pi.y - q.y, pi.z - q.z);
       e += d.lambda_N * dot3(df, df);
       sd.x += df.x; sd.y += df.y; sd.z += df.z;

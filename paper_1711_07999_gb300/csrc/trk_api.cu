@@ -174,6 +174,10 @@ trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsi
     return fail(TRK_ERR_INVALID_ARG, "mode %d not supported", p->mode);
   if (p->association != 0 && p->association != 1)
     return fail(TRK_ERR_INVALID_ARG, "association %d not supported", p->association);
+  if (p->jtj_group != 0 && p->jtj_group != 1 && p->jtj_group != 2 && p->jtj_group != 4)
+    return fail(TRK_ERR_INVALID_ARG, "jtj_group %d not supported", p->jtj_group);
+  if (p->jtj_group > 1 && p->precision != TRK_PRECISION_FP32)
+    return fail(TRK_ERR_INVALID_ARG, "jtj_group > 1 needs precision FP32");
   if (p->pose_iters < 0 || p->shape_iters < 0 || p->shape_sweeps < 1 || p->knn < 0 || p->knn > 4 ||
       p->window_half_px < 0 || !(p->cutoff_m > 0) || !(p->lambda_k0 > 0) || p->lambda_s < 0 || p->lambda_phi < 0 ||
       p->lambda_N < 0 || p->lambda_w < 0 || !(p->z_near_m > 0) || !(p->eps_vis_m >= 0))
@@ -517,6 +521,10 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   const int NP = L + 1;
   const size_t npx = (size_t)W * H;
   d.nblk_jtj = (V + 255) / 256;
+  d.jtj_group = prm->jtj_group;
+  if (d.jtj_group == 0)
+    d.jtj_group = prm->precision != TRK_PRECISION_FP32 || d.nblk_jtj <= 304 ? 1 : d.nblk_jtj <= 608 ? 2 : 4;
+  d.nblk_rows = (d.nblk_jtj + d.jtj_group - 1) / d.jtj_group;
   d.nblk_v = (V + 255) / 256;
   LinkTable* dlt;
   float4 *dv0, *dbw, *phi0buf, *phi1buf;
@@ -550,8 +558,9 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   float* ddepth;
   TRY(dalloc(s, &ddepth, npx));
   TRY(dalloc(s, &s->d_render, npx));
-  TRY(dalloc(s, &d.partial, (size_t)d.nblk_jtj * NP * NP));
-  TRY(dalloc(s, &d.jtj_rows, (size_t)d.nblk_jtj));
+  TRY(dalloc(s, &d.partial, (size_t)d.nblk_rows * NP * NP));
+  TRY(dalloc(s, &d.jtj_rows, (size_t)d.nblk_rows));
+  TRY(dalloc(s, &d.arec, (size_t)d.nblk_jtj * 256 * 4));
   TRY(dalloc(s, &d.A, (size_t)NP * NP));
   TRY(dalloc(s, &d.epart, (size_t)std::max(d.nblk_v, 1) * 8));
   TRY(dalloc(s, &d.counter, 4));
@@ -801,6 +810,7 @@ trk_status trk_get_info(trk_session* s, trk_info* out) {
   const int shape_k = s->prm.shape_solver == 1 ? 3 * s->prm.shape_sweeps + 1 : s->prm.shape_sweeps;
   out->kernels_per_frame = s->prm.pose_iters * (per_assoc + 5) + s->prm.shape_iters * (per_assoc + shape_k);
   out->device_bytes = s->device_bytes;
+  out->jtj_group = s->d.jtj_group;
   return TRK_OK;
 }
 

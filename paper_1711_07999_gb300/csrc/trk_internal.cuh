@@ -286,8 +286,11 @@ struct Dev {
   float4* phi0;
   const float* depth;
   // reductions
-  float* partial;   // [nblk_jtj][NP*NP]
-  int* jtj_rows;    // [nblk_jtj] rows of [J r] each block contributed (0: its partial is not written)
+  float* partial;   // [nblk_rows][NP*NP]
+  int jtj_group;    // 256-vertex blocks per [J r] block (1, 2 or 4)
+  int nblk_rows;    // [J r] blocks: ceil(nblk_jtj / jtj_group)
+  int* jtj_rows;    // [nblk_rows] rows of [J r] each block contributed (0: its partial is not written)
+  float4* arec;     // [nblk_jtj * 256][4] per row of [J r]: what the candidate energies need of its vertex
   int nblk_jtj;
   double* A;        // [NP*NP]
   double* epart;    // [nblk_v][8]

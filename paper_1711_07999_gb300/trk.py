@@ -63,12 +63,14 @@ class Params(C.Structure):
                 ("lambda_k0", C.c_float), ("lambda_s", C.c_float), ("lambda_phi", C.c_float), ("lambda_N", C.c_float),
                 ("lambda_w", C.c_float), ("cutoff_m", C.c_float), ("eps_vis_m", C.c_float), ("z_near_m", C.c_float),
                 ("window_half_px", C.c_int32), ("knn", C.c_int32), ("precision", C.c_int32),
-                ("shape_solver", C.c_int32), ("mode", C.c_int32), ("association", C.c_int32)]
+                ("shape_solver", C.c_int32), ("mode", C.c_int32), ("association", C.c_int32),
+                ("jtj_group", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("n_links", C.c_int32), ("n_verts", C.c_int32), ("n_tris", C.c_int32), ("width", C.c_int32),
-                ("height", C.c_int32), ("kernels_per_frame", C.c_int32), ("device_bytes", C.c_size_t)]
+                ("height", C.c_int32), ("kernels_per_frame", C.c_int32), ("device_bytes", C.c_size_t),
+                ("jtj_group", C.c_int32)]
 
 
 class ScheduleConfig(C.Structure):
@@ -211,7 +213,8 @@ def params_struct(p: dict) -> Params:
                   lambda_N=p["lambda_N"], lambda_w=p["lambda_w"], cutoff_m=p["cutoff"], eps_vis_m=p["eps_vis"],
                   z_near_m=p["z_near"], window_half_px=p["window_half"], knn=p["knn"],
                   precision=p.get("precision", PRECISION_FP32), shape_solver=p.get("shape_solver", 0),
-                  mode=p.get("mode", MODE_TRACK), association=p.get("association", 0))
+                  mode=p.get("mode", MODE_TRACK), association=p.get("association", 0),
+                  jtj_group=p.get("jtj_group", 0))
 
 
 class Session:
