@@ -1,0 +1,83 @@
+"""Grouped [J r] blocks (trk_params.jtj_group = 1, 2, 4): each block adds the rows of G consecutive
+256-vertex blocks into one partial and writes a record per row for the candidate energies.  Whatever the
+grouping, the normal equations, the energy and the LM step match the FP64 oracle at the GPU's own
+association (the tolerances of the FP32 path: 1e-5 of the matrix scale, 1e-5 relative energy, the
+oracle's LM decision and its step within 1e-6 rad)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_07999_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1711_07999_gb300 import trk  # noqa: E402
+
+
+def _scene(G, V=4700, seed=0):
+    # 4700 vertices: 19 blocks of 256, so groups of 2 and 4 end with a partial group and a ragged block
+    m = synth.make_model(1, V=V, jtj_group=G)
+    o = oracle.Oracle(m)
+    gt = synth.gt_theta(m, 0.0)
+    depth = synth.add_noise(o.render(gt, synth.gt_offsets(m, 0.0)), 1, np.random.default_rng(seed))
+    rng = np.random.default_rng(seed + 7)
+    th = gt + np.radians(2.0) * rng.normal(size=o.L) * (m["skeleton"]["type"] == 0)
+    phi = (synth.gt_offsets(m, 0.0) * 0.5).astype(np.float32).astype(np.float64)
+    return m, o, depth, th, phi
+
+
+@pytest.mark.parametrize("G", [1, 2, 4])
+def test_grouped_blocks_match_the_oracle(G):
+    m, o, depth, th, phi = _scene(G)
+    with trk.Session(m) as s:
+        assert s.info()["jtj_group"] == G
+        s.set_pose(th, phi)
+        s.set_depth(depth)
+        for st in ("skin", "raster", "visibility", "associate", "normal_equations"):
+            s.step(st)
+        A = s.read("NORMAL_EQ")
+        E = s.read("ENERGY")[0]
+        lam0 = s.read("LAMBDA")[0]
+        corr = s.read("CORR")
+        s.step("lm")
+        trials = s.read("LM_TRIALS")
+        th_gpu = s.read("THETA")
+        lam_gpu = s.read("LAMBDA")[0]
+    v, _ = o.skin(th, phi)
+    n, ok = o.normals(v)
+    acc, cnt = o.accumulate(v, depth, corr)
+    r, inA, E_ref = o.residuals(th, n, ok, acc, cnt)
+    assert inA.sum() > 500
+    J = o.jacobian(th, phi, n, inA)
+    JTJ, JTr = oracle.normal_eq(J, r, inA)
+    L = o.L
+    assert np.abs(A[:L, :L] - JTJ).max() / np.abs(JTJ).max() < 1e-5
+    assert np.abs(A[:L, L] - JTr).max() <= 1e-4 * np.abs(JTr).max() + 1e-9
+    assert E == pytest.approx(E_ref, rel=1e-5)
+    o.set_state(th, phi)
+    a_ref, th_ref, lam_ref, Ec = o.lm_step(A[:L, :L], A[:L, L], trials[6], v, n, acc, cnt, inA, th, lam0)
+    assert int(trials[7]) == a_ref
+    assert np.abs(th_gpu - th_ref).max() < 1e-6
+    assert lam_gpu == pytest.approx(lam_ref, rel=1e-12)
+    both = np.isfinite(Ec) & np.isfinite(trials[:6])
+    assert both.any() and np.allclose(trials[:6][both], Ec[both], rtol=1e-5)
+
+
+def test_group_chosen_from_the_mesh_size():
+    # 1 up to 304 blocks of 256 vertices, 2 up to 608, else 4; tensor-core precisions keep 1
+    for V, G in ((5000, 1), (100000, 2), (170000, 4)):
+        with trk.Session(synth.make_model(1, V=V, width=64)) as s:
+            assert s.info()["jtj_group"] == G, V
+    with trk.Session(synth.make_model(1, V=170000, width=64, precision=trk.PRECISION_TF32X3)) as s:
+        assert s.info()["jtj_group"] == 1
+
+
+@pytest.mark.parametrize("kw", [dict(jtj_group=3), dict(jtj_group=-1),
+                                dict(jtj_group=2, precision=1)])
+def test_invalid_group_is_rejected(kw):
+    with pytest.raises(trk.TrkError) as e:
+        trk.Session(synth.make_model(1, V=500, width=64, **kw))
+    assert e.value.status == trk.TRK_ERR_INVALID_ARG
