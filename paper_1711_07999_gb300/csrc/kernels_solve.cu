@@ -293,7 +293,7 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
 }
 
 template <int T>
-__global__ void __launch_bounds__(kBlock) k_resid_jtj(BatchGrid g, Dev d0, int phi_buf) {
+__global__ void __launch_bounds__(kBlock, 3) k_resid_jtj(BatchGrid g, Dev d0, int phi_buf) {
   if (g.map == nullptr) {
     resid_jtj_impl<T>(d0, grid_pos(), phi_buf);
     return;
