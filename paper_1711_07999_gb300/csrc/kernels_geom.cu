@@ -219,8 +219,8 @@ void launch_visibility(const Dev& d, cudaStream_t st) {
 // that angle into a distance from p), so the search stops once that bound exceeds the best distance
 // or tau: the result is the same argmin as the exhaustive window search.
 //
-// k_associate: rings 0..kRingsPerThread by the pixel's own thread, each ring's bucket heads and first
-// records loaded together.  Pixels still open after that (no vertex within ~1-2 cm: the first iterations
+// k_associate: rings 0..kRingsPerThread by the pixel's own thread, four buckets' heads and first records
+// loaded together.  Pixels still open after that (no vertex within ~1-2 cm: the first iterations
 // of a frame, silhouettes) go to a queue that k_associate_tail drains with one warp per pixel, the lanes
 // splitting each ring's 8r buckets and combining (d^2, index) keys with a warp-min.
 // The pixel's offset p - v_i is added to the vertex's fixed-point sums (integer atomics: the sums do
@@ -328,11 +328,11 @@ __device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
         const int q0[1] = {k};
         scan_group<1>(d, q0, p, tau2, best, bd2);
       } else {
-        for (int t0 = 0; t0 < 8 * r; t0 += 8) {
-          int q[8];
+        for (int t0 = 0; t0 < 8 * r; t0 += 4) {  // 4 buckets in flight: 64 registers, 4 blocks per SM
+          int q[4];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) q[u] = ring_bucket(px, py, r, t0 + u, c.W, c.H);
-          scan_group<8>(d, q, p, tau2, best, bd2);
+          for (int u = 0; u < 4; ++u) q[u] = ring_bucket(px, py, r, t0 + u, c.W, c.H);
+          scan_group<4>(d, q, p, tau2, best, bd2);
         }
       }
       const float lb = dep * ((float)r + 0.499f) * c.kappa;
@@ -354,10 +354,12 @@ __device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
 
 
 constexpr int kTailWarps = 8;
+constexpr int kTailPerLane = 4;  // buckets a lane loads at once (a ring of up to 128 buckets in one round trip)
 
-// The rings beyond the thread-owned ones for queue entry `item` of session d, by one warp (the lanes
-// split each ring's buckets; (d^2, index) keys combined by a warp-min).  Returns, in every lane, whether
-// the pixel got a correspondence (lane 0 writes it and adds the pixel's sums).
+// The rings beyond the thread-owned ones for queue entry `item` of session d, by one warp: the lanes split
+// each ring's 8r buckets (up to kTailPerLane each, their heads and first records loaded all at once) and
+// combine (d^2, index) keys with a warp-min.  Returns, in every lane, whether the pixel got a correspondence
+// (lane 0 writes it and adds the pixel's sums).
 __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item) {
   const Cam c = d.cam;
   const int lane = threadIdx.x & 31;
@@ -370,9 +372,14 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item) {
   int wb = -1;
   float wd2 = 0.f;
   for (int r = kRingsPerThread + 1; r <= c.R; ++r) {
-    for (int t0 = 0; t0 < 8 * r; t0 += 32) {
-      const int q[1] = {t0 + lane < 8 * r ? ring_bucket(px, py, r, t0 + lane, c.W, c.H) : -1};
-      scan_group<1>(d, q, p, tau2, wb, wd2);
+    for (int t0 = 0; t0 < 8 * r; t0 += 32 * kTailPerLane) {
+      int q[kTailPerLane];
+#pragma unroll
+      for (int u = 0; u < kTailPerLane; ++u) {
+        const int t = t0 + lane + 32 * u;
+        q[u] = t < 8 * r ? ring_bucket(px, py, r, t, c.W, c.H) : -1;
+      }
+      scan_group<kTailPerLane>(d, q, p, tau2, wb, wd2);
     }
     unsigned long long kk = key_of(wb, wd2);
     kk = kk < key ? kk : key;
@@ -396,7 +403,7 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item) {
 // One session: one 16 x 16 tile per block.  A batch: persistent blocks take the frame's occupied tiles
 // (listed by the depth gather) from a shared counter, reloading the session descriptor when the session
 // changes; pixels of empty tiles keep the "no correspondence" the skinning pass wrote.
-__global__ void __launch_bounds__(kBlock) k_associate(const Dev* devs, const int4* tiles, unsigned* ctl, Dev d0) {
+__global__ void __launch_bounds__(kBlock, 4) k_associate(const Dev* devs, const int4* tiles, unsigned* ctl, Dev d0) {
   if (devs == nullptr) {
     associate_impl(d0, grid_pos());
     return;
