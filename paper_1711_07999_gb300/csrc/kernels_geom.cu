@@ -220,13 +220,14 @@ void launch_visibility(const Dev& d, cudaStream_t st) {
 // or tau: the result is the same argmin as the exhaustive window search.
 //
 // k_associate: rings 0..kRingsPerThread by the pixel's own thread, four buckets' heads and first records
-// loaded together.  Pixels still open after that (no vertex within ~1-2 cm: the first iterations
-// of a frame, silhouettes) go to a queue that k_associate_tail drains with one warp per pixel, the lanes
-// splitting each ring's 8r buckets and combining (d^2, index) keys with a warp-min.
+// loaded together.  Pixels still open after that (the bound of ring 1 is ~4 mm at 2-3 m: pixels whose
+// nearest vertex is farther, in the first iterations of a frame, at silhouettes and where vertices are
+// sparse) go to a queue that k_associate_tail drains with one warp per pixel, the lanes splitting each
+// ring's 8r buckets and combining (d^2, index) keys with a warp-min.
 // The pixel's offset p - v_i is added to the vertex's fixed-point sums (integer atomics: the sums do
 // not depend on the order of the additions).
 // ---------------------------------------------------------------------------------------------
-constexpr int kRingsPerThread = 2;
+constexpr int kRingsPerThread = 1;
 
 __device__ __forceinline__ void consider(int i, float3 p, float4 r, float tau2, int& best, float& bd2) {
   const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
