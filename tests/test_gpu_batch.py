@@ -84,3 +84,10 @@ def test_members_must_share_schedule_and_precision():
         assert e.value.status == trk.TRK_ERR_INVALID_ARG
     for s in (a, b, c):
         s.close()
+
+
+def test_members_with_different_jtj_groups():
+    # the same kind of session with 1, 2 and 4 vertex blocks per [J r] block, in one batch
+    ms = [synth.make_model(1, session=10 + G, V=6000, width=96, jtj_group=G) for G in (1, 2, 4)]
+    alone, got = _run(ms, trk.PRECISION_FP32, 2)
+    _assert_same(alone, got)
