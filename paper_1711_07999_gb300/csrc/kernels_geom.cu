@@ -137,6 +137,12 @@ __global__ void __launch_bounds__(kBlock) k_raster(BatchGrid g, Dev d0) {
   raster_impl(sd, batch_block(g, sd));
 }
 
+// A batch's launch: registers sized for kBatchMinBlocks resident blocks (a few spills for occupancy).
+__global__ void __launch_bounds__(kBlock, kBatchMinBlocks) k_raster_b(BatchGrid g) {
+  __shared__ Dev sd;
+  raster_impl(sd, batch_block(g, sd));
+}
+
 void launch_raster(const Dev& d, cudaStream_t st) {
   if (d.F > 0) k_raster<<<grid_for(d.F, kBlock), kBlock, 0, st>>>(kSingle, d);
 }
@@ -202,6 +208,11 @@ __global__ void __launch_bounds__(kBlock) k_visibility(BatchGrid g, Dev d0) {
     visibility_impl(d0, grid_pos());
     return;
   }
+  __shared__ Dev sd;
+  visibility_impl(sd, batch_block(g, sd));
+}
+
+__global__ void __launch_bounds__(kBlock, kBatchMinBlocks) k_visibility_b(BatchGrid g) {
   __shared__ Dev sd;
   visibility_impl(sd, batch_block(g, sd));
 }
@@ -506,10 +517,10 @@ void launch_skin_b(const BatchGrid& g, int nblk, int max_links, int phi_buf, uns
   if (nblk > 0) k_skin<<<nblk, kBlock, max_links * sizeof(DQ), st>>>(g, Dev{}, phi_buf, ctl);
 }
 void launch_raster_b(const BatchGrid& g, int nblk, cudaStream_t st) {
-  if (nblk > 0) k_raster<<<nblk, kBlock, 0, st>>>(g, Dev{});
+  if (nblk > 0) k_raster_b<<<nblk, kBlock, 0, st>>>(g);
 }
 void launch_visibility_b(const BatchGrid& g, int nblk, cudaStream_t st) {
-  if (nblk > 0) k_visibility<<<nblk, kBlock, 0, st>>>(g, Dev{});
+  if (nblk > 0) k_visibility_b<<<nblk, kBlock, 0, st>>>(g);
 }
 void launch_associate_b(const Dev* devs, int n_sessions, const int4* tiles, unsigned* ctl, unsigned* prefix,
                         int assoc_blocks, int tail_blocks, cudaStream_t st) {

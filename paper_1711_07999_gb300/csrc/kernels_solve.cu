@@ -1165,6 +1165,12 @@ __global__ void __launch_bounds__(kBlock) k_shape(BatchGrid g, Dev d0, int src, 
   shape_impl(sd, batch_block(g, sd), src, slot);
 }
 
+// A batch's launch: registers sized for kBatchMinBlocks resident blocks (a few spills for occupancy).
+__global__ void __launch_bounds__(kBlock, kBatchMinBlocks) k_shape_b(BatchGrid g, int src, int slot) {
+  __shared__ Dev sd;
+  shape_impl(sd, batch_block(g, sd), src, slot);
+}
+
 // Further Jacobi sweeps: r_i is updated linearly, r_i = r0_i + g_i . (phi_i - phi0_i).
 __device__ __forceinline__ void shape_sweep_impl(const Dev& d, BlockPos bp, int src) {
   const int i = bp.x * kBlock + threadIdx.x;
@@ -1488,7 +1494,7 @@ int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int s
     launch_shape_pcg(gv, nv, Dev{}, max_links, sweeps, phi_src, slot, st);
     return 1 - phi_src;
   }
-  if (nv > 0) k_shape<<<nv, kBlock, max_links * sizeof(DQ), st>>>(gv, Dev{}, phi_src, slot);
+  if (nv > 0) k_shape_b<<<nv, kBlock, max_links * sizeof(DQ), st>>>(gv, phi_src, slot);
   int cur = 1 - phi_src;
   for (int s = 1; s < sweeps; ++s) {
     if (nv > 0) k_shape_sweep<<<nv, kBlock, 0, st>>>(gv, Dev{}, cur);

@@ -353,5 +353,8 @@ __device__ __forceinline__ BlockPos batch_block(const BatchGrid& g, Dev& sd) {
   return BlockPos{m.y, m.z, m.w};
 }
 constexpr BatchGrid kSingle{nullptr, nullptr};
+// Resident blocks per SM that a batch's launches of the streaming stages (raster, visibility, shape) size
+// their registers for: their grids span many sessions, where occupancy hides the gathers' latency.
+constexpr int kBatchMinBlocks = 7;
 
 }  // namespace trk
