@@ -1134,9 +1134,13 @@ __device__ __forceinline__ void shape_impl(const Dev& d, BlockPos bp, int src, i
     int nn_count = 0;
     const int4 nb = d.nbr[i];
     const int nbs[4] = {nb.x, nb.y, nb.z, nb.w};
-    for (int t = 0; t < d.knn; ++t) {
-      if (nbs[t] < 0) continue;
-      const float3 q = f3(phi[nbs[t]]);
+    float4 qn[4];  // the neighbours' offsets, all in flight before they are used
+#pragma unroll
+    for (int t = 0; t < 4; ++t) qn[t] = t < d.knn && nbs[t] >= 0 ? phi[nbs[t]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (t >= d.knn || nbs[t] < 0) continue;
+      const float3 q = f3(qn[t]);
       const float3 df = make_float3(pi.x - q.x, pi.y - q.y, pi.z - q.z);
       e += d.lambda_N * dot3(df, df);
       sd.x += df.x; sd.y += df.y; sd.z += df.z;
@@ -1184,9 +1188,13 @@ __device__ __forceinline__ void shape_sweep_impl(const Dev& d, BlockPos bp, int 
   int nn_count = 0;
   const int4 nb = d.nbr[i];
   const int nbs[4] = {nb.x, nb.y, nb.z, nb.w};
-  for (int t = 0; t < d.knn; ++t) {
-    if (nbs[t] < 0) continue;
-    const float3 q = f3(phi[nbs[t]]);
+  float4 qn[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) qn[t] = t < d.knn && nbs[t] >= 0 ? phi[nbs[t]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (t >= d.knn || nbs[t] < 0) continue;
+    const float3 q = f3(qn[t]);
     sd.x += pi.x - q.x; sd.y += pi.y - q.y; sd.z += pi.z - q.z;
     ++nn_count;
   }
