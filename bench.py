@@ -593,7 +593,7 @@ def run_uneven(args, rank, flush):
     import torch
     from paper_1711_07999_gb300 import synth, trk
     B = args.uneven_sessions
-    models = [synth.make_model(4, session=rank * 10000 + k) for k in range(B)]
+    models = [synth.make_model(4, session=rank * 10000 + k, jtj_group=args.uneven_jtj_group) for k in range(B)]
     sess = [trk.Session(m) for m in models]
     nf = 4
     frames = []
@@ -921,6 +921,8 @@ def main():
     ap.add_argument("--admission-budget-gib", type=float, default=1.0)
     ap.add_argument("--experiment-frames", type=int, default=30,
                     help="frames of the sequence tracked in each of the paper's experiment conditions")
+    ap.add_argument("--uneven-jtj-group", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="vertex blocks per [J r] block of the uneven sessions (0: chosen from each mesh's size)")
     ap.add_argument("--uneven-sessions", type=int, default=64,
                     help="sessions of the uneven batch (one by one / streams / fused batch / tuned schedule)")
     ap.add_argument("--precision-modes", type=int, default=1,

@@ -91,8 +91,10 @@ typedef struct {
   int32_t association;  /* 0: the closest visible vertex in the window (Sec. 4.1); 1: the nearest
                            corner of the triangle the z-buffer holds at the pixel (O(1) per pixel)   */
   int32_t jtj_group;    /* vertices per block of the [J r]^T [J r] contraction, in units of 256: 1, 2
-                           or 4 (fewer block partials to add; FP32 precision only), 0: chosen from the
-                           mesh size (1 up to 304 units, 2 up to 608, else 4)                         */
+                           or 4 (fewer block partials to add; FP32 precision only).  0: the larger of
+                           the choice by mesh size (1 up to 304 units, 2 up to 608, else 4) and by the
+                           expected rows per unit r = 128 c / V, c = distinct pixels the template's
+                           vertices round to at the bind pose (4 if r < 18, 2 if r < 30, else 1)      */
 } trk_params;
 
 /* TRACK: every frame estimates the shape (the full method).  SHAPE_MATCH: only the first frame after

@@ -66,12 +66,34 @@ def test_grouped_blocks_match_the_oracle(G):
     assert both.any() and np.allclose(trials[:6][both], Ec[both], rtol=1e-5)
 
 
-def test_group_chosen_from_the_mesh_size():
-    # 1 up to 304 blocks of 256 vertices, 2 up to 608, else 4; tensor-core precisions keep 1
-    for V, G in ((5000, 1), (100000, 2), (170000, 4)):
-        with trk.Session(synth.make_model(1, V=V, width=64)) as s:
-            assert s.info()["jtj_group"] == G, V
-    with trk.Session(synth.make_model(1, V=170000, width=64, precision=trk.PRECISION_TF32X3)) as s:
+def _auto_group(m):
+    """The grouping trk_create picks: the larger of the choice by mesh size and by the expected rows per
+    256 vertices, r = 128 c / V with c the distinct pixels the template's vertices round to."""
+    v = np.asarray(m["mesh"]["verts"], np.float32).astype(np.float64).reshape(-1, 3)  # as the C ABI gets them
+    c = {k: float(np.float32(x)) if isinstance(x, float) else x for k, x in m["camera"].items()}
+    V, W, H = len(v), c["width"], c["height"]
+    nblk = -(-V // 256)
+    by_size = 1 if nblk <= 304 else 2 if nblk <= 608 else 4
+    z = v[:, 2]
+    ok = z > float(np.float32(m["params"]["z_near"]))
+    u = np.floor(c["fx"] * v[ok, 0] / z[ok] + c["cx"] + 0.5)
+    w = np.floor(c["fy"] * v[ok, 1] / z[ok] + c["cy"] + 0.5)
+    ins = (u >= 0) & (w >= 0) & (u < W) & (w < H)
+    covered = len(np.unique((w[ins] * W + u[ins]).astype(np.int64)))
+    rows = 256 * 0.5 * covered / V
+    return max(by_size, 4 if rows < 18 else 2 if rows < 30 else 1)
+
+
+def test_group_chosen_from_the_mesh_and_its_image_coverage():
+    # tensor-core precisions keep 1
+    seen = set()
+    for m in (synth.make_model(2), synth.make_model(1, V=5000, width=640), synth.make_model(4, session=3),
+              synth.make_model(4, session=5), synth.make_model(3)):
+        with trk.Session(m) as s:
+            assert s.info()["jtj_group"] == _auto_group(m)
+            seen.add(s.info()["jtj_group"])
+    assert seen == {1, 2, 4}, seen
+    with trk.Session(synth.make_model(4, session=5, precision=trk.PRECISION_TF32X3)) as s:
         assert s.info()["jtj_group"] == 1
 
 
