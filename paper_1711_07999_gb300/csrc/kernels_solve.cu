@@ -869,7 +869,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_lm_solve(BatchGrid g, Dev d0)
 // once (each candidate's sum has the same blocks in the same order).  Candidates not scored report +inf.
 constexpr double kPending = -2.0;
 
-__device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_buf, int c0, int c1) {
+__device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int c0, int c1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DQ* sH = reinterpret_cast<DQ*>(smem_raw);  // [kCandidates][L]
   __shared__ int sok[kCandidates];
@@ -1013,13 +1013,13 @@ __device__ __forceinline__ void lm_eval_impl(const Dev& d, BlockPos bp, int phi_
 
 constexpr int kFirstPass = 2;  // candidates scored by the first pass
 
-__global__ void __launch_bounds__(kBlock) k_lm_eval(BatchGrid g, Dev d0, int phi_buf, int c0, int c1) {
+__global__ void __launch_bounds__(kBlock) k_lm_eval(BatchGrid g, Dev d0, int c0, int c1) {
   if (g.map == nullptr) {
-    lm_eval_impl(d0, grid_pos(), phi_buf, c0, c1);
+    lm_eval_impl(d0, grid_pos(), c0, c1);
     return;
   }
   __shared__ Dev sd;
-  lm_eval_impl(sd, batch_block(g, sd), phi_buf, c0, c1);
+  lm_eval_impl(sd, batch_block(g, sd), c0, c1);
 }
 
 static int lm_solve_smem(int L) {
@@ -1031,10 +1031,10 @@ void launch_lm_solve(const Dev& d, cudaStream_t st) {
   k_lm_solve<<<kCandidates, kSolveThreads, lm_solve_smem(d.L), st>>>(kSingle, d);
 }
 
-void launch_lm_eval(const Dev& d, int phi_buf, cudaStream_t st) {
+void launch_lm_eval(const Dev& d, int /*phi_buf: the rows' records already hold x0 + phi*/, cudaStream_t st) {
   const size_t sm = kCandidates * d.L * sizeof(DQ);
-  k_lm_eval<<<d.nblk_rows, kBlock, sm, st>>>(kSingle, d, phi_buf, 0, kFirstPass);
-  k_lm_eval<<<d.nblk_rows, kBlock, sm, st>>>(kSingle, d, phi_buf, kFirstPass, kCandidates);
+  k_lm_eval<<<d.nblk_rows, kBlock, sm, st>>>(kSingle, d, 0, kFirstPass);
+  k_lm_eval<<<d.nblk_rows, kBlock, sm, st>>>(kSingle, d, kFirstPass, kCandidates);
 }
 
 void launch_lm(const Dev& d, int phi_buf, cudaStream_t st) {
@@ -1491,8 +1491,8 @@ void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int
   if (nlm > 0) k_lm_solve<<<nlm, kSolveThreads, lm_solve_smem(max_links), st>>>(glm, Dev{});
   if (nv > 0) {
     const size_t sm = kCandidates * max_links * sizeof(DQ);
-    k_lm_eval<<<nv, kBlock, sm, st>>>(gv, Dev{}, phi_buf, 0, kFirstPass);
-    k_lm_eval<<<nv, kBlock, sm, st>>>(gv, Dev{}, phi_buf, kFirstPass, kCandidates);
+    k_lm_eval<<<nv, kBlock, sm, st>>>(gv, Dev{}, 0, kFirstPass);
+    k_lm_eval<<<nv, kBlock, sm, st>>>(gv, Dev{}, kFirstPass, kCandidates);
   }
 }
 
