@@ -233,8 +233,9 @@ void launch_visibility(const Dev& d, cudaStream_t st) {
 // k_associate: rings 0..kRingsPerThread by the pixel's own thread, four buckets' heads and first records
 // loaded together.  Pixels still open after that (the bound of ring 1 is ~4 mm at 2-3 m: pixels whose
 // nearest vertex is farther, in the first iterations of a frame, at silhouettes and where vertices are
-// sparse) go to a queue that k_associate_tail drains with one warp per pixel, the lanes splitting each
-// ring's 8r buckets and combining (d^2, index) keys with a warp-min.
+// sparse) go to a queue that the tail kernels drain with a group of lanes per pixel (a warp for one session,
+// 8 lanes in a batch), the lanes splitting each ring's 8r buckets and combining (d^2, index) keys with a
+// group min.
 // The pixel's offset p - v_i is added to the vertex's fixed-point sums (integer atomics: the sums do
 // not depend on the order of the additions).
 // ---------------------------------------------------------------------------------------------
@@ -366,15 +367,18 @@ __device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
 
 
 constexpr int kTailWarps = 8;
-constexpr int kTailPerLane = 4;  // buckets a lane loads at once (a ring of up to 128 buckets in one round trip)
+constexpr int kTailPerLane = 4;  // buckets a lane loads at once
 
-// The rings beyond the thread-owned ones for queue entry `item` of session d, by one warp: the lanes split
-// each ring's 8r buckets (up to kTailPerLane each, their heads and first records loaded all at once) and
-// combine (d^2, index) keys with a warp-min.  Returns, in every lane, whether the pixel got a correspondence
-// (lane 0 writes it and adds the pixel's sums).
-__device__ __forceinline__ bool tail_item(const Dev& d, unsigned item) {
+// The rings beyond the thread-owned ones for queue entry `item` of session d, by a group of GL lanes (lanes
+// gl = lane % GL of the group starting at lane gbase, gmask naming them): the lanes split each
+// ring's 8r buckets (up to kTailPerLane each per round trip, heads and first records loaded together) and
+// combine (d^2, index) keys with a group min.  Returns, in every lane of the group, whether the pixel got a
+// correspondence (its first lane writes it and adds the pixel's sums).
+// One session's tail takes a warp per pixel (its queue is short and its latency is the slowest pixel's
+// rings); a batch's takes 8 lanes per pixel (four pixels per warp: throughput over many queues).
+template <int GL>
+__device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, unsigned gmask) {
   const Cam c = d.cam;
-  const int lane = threadIdx.x & 31;
   const float tau2 = c.tau * c.tau;
   const int4 e = d.queue[item];
   const int k = e.x, px = k % c.W, py = k / c.W;
@@ -384,11 +388,11 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item) {
   int wb = -1;
   float wd2 = 0.f;
   for (int r = kRingsPerThread + 1; r <= c.R; ++r) {
-    for (int t0 = 0; t0 < 8 * r; t0 += 32 * kTailPerLane) {
+    for (int t0 = 0; t0 < 8 * r; t0 += GL * kTailPerLane) {
       int q[kTailPerLane];
 #pragma unroll
       for (int u = 0; u < kTailPerLane; ++u) {
-        const int t = t0 + lane + 32 * u;
+        const int t = t0 + gl + GL * u;
         q[u] = t < 8 * r ? ring_bucket(px, py, r, t, c.W, c.H) : -1;
       }
       scan_group<kTailPerLane>(d, q, p, tau2, wb, wd2);
@@ -396,8 +400,8 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item) {
     unsigned long long kk = key_of(wb, wd2);
     kk = kk < key ? kk : key;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long other = __shfl_xor_sync(0xffffffffu, kk, o);
+    for (int o = GL / 2; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(gmask, kk, o);
       kk = other < kk ? other : kk;
     }
     key = kk;
@@ -405,7 +409,7 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item) {
     if (lb > c.tau || (key != ~0ull && lb * lb > __uint_as_float((unsigned)(key >> 32)))) break;
   }
   const int best = key == ~0ull ? -1 : (int)(unsigned)(key & 0xffffffffu);
-  if (lane == 0) {
+  if (gl == 0) {
     d.corr[k] = best;
     if (best >= 0) commit_pixel(d, best, p);
   }
@@ -445,17 +449,18 @@ __global__ void __launch_bounds__(kBlock, 4) k_associate(const Dev* devs, const 
 
 // One session: the warps of all blocks take its queue entries from the session's counter.
 __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, gl = lane, gbase = 0;
+  const unsigned gmask = 0xffffffffu;
   const unsigned n = *(volatile unsigned*)&d.qctl[0];
   int done = 0;
   for (;;) {
     unsigned item = 0;
-    if (lane == 0) item = atomicAdd(&d.qctl[1], 1u);
-    item = __shfl_sync(0xffffffffu, item, 0);
+    if (gl == 0) item = atomicAdd(&d.qctl[1], 1u);
+    item = __shfl_sync(gmask, item, gbase);
     if (item >= n) break;
-    done += tail_item(d, item);
+    done += tail_item<32>(d, item, gl, gmask);
   }
-  if (lane == 0 && done) atomicAdd(&d.stats[0], done);
+  if (gl == 0 && done) atomicAdd(&d.stats[0], done);
 }
 
 // A batch: prefix[s] = queued pixels of the sessions before s (one block; at most 1024 x 4 sessions).
@@ -489,12 +494,14 @@ __global__ void __launch_bounds__(1024) k_tail_prefix(const Dev* devs, int n_ses
 // entry's session is found in the prefix and its descriptor read through the cache.
 __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const Dev* devs, int n_sessions,
                                                                           const unsigned* prefix, unsigned* ctl) {
-  const int lane = threadIdx.x & 31;
+  constexpr int GL = 8;
+  const int lane = threadIdx.x & 31, gl = lane % GL, gbase = lane - gl;
+  const unsigned gmask = ((1u << GL) - 1u) << gbase;
   const unsigned total = prefix[n_sessions];
   for (;;) {
     unsigned item = 0;
-    if (lane == 0) item = atomicAdd(&ctl[2], 1u);
-    item = __shfl_sync(0xffffffffu, item, 0);
+    if (gl == 0) item = atomicAdd(&ctl[2], 1u);
+    item = __shfl_sync(gmask, item, gbase);
     if (item >= total) break;
     int lo = 0, hi = n_sessions - 1;  // the last session whose prefix is <= item
     while (lo < hi) {
@@ -502,7 +509,7 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const 
       if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
     }
     const Dev& d = devs[lo];
-    if (tail_item(d, item - prefix[lo]) && lane == 0) atomicAdd(&d.stats[0], 1);
+    if (tail_item<GL>(d, item - prefix[lo], gl, gmask) && gl == 0) atomicAdd(&d.stats[0], 1);
   }
 }
 
