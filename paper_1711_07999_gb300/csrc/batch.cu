@@ -4,7 +4,7 @@
 // acceptance, the shape step) runs as ONE kernel launch over the blocks of all sessions: a per-stage
 // table maps each block to (session, block position in that session's grid), and the block reads its
 // session's descriptor from a device array.  A frame of the whole batch is one CUDA graph of the same
-// ~90 launches a single session needs, however many sessions there are, and the sessions' blocks share
+// ~110 launches a single session needs, however many sessions there are, and the sessions' blocks share
 // each launch's waves (small sessions fill the gaps of large ones).  Each session computes exactly what
 // it computes alone: blocks of different sessions touch disjoint buffers, and every per-session
 // reduction keeps its fixed order.
