@@ -16,16 +16,19 @@ Prints one JSON line (rank 0):
              Theta, Phi and the energies inside the timed region
   precision  per [J r]^T [J r] arithmetic (fp32, bf16x3, tf32x3; the last two on the tensor cores): batched
              frames/s, the contraction stage's time and each result's error against the oracle on the
-             CPU-baseline frames
+             CPU-baseline frames (joint values, also where the energy determines them; offsets, also where
+             the two final poses agree; energies)
   uneven     --uneven-sessions sessions of random-tree bodies (5k-200k vertices, 12-40 bones, 320x240 to
              1280x720): frames/s one by one, on one stream each, as one fused batch (trk_batch_*), and
-             under the schedule the autotuner picks (trk_schedule_*)
+             under the schedule the autotuner picks (trk_schedule_*); each stage's HBM roofline in the fused
+             batch, profiled at the first frame's state (--uneven-jtj-group sets the sessions' [J r] grouping)
   admission_serving  --admission-streams streams of uneven sessions with Poisson starts under a 1 GiB HBM
              budget: admitted as capacity frees, 30 Poisson frames/s each, then leaving; served frames/s,
              latency, admission waits, peak admitted bytes
   experiments  the paper's conditions (full tracking, shape-match, smooth-bind) on the sequence with its
              ground truth: joint accuracy (AUC up to 10 cm) and reconstruction error
-  roofline   the dominant kernel's achieved rate against the measured peak of MEASURED_PEAKS.json
+  roofline   the dominant kernel's achieved rate against the measured peak of MEASURED_PEAKS.json, with a
+             note on what bounds it
   cpu_baseline  the FP64 oracle on the host, one core, a bounded sample of the same sequence
 --impl reference times the oracle itself (on host cores) on the same workload and metric.
 """
