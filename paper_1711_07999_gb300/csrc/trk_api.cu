@@ -128,6 +128,7 @@ struct trk_session {
   std::vector<void*> allocs;
   size_t device_bytes = 0;
   double* h_pinned = nullptr;  // pinned staging for results
+  float4* h_phi = nullptr;     // pinned staging for the offsets of a result [V]
   float* d_render = nullptr;
   int phi_cur = 0;
 };
@@ -267,11 +268,8 @@ trk_status fetch_result(trk_session* s, cudaStream_t st, trk_result* out) {
   CK(cudaMemcpyAsync(h, d.theta, sizeof(double) * d.L, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h + d.L, d.energy, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h + d.L + ne, d.stats, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
-  std::vector<float4> phi;
-  if (out->offsets) {
-    phi.resize(d.V);
-    CK(cudaMemcpyAsync(phi.data(), d.phi[0], sizeof(float4) * d.V, cudaMemcpyDeviceToHost, st));
-  }
+  const float4* phi = s->h_phi;
+  if (out->offsets) CK(cudaMemcpyAsync(s->h_phi, d.phi[0], sizeof(float4) * d.V, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (out->theta) std::memcpy(out->theta, h, sizeof(double) * d.L);
   if (out->energy) std::memcpy(out->energy, h + d.L, sizeof(double) * ne);
@@ -347,6 +345,7 @@ void trk_destroy(trk_session* s) {
   if (s->graph_pose) cudaGraphExecDestroy(s->graph_pose);
   for (void* p : s->allocs) cudaFree(p);
   if (s->h_pinned) cudaFreeHost(s->h_pinned);
+  if (s->h_phi) cudaFreeHost(s->h_phi);
   if (s->stream) cudaStreamDestroy(s->stream);
   cudaSetDevice(cur);
   delete s;
@@ -593,6 +592,7 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   d.adj_off = dadj_off;
   d.adj = dadj;
   CK(cudaMallocHost(&s->h_pinned, sizeof(double) * (L + prm->pose_iters + prm->shape_iters + 4)));
+  CK(cudaMallocHost(&s->h_phi, sizeof(float4) * std::max(V, 1)));
   cudaStream_t st = s->stream;
   CK(cudaMemcpyAsync(dlt, &lt, sizeof(lt), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(dv0, v0.data(), sizeof(float4) * V, cudaMemcpyHostToDevice, st));
