@@ -734,7 +734,7 @@ __device__ __forceinline__ void lm_solve_impl(const Dev& d, BlockPos bp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float F[kMaxPad][kMaxPad + 1];  // FP32 scaled system -> its Cholesky factor
   __shared__ float ivd[kMaxPad], ys[kMaxPad], sc[kMaxPad];
-  const int P = d.L, NP = d.NP, c = bp.x, tid = threadIdx.x, nt = blockDim.x;
+  const int P = d.L, NP = d.NP, c = bp.x, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int Pp = (P + kBlk - 1) / kBlk * kBlk;
   double* M = reinterpret_cast<double*>(smem_raw);  // [P][P] FP64 system for the residuals
   double* x = M + P * P;
@@ -772,17 +772,24 @@ __device__ __forceinline__ void lm_solve_impl(const Dev& d, BlockPos bp) {
     b[r] = fr ? 0.0 : b[r] + p2[r] * th[r];
     x[r] = 0.0;
     res[r] = b[r];
+    double& mrr = M[(size_t)r * P + r];
+    mrr = fr ? 1.0 : mrr + (p2[r] + lam * dgr);
     atomicMax(&bmax_bits, __float_as_uint(fabsf((float)b[r] * sc[r])));
   }
   __syncthreads();
-  // M and, in the same pass, the FP32 lower triangle of D M D (FP64 arithmetic only on the diagonal)
-  for (int e = tid; e < P * P; e += nt) {
-    const int r = e / P, q = e % P;
-    double m = M[e];
-    if (frz[r] | frz[q]) m = r == q ? 1.0 : 0.0;
-    else if (r == q) m = m + (p2[r] + lam * dg[r]);
-    M[e] = m;
-    if (q <= r) F[r][q] = (float)m * sc[r] * sc[q];
+  // the off-diagonal of M (zero in frozen rows and columns) and, in the same pass, the FP32 lower triangle
+  // of D M D; a warp per row
+  for (int r = warp; r < P; r += nt >> 5) {
+    const bool fr = frz[r];
+    const float sr = sc[r];
+    for (int q = lane; q < P; q += 32) {
+      double m = M[(size_t)r * P + q];
+      if (q != r && (fr || frz[q])) {
+        m = 0.0;
+        M[(size_t)r * P + q] = 0.0;
+      }
+      if (q <= r) F[r][q] = (float)m * sr * sc[q];
+    }
   }
   for (int e = tid; e < (Pp - P) * Pp; e += nt) {  // identity rows padding P to a multiple of the block
     const int r = P + e / Pp, q = e % Pp;
