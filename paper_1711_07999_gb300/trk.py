@@ -188,6 +188,16 @@ def joint_positions(skeleton: dict, theta) -> np.ndarray:
     return out
 
 
+def subdivide_counts(face_off, face_vert, n_verts: int, levels: int = 2):
+    """trk_subdivide_counts: (vertices, triangles) after `levels` Catmull-Clark levels of a polygon cage
+    (host connectivity only; no device work)."""
+    fo = np.ascontiguousarray(face_off, np.int32)
+    fv = np.ascontiguousarray(face_vert, np.int32)
+    nv, nt = C.c_int32(), C.c_int32()
+    _check(lib().trk_subdivide_counts(_p(fo), _p(fv), n_verts, len(fo) - 1, levels, C.byref(nv), C.byref(nt)))
+    return nv.value, nt.value
+
+
 def subdivide(verts, face_off, face_vert, bone_idx, bone_w, n_bones: int, levels: int = 2):
     """Template authoring (trk_subdivide): Catmull-Clark subdivision of a polygon cage with its skin
     weights; returns (verts [V'][3] float32, tris [T'][3] int32, bone_idx [V'][4] uint8, bone_w [V'][4])."""
