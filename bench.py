@@ -62,6 +62,24 @@ def _env_int(k, d):
         return d
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values of x (the job takes as long as its slowest rank): an all-reduce of
+    one float64 over the process group (NCCL on the GPUs; gloo when device is "cpu"); x itself at world 1."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, max_seconds):
+    """Units per second of the whole job: every rank processes units_per_rank units (weak scaling, sessions
+    sharded by rank, no data-path collective) and the job ends with its slowest rank."""
+    return world * units_per_rank / max_seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -787,11 +805,8 @@ def run_ours(args, rank, world, local_rank):
     times = np.array([a.elapsed_time(b) for a, b in ev])  # ms
     total_ms = float(times.sum())
     res = sess.read_result(want_offsets=False)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
-    value = world * args.steps / (max_ms / 1000.0)
+    max_ms = max_over_ranks(total_ms, world)
+    value = whole_job_rate(world, args.steps, max_ms / 1000.0)
 
     # end to end through the public call: host pinned depth in, Theta / Phi / energies out
     e2e_t = []
@@ -801,11 +816,7 @@ def run_ours(args, rank, world, local_rank):
         t0 = time.perf_counter()
         sess.track_frame(host[(args.warmup + args.steps + k) % n_seq].numpy(), want_offsets=True)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_t)
-    te = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / float(te.item())
+    e2e_value = whole_job_rate(world, args.steps, max_over_ranks(sum(e2e_t), world))
 
     # per-stage kernel times (CUDA events on the launching stream, cold L2), dominant kernel, roofline
     sess.set_depth(frames[(args.warmup + 2 * args.steps) % n_seq])
@@ -844,17 +855,12 @@ def run_ours(args, rank, world, local_rank):
         for b, x in enumerate(group):
             x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
         tb, lat_b = run_batched(group, dev, n_seq, args.steps, args.warmup, flush)
-        tbt = torch.tensor([tb], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tbt, op=dist.ReduceOp.MAX)
+        tb_max = max_over_ranks(tb, world)
         wall_b, lat_be = run_batched_e2e(group, [host[i].numpy() for i in range(n_seq)], n_seq, args.steps, flush)
-        twb = torch.tensor([wall_b], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(twb, op=dist.ReduceOp.MAX)
-        batched = {"sessions": B, "value": world * B * args.steps / (float(tbt.item()) / 1000.0),
-                   "ms_per_step": float(tbt.item()) / args.steps,
+        batched = {"sessions": B, "value": whole_job_rate(world, B * args.steps, tb_max / 1000.0),
+                   "ms_per_step": tb_max / args.steps,
                    "latency_ms": {"p50": float(np.percentile(lat_b, 50)), "p99": float(np.percentile(lat_b, 99))},
-                   "e2e": {"value": world * B * args.steps / float(twb.item()),
+                   "e2e": {"value": whole_job_rate(world, B * args.steps, max_over_ranks(wall_b, world)),
                            "p50_ms": float(np.percentile(lat_be, 50)), "p99_ms": float(np.percentile(lat_be, 99))}}
         serving = None
         if args.serve_streams > 0:
