@@ -176,6 +176,21 @@ trk_status trk_read_result(trk_session* s, trk_result* out);
  * depth_m (host [height][width], 0 where no triangle covers the pixel).  Does not change the state. */
 trk_status trk_render_depth(trk_session* s, const double* theta, const float* offsets, float* depth_m);
 
+/* Checkpoint of the tracking state: what one frame hands to the next (Theta, Phi, the LM damping lambda
+ * of R14 and the count of frames since trk_set_pose, which shape-match mode reads), as a host byte blob.
+ * A session created from the same model and parameters resumes from it and tracks the following frames
+ * bit for bit as the exporting session would have.  Layout (little-endian): 8 bytes "TRKSTATE", int32
+ * version (1), int32 n_links, int32 n_verts, int32 frames_done, then double Theta [n_links], double
+ * lambda, float Phi [n_verts][4] (x, y, z, 0).
+ * trk_session_export: blob NULL -> *size_bytes = the blob's size; otherwise waits for the session's last
+ * frame, writes the blob into blob (host, *size_bytes bytes) and sets *size_bytes to its size.
+ * trk_session_import: checks the header against the session (format, n_links, n_verts, size) and the
+ * values (finite; lambda > 0; frames_done >= 0), waits for the session's last frame, then sets the
+ * state.  Synchronous.  Errors: TRK_ERR_INVALID_ARG (NULL, a buffer too small, a blob of another
+ * format, model size or length; nothing was changed), TRK_ERR_NUMERIC (non-finite values), TRK_ERR_CUDA. */
+trk_status trk_session_export(trk_session* s, void* blob, size_t* size_bytes);
+trk_status trk_session_import(trk_session* s, const void* blob, size_t size_bytes);
+
 /* Releases every resource of the session.  NULL is allowed. */
 void trk_destroy(trk_session* s);
 

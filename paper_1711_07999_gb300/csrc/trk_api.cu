@@ -675,6 +675,82 @@ trk_status trk_set_pose(trk_session* s, const double* theta, const float* offset
   return sync_check(s);
 }
 
+namespace {
+struct CheckpointHeader {
+  char magic[8];
+  int32_t version, n_links, n_verts, frames_done;
+};
+static_assert(sizeof(CheckpointHeader) == 24, "checkpoint header layout");
+constexpr char kCheckpointMagic[8] = {'T', 'R', 'K', 'S', 'T', 'A', 'T', 'E'};
+constexpr int32_t kCheckpointVersion = 1;
+
+size_t checkpoint_bytes(const Dev& d) {
+  return sizeof(CheckpointHeader) + sizeof(double) * ((size_t)d.L + 1) + sizeof(float4) * (size_t)d.V;
+}
+}  // namespace
+
+trk_status trk_session_export(trk_session* s, void* blob, size_t* size_bytes) {
+  if (!s || !size_bytes) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  const Dev& d = s->d;
+  const size_t need = checkpoint_bytes(d);
+  if (!blob) {
+    *size_bytes = need;
+    return TRK_OK;
+  }
+  if (*size_bytes < need) return fail(TRK_ERR_INVALID_ARG, "checkpoint buffer of %zu bytes, %zu needed", *size_bytes, need);
+  CheckpointHeader h{};
+  std::memcpy(h.magic, kCheckpointMagic, sizeof(h.magic));
+  h.version = kCheckpointVersion;
+  h.n_links = d.L;
+  h.n_verts = d.V;
+  h.frames_done = s->frames_done;
+  unsigned char* p = static_cast<unsigned char*>(blob);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  // on the stream of the last frame, so that the copies follow it
+  cudaStream_t st = s->last_stream ? s->last_stream : s->stream;
+  CK(cudaMemcpyAsync(p, d.theta, sizeof(double) * d.L, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(p + sizeof(double) * d.L, d.lam, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(p + sizeof(double) * (d.L + 1), d.phi[0], sizeof(float4) * d.V, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *size_bytes = need;
+  return TRK_OK;
+}
+
+trk_status trk_session_import(trk_session* s, const void* blob, size_t size_bytes) {
+  if (!s || !blob) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  Dev& d = s->d;
+  CheckpointHeader h;
+  if (size_bytes < sizeof(h)) return fail(TRK_ERR_INVALID_ARG, "checkpoint of %zu bytes is too short", size_bytes);
+  std::memcpy(&h, blob, sizeof(h));
+  if (std::memcmp(h.magic, kCheckpointMagic, sizeof(h.magic)) != 0 || h.version != kCheckpointVersion)
+    return fail(TRK_ERR_INVALID_ARG, "not a session checkpoint of format version %d", kCheckpointVersion);
+  if (h.n_links != d.L || h.n_verts != d.V)
+    return fail(TRK_ERR_INVALID_ARG, "checkpoint of a model with %d links and %d vertices; the session has %d and %d",
+                h.n_links, h.n_verts, d.L, d.V);
+  const size_t need = checkpoint_bytes(d);
+  if (size_bytes != need) return fail(TRK_ERR_INVALID_ARG, "checkpoint of %zu bytes, %zu expected", size_bytes, need);
+  if (h.frames_done < 0) return fail(TRK_ERR_INVALID_ARG, "checkpoint frame count %d", h.frames_done);
+  const unsigned char* p = static_cast<const unsigned char*>(blob) + sizeof(h);
+  std::vector<double> th(d.L + 1);  // Theta, then lambda
+  std::memcpy(th.data(), p, sizeof(double) * (d.L + 1));
+  std::vector<float4> phi(d.V);
+  std::memcpy(phi.data(), p + sizeof(double) * (d.L + 1), sizeof(float4) * d.V);
+  for (int j = 0; j < d.L; ++j)
+    if (!std::isfinite(th[j])) return fail(TRK_ERR_NUMERIC, "checkpoint theta[%d] not finite", j);
+  if (!std::isfinite(th[d.L]) || !(th[d.L] > 0.0)) return fail(TRK_ERR_NUMERIC, "checkpoint lambda %g", th[d.L]);
+  for (int i = 0; i < d.V; ++i)
+    if (!std::isfinite(phi[i].x) || !std::isfinite(phi[i].y) || !std::isfinite(phi[i].z))
+      return fail(TRK_ERR_NUMERIC, "checkpoint offset %d not finite", i);
+  if (s->last_stream) CK(cudaStreamSynchronize(s->last_stream));  // the last frame still reads the state
+  CK(cudaMemcpyAsync(d.theta, th.data(), sizeof(double) * d.L, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(d.lam, th.data() + d.L, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(d.phi[0], phi.data(), sizeof(float4) * d.V, cudaMemcpyHostToDevice, s->stream));
+  launch_fk(d, s->stream);  // H_{j,Delta} and the twists of Theta, as after the frame that wrote them
+  s->frames_done = h.frames_done;
+  return sync_check(s);
+}
+
 trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out) {
   if (!s || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
   cudaGraphExec_t ge;

@@ -23,7 +23,8 @@ FIELDS = dict(VERTS=0, NORMALS=1, ZBUF=2, VISPIX=3, CORR=4, ACC=5, NORMAL_EQ=6, 
 
 # symbols include/trk.h declares (checked by the tests against the library's exports)
 EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_device", "trk_read_result",
-           "trk_render_depth", "trk_destroy", "trk_last_error", "trk_set_depth", "trk_step_skin", "trk_step_raster",
+           "trk_render_depth", "trk_session_export", "trk_session_import", "trk_destroy", "trk_last_error",
+           "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
            "trk_read", "trk_get_info", "trk_profile_iteration", "trk_jtj_rows", "trk_jtj_rows_noalloc",
            "trk_jtj_rows_tc", "trk_fk_joint_positions", "trk_subdivide_counts", "trk_subdivide",
@@ -104,7 +105,8 @@ def lib(build_if_missing: bool = True):
         sigs = {
             "trk_create": [vp, vp, vp, vp, C.POINTER(vp)], "trk_set_pose": [vp, vp, vp],
             "trk_track_frame": [vp, vp, vp], "trk_track_frame_device": [vp, vp, vp], "trk_read_result": [vp, vp],
-            "trk_render_depth": [vp, vp, vp, vp], "trk_set_depth": [vp, vp], "trk_step_skin": [vp],
+            "trk_render_depth": [vp, vp, vp, vp], "trk_session_export": [vp, vp, C.POINTER(sz)],
+            "trk_session_import": [vp, vp, sz], "trk_set_depth": [vp, vp], "trk_step_skin": [vp],
             "trk_step_raster": [vp], "trk_step_visibility": [vp], "trk_step_associate": [vp],
             "trk_step_normal_equations": [vp], "trk_step_lm": [vp], "trk_step_shape": [vp],
             "trk_read": [vp, i32, vp, sz], "trk_get_info": [vp, vp], "trk_profile_iteration": [vp, i32, sz, vp],
@@ -269,6 +271,19 @@ class Session:
         th = np.ascontiguousarray(theta, np.float64)
         of = None if offsets is None else np.ascontiguousarray(offsets, np.float32).reshape(self.V, 3)
         _check(lib().trk_set_pose(self.h, _p(th), _p(of)))
+
+    def export_state(self) -> bytes:
+        """trk_session_export: the tracking state (Theta, Phi, lambda, frames since set_pose) as bytes."""
+        n = C.c_size_t(0)
+        _check(lib().trk_session_export(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib().trk_session_export(self.h, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def import_state(self, blob: bytes):
+        """trk_session_import: resumes from a blob of export_state (same model and parameters)."""
+        b = bytes(blob)
+        _check(lib().trk_session_import(self.h, b, len(b)))
 
     def _result(self, want_offsets=True):
         th = np.empty(self.L, np.float64)

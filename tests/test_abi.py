@@ -27,3 +27,10 @@ def test_library_exports_every_declared_symbol():
 def test_binding_reports_errors_without_a_device():
     lib = trk.lib()
     assert lib.trk_last_error() is not None
+
+
+def test_checkpoint_calls_refuse_null_arguments_without_a_device():
+    lib = trk.lib()
+    n = ctypes.c_size_t(0)
+    assert lib.trk_session_export(None, None, ctypes.byref(n)) == trk.TRK_ERR_INVALID_ARG
+    assert lib.trk_session_import(None, b"TRKSTATE", 8) == trk.TRK_ERR_INVALID_ARG
