@@ -122,6 +122,43 @@ def test_visibility_occlusion_backface_and_image_bounds():
     assert not vis[59:].any()              # projects outside the image
 
 
+def _tiny_triangle(x, y, z, h=0.004):
+    # facing the camera (normal -z), too small to cover a pixel centre of the 40 x 40 camera below
+    return [[x, y, z], [x, y + h, z], [x + h, y, z]]
+
+
+def test_visibility_rounds_to_the_nearest_pixel_and_tolerates_eps_vis():
+    # camera fx = fy = 40, principal point (20, 20), depth 2: u = 20 x + 20.  R7: a front-facing vertex is
+    # visible in the pixel its projection rounds to, if that pixel is in the image and the vertex is at
+    # most eps_vis (1 cm) behind the z-buffer there (or the pixel is empty)
+    occluder, To = H.grid_patch(3, 3, 0.2, 0.6, 0.2, 0.6, 2.0)  # covers pixels 24..32 in u and v
+    tiny = [_tiny_triangle(-0.48, 0.0, 2.0),   # u = 10.4: pixel 10
+            _tiny_triangle(-0.47, 0.0, 2.0),   # u = 10.6: pixel 11
+            _tiny_triangle(0.97, 0.0, 2.0),    # u = 39.4: pixel 39, the last column
+            _tiny_triangle(0.98, 0.0, 2.0),    # u = 39.6: rounds to 40, outside
+            _tiny_triangle(0.4, 0.4, 2.005),   # 5 mm behind the occluder: visible
+            _tiny_triangle(0.3, 0.3, 2.02)]    # 2 cm behind it: hidden
+    verts = np.concatenate([occluder, np.concatenate(tiny)])
+    tris = np.concatenate([To, 9 + np.arange(18).reshape(6, 3)])
+    nV = len(verts)
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, tris, [[0, 0, 0, 0]] * nV, [[1, 0, 0, 0]] * nV,
+                     W=40, H=40, fx=40.0, fy=40.0, cx=20.0, cy=20.0)
+    assert m["params"]["eps_vis"] == 0.01
+    o = oracle.Oracle(m)
+    v, _ = o.skin([0.0])
+    n, ok = o.normals(v)
+    z, _, _ = o.raster(v)
+    vis, pix, _ = o.visibility(v, n, ok, z)
+    t = lambda k: slice(9 + 3 * k, 12 + 3 * k)
+    assert vis[:9].all()
+    assert vis[t(0)].all() and (pix[t(0)] == 20 * 40 + 10).all()
+    assert vis[t(1)].all() and (pix[t(1)] == 20 * 40 + 11).all()
+    assert vis[t(2)].all() and (pix[t(2)] == 20 * 40 + 39).all()
+    assert not vis[t(3)].any() and (pix[t(3)] == -1).all()
+    assert np.isfinite(z.ravel()[pix[t(4)]]).all() and vis[t(4)].all()
+    assert not vis[t(5)].any()
+
+
 def _bruteforce_assoc(o, v, vis, pix, depth, R):
     """Every pixel against every visible vertex whose bucket lies in the window (vectorised over vertices)."""
     W, Hh = o.W, o.H
@@ -189,7 +226,7 @@ def test_single_vertex_collects_every_pixel_within_cutoff():
 def test_association_ties_go_to_smaller_index():
     verts = np.array([[-0.01, 0.0, 2.0], [0.01, 0.0, 2.0], [0.0, 0.2, 2.0]])
     m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 2, 1]], [[0, 0, 0, 0]] * 3, [[1, 0, 0, 0]] * 3,
-                     W=31, H=31, fx=100.0, fy=100.0, window_half=5, cutoff=0.05)
+                     W=31, H=31, fx=100.0, fy=100.0, cx=15.0, cy=15.0, window_half=5, cutoff=0.05)
     o = oracle.Oracle(m)
     v = verts.astype(np.float64)
     vis = np.array([1, 1, 0], np.int32)

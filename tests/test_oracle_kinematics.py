@@ -118,3 +118,24 @@ def test_point_map_is_scale_invariant():
     c = np.array([0, 0, 2.0])
     x = m["mesh"]["verts"].astype(np.float64)
     assert np.allclose(v, (x - c) @ R.T + c, atol=1e-12)
+
+
+def test_blend_of_coaxial_rotations_turns_by_the_blended_half_angle():
+    # Bones 0 and 1 turn about the same axis line (y through (0, 0, 2); link 1 has no offset) by 0.9 and
+    # 0.9 - 1.2 = -0.3 rad.  Blended with weights 0.3 / 0.7 the dual quaternion is not unit (|a|^2 = 0.93);
+    # the point map of R2 then gives the rotation about that line by phi, tan(phi / 2) =
+    # (0.3 sin 0.45 + 0.7 sin -0.15) / (0.3 cos 0.45 + 0.7 cos -0.15) (the blend of coaxial rotations).
+    parent, jtype = [-1, 0], [0, 0]
+    axis = [[0, 1, 0], [0, 1, 0]]
+    offs = [[0, 0, 2.0], [0, 0, 0]]
+    verts = [[0.1, 0.05, 2.0], [0.3, -0.05, 2.1], [0.2, 0.1, 1.95]]
+    m = H.make_model(parent, jtype, axis, offs, verts, [[0, 1, 2]], [[0, 1, 0, 0]] * 3, [[0.3, 0.7, 0, 0]] * 3)
+    o = oracle.Oracle(m)
+    v, _ = o.skin(np.array([0.9, -1.2]))
+    h1, h2 = 0.45, -0.15
+    phi = 2 * math.atan2(0.3 * math.sin(h1) + 0.7 * math.sin(h2), 0.3 * math.cos(h1) + 0.7 * math.cos(h2))
+    R = H.rot_matrix([0, 1, 0], phi)
+    c = np.array([0, 0, 2.0])
+    x = m["mesh"]["verts"].astype(np.float64)
+    assert np.allclose(v, (x - c) @ R.T + c, atol=1e-12)
+

@@ -309,3 +309,64 @@ def test_frame_from_perturbed_start_reduces_energy():
     o.set_state(synth.start_theta(m), None)
     e, acc, na = o.track_frame(depth)
     assert e[m["params"]["pose_iters"] - 1] < 0.6 * e[0]
+
+
+def test_residual_averages_the_points_a_vertex_collects():
+    # Eq. residual with p~_i the mean of the back-projected points assigned to vertex i: a coarse patch
+    # (vertices 0.1 m apart) seen at ~5 px per vertex spacing collects ~25 pixels per vertex; the depth is
+    # a tilted plane in front of it, so the residuals differ from vertex to vertex
+    V, T = H.grid_patch(5, 5, -0.2, 0.2, -0.2, 0.2, 2.0)
+    n = len(V)
+    W = Hh = 64
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], V, T, [[0, 0, 0, 0]] * n, [[1, 0, 0, 0]] * n,
+                     W=W, H=Hh, fx=100.0, fy=100.0, window_half=4, cutoff=0.1)
+    o = oracle.Oracle(m)
+    fx, fy, cx, cy = (m["camera"][k] for k in ("fx", "fy", "cx", "cy"))
+    ys, xs = np.mgrid[0:Hh, 0:W]
+    depth = (2.02 + 0.1 * (xs - cx) / W + 0.05 * (ys - cy) / Hh).astype(np.float32)
+    P = o.pass_at(np.zeros(1), None, depth)
+    assert P["cnt"].max() >= 16
+    sums = np.zeros((n, 3))
+    cnt = np.zeros(n, np.int64)
+    for py, px in zip(*np.nonzero(P["corr"] >= 0)):
+        d = float(depth[py, px])
+        i = P["corr"][py, px]
+        sums[i] += [(px - cx) * d / fx, (py - cy) * d / fy, d]
+        cnt[i] += 1
+    A = cnt > 0
+    r = np.zeros(n)
+    r[A] = (P["n"][A] * (sums[A] / cnt[A, None] - P["v"][A])).sum(1)
+    assert np.array_equal(P["inA"].astype(bool), A & P["nvalid"].astype(bool))
+    assert np.allclose(P["r"], r, rtol=0, atol=1e-12)
+    assert abs(P["E"] - (r ** 2).sum()) <= 1e-12 * (r ** 2).sum()
+
+
+def test_smoothness_alone_moves_each_offset_to_its_neighbours_mean():
+    # Sec. 4.3 with no data term (no associated vertex), lambda_phi = lambda_w = 0: a vertex's energy is
+    # lambda_N sum_{n in N(i)} |phi_i - phi_n|^2 with the neighbours frozen, minimised at their mean; one
+    # Jacobi sweep moves every vertex there at once
+    V, T = H.grid_patch(6, 6, -0.2, 0.2, -0.2, 0.2, 2.0)
+    n = len(V)
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], V, T, [[0, 0, 0, 0]] * n, [[1, 0, 0, 0]] * n,
+                     W=40, H=40, fx=60.0, fy=60.0, window_half=3, lambda_phi=0.0, lambda_w=0.0, shape_sweeps=1)
+    o = oracle.Oracle(m)
+    _, _, nbr = o.derived()
+    phi = np.random.default_rng(9).normal(0, 0.003, (n, 3))
+    zeros3 = np.zeros((n, 3))
+    E, phi1, _, _ = o.shape_step(np.zeros(1), phi, zeros3, zeros3, np.zeros(n, np.int32), np.zeros(n, np.int32))
+    assert np.allclose(phi1, phi[nbr].mean(axis=1), rtol=0, atol=1e-15)
+    lN = m["params"]["lambda_N"]
+    assert abs(E - lN * ((phi[:, None, :] - phi[nbr]) ** 2).sum()) <= 1e-12 * E
+
+
+def test_energy_without_data_is_the_pose_prior():
+    # no depth pixel: A is empty and E_pose = sum_k (lambda_s S_kk theta_k)^2 (Sec. 4.2 pose prior, R10)
+    m = synth.make_model(1, V=800, width=48)
+    o = oracle.Oracle(m)
+    th = synth.start_theta(m) + 0.1
+    P = o.pass_at(th, None, np.zeros((o.H, o.W), np.float32))
+    assert not P["inA"].any()
+    _, S, _ = o.derived()
+    prior = ((m["params"]["lambda_s"] * S * th) ** 2).sum()
+    assert prior > 0 and abs(P["E"] - prior) <= 1e-14 * prior
+

@@ -3,6 +3,7 @@ triangle the z-buffer holds there)."""
 import numpy as np
 
 import oracle
+from tests import helpers as H
 from paper_1711_07999_gb300 import synth
 
 
@@ -69,3 +70,20 @@ def test_uncovered_pixels_get_no_correspondence():
     ztri = np.full_like(P["ztri"], -1)
     corr, acc, cnt, _ = o.associate_rid(P["v"], ztri, depth)
     assert np.all(corr == -1) and np.all(cnt == 0)
+
+
+def test_equidistant_corners_go_to_the_smaller_index():
+    # the pixel at the principal point back-projects to p = (0, 0, 2), inside the triangle and exactly as
+    # far from corner 0 as from corner 1 (mirror images in x); corner 2 is farther
+    verts = np.array([[-0.01, -0.01, 2.0], [0.01, -0.01, 2.0], [0.0, 0.02, 2.0]])
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 2, 1]], [[0, 0, 0, 0]] * 3, [[1, 0, 0, 0]] * 3,
+                     W=31, H=31, fx=100.0, fy=100.0, cx=15.0, cy=15.0, cutoff=0.05)
+    o = oracle.Oracle(m)
+    v = verts.astype(np.float64)
+    _, ztri, _ = o.raster(v)
+    assert ztri[15, 15] == 0
+    depth = np.zeros((31, 31), np.float32)
+    depth[15, 15] = 2.0
+    corr, _, cnt, _ = o.associate_rid(v, ztri, depth)
+    assert corr[15, 15] == 0 and cnt[0] == 1 and cnt[1] == 0
+
