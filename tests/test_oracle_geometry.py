@@ -122,6 +122,23 @@ def test_visibility_occlusion_backface_and_image_bounds():
     assert not vis[59:].any()              # projects outside the image
 
 
+def test_triangle_crossing_the_near_plane_is_skipped():
+    # R6: a triangle with a vertex at z <= z_near is not rasterised (no clipping); a background plane at
+    # 3 m covers the whole image and keeps every pixel
+    back, Tb = H.grid_patch(2, 2, -3.0, 3.0, -3.0, 3.0, 3.0)
+    cross = [[0.0, 0.0, 1.0], [0.2, 0.0, 1.0], [0.1, 0.1, 0.01]]
+    verts = np.concatenate([back, cross])
+    tris = np.concatenate([Tb, [[4, 5, 6]]])
+    nV = len(verts)
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, tris, [[0, 0, 0, 0]] * nV, [[1, 0, 0, 0]] * nV)
+    assert m["params"]["z_near"] > 0.01
+    o = oracle.Oracle(m)
+    v, _ = o.skin([0.0])
+    z, zt, _ = o.raster(v)
+    assert (zt >= 0).all() and (zt < 2).all()
+    assert np.allclose(z, 3.0, rtol=0, atol=1e-12)
+
+
 def _tiny_triangle(x, y, z, h=0.004):
     # facing the camera (normal -z), too small to cover a pixel centre of the 40 x 40 camera below
     return [[x, y, z], [x, y + h, z], [x + h, y, z]]

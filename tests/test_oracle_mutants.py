@@ -175,6 +175,31 @@ MUTANTS = [
     ("subdivision: quad corners in the wrong order",
      "out_quads[4 * q + 1] = V + fedge[face_off[f] + i];", "out_quads[4 * q + 1] = V + fedge[face_off[f] + (i + k - 1) % k];",
      [sub.test_counts_and_euler_characteristic]),
+    ("Jacobian: bone derivatives blended without the R1 signs",
+     "dH = dq_axpy(dH, w * sg[s], dHd[j * L + k]);", "dH = dq_axpy(dH, w, dHd[j * L + k]);",
+     [opt.test_jacobian_matches_central_differences_across_an_antipodal_bone]),
+    ("prismatic derivative: not halved",
+     "h.d = q_make(0, 0.5 * z[0], 0.5 * z[1], 0.5 * z[2]);", "h.d = q_make(0, z[0], z[1], z[2]);",
+     [opt.test_jacobian_matches_central_differences]),
+    ("shape step: residual not re-linearised in later sweeps",
+     "if (inA[i]) ri = r0[i] + gi[0] * (pi[0] - phi0[3 * i]) + gi[1] * (pi[1] - phi0[3 * i + 1]) + gi[2] * (pi[2] - phi0[3 * i + 2]);",
+     "if (inA[i]) ri = r0[i];",
+     [opt.test_second_sweep_is_a_fixed_point_without_smoothness_and_damping]),
+    ("PCG: step length halved",
+     "const double alpha = rz / pAp;", "const double alpha = 0.5 * rz / pAp;",
+     [pcg.test_converged_pcg_minimises_the_quadratic_model, pcg.test_without_smoothness_one_pcg_iteration_is_the_per_vertex_solve]),
+    ("PCG: search directions not conjugated",
+     "for (size_t k = 0; k < n3; ++k) pv[k] = z[k] + beta * pv[k];", "for (size_t k = 0; k < n3; ++k) pv[k] = z[k];",
+     [pcg.test_pcg_iterate_minimises_over_the_krylov_subspace]),
+    ("raster: triangles behind the near plane not skipped",
+     "if (A[2] <= znear || B[2] <= znear || C[2] <= znear) continue;\n    double ua", "double ua",
+     [geo.test_triangle_crossing_the_near_plane_is_skipped]),
+    ("LM: five damping attempts instead of six (R14)",
+     "for (int t = 0; t < 6; ++t) {\n    /* (A + lambda diag A)", "for (int t = 0; t < 5; ++t) {\n    /* (A + lambda diag A)",
+     [opt.test_lm_accepts_only_descent_and_updates_lambda]),
+    ("subdivision: boundary edge point not the midpoint",
+     "EP[(size_t)e * A + c] = E[e].fb < 0 ? 0.5 * (pa + pb)", "EP[(size_t)e * A + c] = E[e].fb < 0 ? (pa + pb) / 3.0",
+     [sub.test_triangle_cage_and_open_boundary]),
 ]
 
 

@@ -370,3 +370,54 @@ def test_energy_without_data_is_the_pose_prior():
     prior = ((m["params"]["lambda_s"] * S * th) ** 2).sum()
     assert prior > 0 and abs(P["E"] - prior) <= 1e-14 * prior
 
+
+def test_jacobian_matches_central_differences_across_an_antipodal_bone():
+    # R1: the child's hinge at 2 pi + 0.3 has a dual quaternion of the opposite sign to its parent's; the
+    # blend and its derivative both carry the alignment sign, so the Jacobian still equals the central
+    # differences of r_i = n_i.(p~_i - v_i(Theta)) (n, p~ fixed)
+    parent, jtype = [-1, 0], [0, 0]
+    axis, offs = [[0, 0, 1], [1, 0, 0]], [[0, 0, 2.0], [0.2, 0, 0]]
+    verts = [[0.1, 0.05, 2.0], [0.3, -0.05, 2.1], [0.2, 0.1, 1.95]]
+    m = H.make_model(parent, jtype, axis, offs, verts, [[0, 1, 2]], [[0, 1, 0, 0]] * 3, [[0.4, 0.6, 0, 0]] * 3)
+    o = oracle.Oracle(m)
+    th = np.array([0.4, 2 * math.pi + 0.3])
+    _, Hd = o.fk(th)
+    assert np.dot(Hd[0, :4], Hd[1, :4]) < 0
+    rng = np.random.default_rng(2)
+    n = rng.normal(size=(3, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    pt = rng.normal(0, 0.05, (3, 3)) + [0.2, 0, 2.0]
+    inA = np.ones(3, np.int32)
+    J = o.jacobian(th, None, n, inA)
+
+    def r_of(t):
+        v, _ = o.skin(t)
+        return np.einsum("ij,ij->i", n, pt - v)
+
+    h = 1e-6
+    for k in range(2):
+        e = np.zeros(2)
+        e[k] = h
+        fd = (r_of(th + e) - r_of(th - e)) / (2 * h)
+        assert np.abs(J[:, k] - fd).max() <= 1e-7 * max(1.0, np.abs(fd).max()), k
+
+
+def test_second_sweep_is_a_fixed_point_without_smoothness_and_damping():
+    # lambda_N = lambda_w = 0: a vertex's linearised energy (r_i + g_i.(phi_i - phi0_i))^2 + lp |phi_i|^2 is
+    # quadratic and one Gauss-Newton sweep lands on its minimiser; a second sweep, with r re-linearised at
+    # the new offsets, finds a zero gradient there and does not move
+    m = synth.make_model(1, V=1200, width=96)
+    m["params"].update(lambda_N=0.0, lambda_w=0.0)
+    one = oracle.Oracle(dict(m, params=dict(m["params"], shape_sweeps=1)))
+    two = oracle.Oracle(dict(m, params=dict(m["params"], shape_sweeps=2)))
+    gt = synth.gt_theta(m, 0)
+    depth = synth.add_noise(one.render(gt, synth.gt_offsets(m, 0)), 1, np.random.default_rng(3))
+    phi = np.random.default_rng(4).normal(0, 0.002, (one.V, 3))
+    P = one.pass_at(gt, phi, depth)
+    assert P["inA"].sum() > 100
+    _, phi1, _, _ = one.shape_step(gt, phi, P["n"], P["acc"], P["cnt"], P["inA"])
+    _, phi2, _, _ = two.shape_step(gt, phi, P["n"], P["acc"], P["cnt"], P["inA"])
+    assert np.abs(phi1 - phi).max() > 1e-4
+    # rounding of the second 3x3 solve (condition ~ 1 / lambda_phi = 100): ~1e-15 on offsets of ~1e-2
+    assert np.allclose(phi2, phi1, rtol=0, atol=1e-13)
+

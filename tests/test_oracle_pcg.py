@@ -90,3 +90,46 @@ def test_energy_returned_is_the_same_for_both_solvers():
     E0, _, r0, g0 = _step(m, o, gt, phi, P, 0, 1)
     E1, _, r1, g1 = _step(m, o, gt, phi, P, 1, 5)
     assert E0 == E1 and np.array_equal(r0, r1) and np.array_equal(g0, g1)
+
+
+def _damped_system(phi, r, g, inA, nbr, lp, lN, lw):
+    """The coupled damped system of R22 assembled from the energy's terms: H = data blocks g g^T on A
+    + lp I + lN (graph Laplacian of the neighbourhood edges, each directed edge once per direction),
+    A = H + lw diag(H), right-hand side -b with b = [A] g r + lp phi + lN L phi."""
+    V = len(phi)
+    Hm = lp * np.eye(3 * V)
+    for i in np.nonzero(inA)[0]:
+        Hm[3 * i:3 * i + 3, 3 * i:3 * i + 3] += np.outer(g[i], g[i])
+    Lap = np.zeros((V, V))
+    for i in range(V):
+        for q in nbr[i]:
+            if q < 0:
+                continue
+            Lap[i, i] += 1; Lap[q, q] += 1; Lap[i, q] -= 1; Lap[q, i] -= 1
+    Hm += lN * np.kron(Lap, np.eye(3))
+    b = lp * phi.ravel() + lN * (np.kron(Lap, np.eye(3)) @ phi.ravel())
+    b[np.repeat(inA.astype(bool), 3)] += (g * r[:, None])[inA.astype(bool)].ravel()
+    return Hm + lw * np.diag(np.diag(Hm)), -b
+
+
+def test_pcg_iterate_minimises_over_the_krylov_subspace():
+    # After k iterations from 0, preconditioned CG minimises the A-norm error over the Krylov subspace
+    # span{M^-1 c, (M^-1 A) M^-1 c, ...} (M the 3x3 diagonal blocks of A, c the right-hand side);
+    # the minimiser there is Q (Q^T A Q)^-1 Q^T c for an orthonormal basis Q of the subspace.
+    m, o, gt, phi, P = _setup(V=150)
+    _, _, r, g = _step(m, o, gt, phi, P, 1, 1)
+    _, _, nbr = o.derived()
+    p = m["params"]
+    A, c = _damped_system(phi, r, g, P["inA"], nbr, p["lambda_phi"], p["lambda_N"], p["lambda_w"])
+    Minv = np.zeros_like(A)
+    for i in range(o.V):
+        Minv[3 * i:3 * i + 3, 3 * i:3 * i + 3] = np.linalg.inv(A[3 * i:3 * i + 3, 3 * i:3 * i + 3])
+    for k in (1, 2, 3):
+        u = [Minv @ c]
+        for _ in range(k - 1):
+            u.append(Minv @ (A @ u[-1]))
+        Q, _ = np.linalg.qr(np.stack(u, 1))
+        x = Q @ np.linalg.solve(Q.T @ A @ Q, Q.T @ c)
+        _, phik, _, _ = _step(m, o, gt, phi, P, 1, k)
+        assert np.abs((phik - phi).ravel() - x).max() <= 1e-9 * np.abs(x).max(), k
+
