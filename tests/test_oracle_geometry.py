@@ -139,6 +139,44 @@ def test_triangle_crossing_the_near_plane_is_skipped():
     assert np.allclose(z, 3.0, rtol=0, atol=1e-12)
 
 
+def test_coincident_triangles_keep_the_smaller_index():
+    # R6: equal depths go to the smaller triangle; the quad's two triangles are duplicated with larger ids
+    V, T = H.grid_patch(2, 2, -0.3, 0.3, -0.3, 0.3, 2.0)
+    tris = np.concatenate([T, T])
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], V, tris, [[0, 0, 0, 0]] * 4, [[1, 0, 0, 0]] * 4)
+    o = oracle.Oracle(m)
+    v, _ = o.skin([0.0])
+    z, zt, _ = o.raster(v)
+    covered = zt >= 0
+    assert covered.sum() > 50
+    assert (zt[covered] < 2).all()
+
+
+def test_back_face_is_judged_along_the_view_ray():
+    # R7 front-facing means n . p < 0 for the camera-frame vertex p.  Two tiny triangles at p ~ (0.9, 0, 2):
+    # one tilted so that n_z < 0 but n . p > 0 (it faces the optical axis, not the ray to it): hidden; one
+    # with n . p < 0: visible
+    def facing(p0, nrm, h=0.004):
+        nrm = np.asarray(nrm, float) / np.linalg.norm(nrm)
+        u1 = np.array([0.0, 1.0, 0.0])
+        u2 = np.cross(nrm, u1)  # (h u1) x (h u2) points along nrm
+        return [p0, p0 + h * u1, p0 + h * u2]
+    p0 = np.array([0.9, 0.0, 2.0])
+    away = facing(p0, [0.92, 0.0, -0.39])
+    toward = facing(p0 + [0, 0.1, 0], [0.3, 0.0, -0.95])
+    verts = np.concatenate([away, toward])
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 1, 2], [3, 4, 5]], [[0, 0, 0, 0]] * 6,
+                     [[1, 0, 0, 0]] * 6, W=40, H=40, fx=40.0, fy=40.0, cx=20.0, cy=20.0)
+    o = oracle.Oracle(m)
+    v, _ = o.skin([0.0])
+    n, ok = o.normals(v)
+    assert ok.all() and (n[:, 2] < 0).all()
+    assert ((n * v).sum(1)[:3] > 0).all() and ((n * v).sum(1)[3:] < 0).all()
+    z, _, _ = o.raster(v)
+    vis, pix, _ = o.visibility(v, n, ok, z)
+    assert not vis[:3].any() and vis[3:].all()
+
+
 def _tiny_triangle(x, y, z, h=0.004):
     # facing the camera (normal -z), too small to cover a pixel centre of the 40 x 40 camera below
     return [[x, y, z], [x, y + h, z], [x + h, y, z]]
@@ -252,6 +290,24 @@ def test_association_ties_go_to_smaller_index():
     depth[15, 15] = 2.0  # p = (0, 0, 2): equidistant from vertices 0 and 1
     corr, *_ = o.associate(v, vis, pix, depth)
     assert corr[15, 15] == 0
+
+
+def test_near_ties_are_flagged():
+    # the oracle flags a pixel whose two best candidates are within 1e-5 m of each other (a decision that
+    # FP32 rounding may take either way); candidates 1 mm apart are not flagged
+    def run(dx1):
+        verts = np.array([[-0.01, 0.0, 2.0], [0.01 + dx1, 0.0, 2.0], [0.0, 0.2, 2.0]])
+        m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 2, 1]], [[0, 0, 0, 0]] * 3,
+                         [[1, 0, 0, 0]] * 3, W=31, H=31, fx=100.0, fy=100.0, cx=15.0, cy=15.0, window_half=5,
+                         cutoff=0.05)
+        o = oracle.Oracle(m)
+        depth = np.zeros((31, 31), np.float32)
+        depth[15, 15] = 2.0
+        corr, _, _, tie = o.associate(verts, np.array([1, 1, 0], np.int32),
+                                      np.array([15 * 31 + 15, 15 * 31 + 16, -1], np.int32), depth, with_tie=True)
+        return corr[15, 15], tie[15, 15]
+    assert run(4e-6) == (0, 1)
+    assert run(1e-3) == (0, 0)
 
 
 def test_knn_equals_brute_force():

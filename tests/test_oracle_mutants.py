@@ -200,6 +200,25 @@ MUTANTS = [
     ("subdivision: boundary edge point not the midpoint",
      "EP[(size_t)e * A + c] = E[e].fb < 0 ? 0.5 * (pa + pb)", "EP[(size_t)e * A + c] = E[e].fb < 0 ? (pa + pb) / 3.0",
      [sub.test_triangle_cage_and_open_boundary]),
+    ("normals: a face's third corner not credited",
+     "for (int t = 0; t < 3; ++t)\n      for (int k = 0; k < 3; ++k) acc[3 * tri[3 * f + t] + k] += fn[k];",
+     "for (int t = 0; t < 2; ++t)\n      for (int k = 0; k < 3; ++k) acc[3 * tri[3 * f + t] + k] += fn[k];",
+     [geo.test_flat_grid_has_constant_normal, geo.test_capsule_normals_are_radial_within_mesh_spacing]),
+    ("visibility: front-facing judged along the optical axis instead of the view ray",
+     "double nd = n[3 * i] * p[0] + n[3 * i + 1] * p[1] + n[3 * i + 2] * p[2];", "double nd = n[3 * i + 2];",
+     [geo.test_back_face_is_judged_along_the_view_ray]),
+    ("z-buffer: depth ties to the later triangle",
+     "if (zt < z[k] || (zt == z[k] && f < ztri[k])) { z[k] = zt; ztri[k] = f; }", "if (zt <= z[k]) { z[k] = zt; ztri[k] = f; }",
+     [geo.test_coincident_triangles_keep_the_smaller_index]),
+    ("LM: no lower bound on lambda (R14)",
+     "if (lk < 1e-7) lk = 1e-7;", "",
+     [opt.test_lm_lambda_stays_within_its_bounds]),
+    ("LM: no upper bound on lambda (R14)",
+     "if (lk > 1e7) lk = 1e7;", "",
+     [opt.test_lm_lambda_stays_within_its_bounds]),
+    ("association: near-equal candidates not flagged as ties",
+     "if (tie && d2nd <= tau + tol && d2nd - d1 < tol) tie[k] = 1;", "",
+     [geo.test_near_ties_are_flagged]),
 ]
 
 

@@ -192,6 +192,19 @@ def test_lm_accepts_only_descent_and_updates_lambda():
     assert a2 == -1 and np.array_equal(th2, th) and lam2 == pytest.approx(lam0 * 1e6)
 
 
+def test_lm_lambda_stays_within_its_bounds():
+    # R14: lambda is clamped to [1e-7, 1e7]: a step accepted at once from 1e-7 keeps 1e-7, six rejections
+    # from 1e6 stop at 1e7
+    m, o, gt, phi, depth, th = _scene(V=1500, width=96, pert_deg=4)
+    P = o.pass_at(th, phi, depth)
+    J = o.jacobian(th, phi, P["n"], P["inA"])
+    JTJ, JTr = oracle.normal_eq(J, P["r"], P["inA"])
+    a, _, lam1, _ = o.lm_step(JTJ, JTr, P["E"], P["v"], P["n"], P["acc"], P["cnt"], P["inA"], th, 1e-7)
+    assert a == 0 and lam1 == 1e-7
+    a2, _, lam2, _ = o.lm_step(JTJ, JTr, -1.0, P["v"], P["n"], P["acc"], P["cnt"], P["inA"], th, 1e6)
+    assert a2 == -1 and lam2 == 1e7
+
+
 def test_single_rigid_link_converges_to_truth():
     # one capsule on the 6-DoF root: point-to-plane Gauss-Newton on noise-free data
     # two capsules in an L, both on the root's last link: a rigid body with no symmetry axis
