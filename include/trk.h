@@ -168,7 +168,7 @@ trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out
 
 /* Enqueues one frame on cuda_stream (a cudaStream_t; NULL = the session's own stream) reading depth
  * from device memory d_depth_m [height][width].  Returns without waiting; trk_read_result waits for
- * the frame and copies its outputs. */
+ * the frame and copies its outputs.  cuda_stream must exist until a call has waited for the frame. */
 trk_status trk_track_frame_device(trk_session* s, const float* d_depth_m, void* cuda_stream);
 trk_status trk_read_result(trk_session* s, trk_result* out);
 
@@ -182,12 +182,14 @@ trk_status trk_render_depth(trk_session* s, const double* theta, const float* of
  * bit for bit as the exporting session would have.  Layout (little-endian): 8 bytes "TRKSTATE", int32
  * version (1), int32 n_links, int32 n_verts, int32 frames_done, then double Theta [n_links], double
  * lambda, float Phi [n_verts][4] (x, y, z, 0).
- * trk_session_export: blob NULL -> *size_bytes = the blob's size; otherwise waits for the session's last
- * frame, writes the blob into blob (host, *size_bytes bytes) and sets *size_bytes to its size.
+ * Both wait for the session's last frame on the stream it was enqueued on, which must still exist (as
+ * for trk_read_result).
+ * trk_session_export: blob NULL -> *size_bytes = the blob's size; otherwise writes the blob into blob
+ * (host, *size_bytes bytes) and sets *size_bytes to its size.
  * trk_session_import: checks the header against the session (format, n_links, n_verts, size) and the
- * values (finite; lambda > 0; frames_done >= 0), waits for the session's last frame, then sets the
- * state.  Synchronous.  Errors: TRK_ERR_INVALID_ARG (NULL, a buffer too small, a blob of another
- * format, model size or length; nothing was changed), TRK_ERR_NUMERIC (non-finite values), TRK_ERR_CUDA. */
+ * values (finite; lambda > 0; frames_done >= 0), then sets the state.  Synchronous.
+ * Errors: TRK_ERR_INVALID_ARG (NULL, a buffer too small, a blob of another format, model size or length;
+ * nothing was changed), TRK_ERR_NUMERIC (non-finite values), TRK_ERR_CUDA. */
 trk_status trk_session_export(trk_session* s, void* blob, size_t* size_bytes);
 trk_status trk_session_import(trk_session* s, const void* blob, size_t size_bytes);
 
