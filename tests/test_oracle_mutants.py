@@ -219,6 +219,12 @@ MUTANTS = [
     ("association: near-equal candidates not flagged as ties",
      "if (tie && d2nd <= tau + tol && d2nd - d1 < tol) tie[k] = 1;", "",
      [geo.test_near_ties_are_flagged]),
+    ("frame: shape iterations without re-association (R18)",
+     "    associate_pass(m, &w, depth);\n    energy[m->p.pose_iters + s]", "    energy[m->p.pose_iters + s]",
+     [opt.test_frame_is_the_schedule_of_its_steps]),
+    ("frame: one pose iteration fewer (R18)",
+     "for (int it = 0; it < m->p.pose_iters; ++it) {\n    double E = associate_pass", "for (int it = 1; it < m->p.pose_iters; ++it) {\n    double E = associate_pass",
+     [opt.test_frame_is_the_schedule_of_its_steps]),
 ]
 
 

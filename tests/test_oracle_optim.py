@@ -434,3 +434,32 @@ def test_second_sweep_is_a_fixed_point_without_smoothness_and_damping():
     # rounding of the second 3x3 solve (condition ~ 1 / lambda_phi = 100): ~1e-15 on offsets of ~1e-2
     assert np.allclose(phi2, phi1, rtol=0, atol=1e-13)
 
+
+def test_frame_is_the_schedule_of_its_steps():
+    # R18: a frame is pose_iters LM iterations, each re-associating at the current state (skin, normals,
+    # z-buffer, visibility, association, residuals, Jacobian, normal equations, LM step), then shape_iters
+    # shape iterations, each re-associating too.  The frame equals those steps called one by one: the
+    # same energies, accepted attempts, Theta, Phi and lambda, bit for bit.
+    m, _, gt, phi0, depth, th0 = _scene(V=1500, width=96, pert_deg=3)
+    m = dict(m, params=dict(m["params"], pose_iters=3, shape_iters=1, shape_sweeps=1))
+    frame, steps = oracle.Oracle(m), oracle.Oracle(m)
+    lam0 = 1e-3
+    frame.set_state(th0, phi0, lam0)
+    steps.set_state(th0, phi0, lam0)
+    th, lam, E_ref, acc_ref = th0.copy(), lam0, [], []
+    for _ in range(3):
+        P = steps.pass_at(th, phi0, depth)
+        E_ref.append(P["E"])
+        J = steps.jacobian(th, phi0, P["n"], P["inA"])
+        JTJ, JTr = oracle.normal_eq(J, P["r"], P["inA"])
+        a, th, lam, _ = steps.lm_step(JTJ, JTr, P["E"], P["v"], P["n"], P["acc"], P["cnt"], P["inA"], th, lam)
+        acc_ref.append(a)
+    P = steps.pass_at(th, phi0, depth)
+    E_shape, phi1, _, _ = steps.shape_step(th, phi0, P["n"], P["acc"], P["cnt"], P["inA"])
+    e, acc, n_assoc = frame.track_frame(depth)
+    th_f, phi_f, lam_f = frame.get_state()
+    assert list(acc) == acc_ref and max(acc_ref) >= 0
+    assert list(e) == E_ref + [E_shape]
+    assert np.array_equal(th_f, th) and np.array_equal(phi_f, phi1) and lam_f == lam
+    assert n_assoc == int((P["corr"] >= 0).sum())
+
