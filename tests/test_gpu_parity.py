@@ -182,6 +182,7 @@ def test_shape_step(cfg1):
 
 def test_render_depth_matches_oracle(cfg1):
     m, o, depth, th, phi, s = cfg1
+    state = [s.read(f) for f in ("THETA", "PHI", "LAMBDA")]
     d_gpu = s.render_depth(th, phi).astype(np.float64)
     v = o.skin(th, phi)[0]
     z_ref, _, amb = o.raster(v, with_amb=True)
@@ -190,19 +191,22 @@ def test_render_depth_matches_oracle(cfg1):
     both = ok & (ref > 0) & (d_gpu > 0)
     assert np.array_equal((d_gpu > 0)[ok], (ref > 0)[ok]) or ((d_gpu > 0) != (ref > 0))[ok].sum() < 5
     assert np.abs(d_gpu[both] - ref[both]).max() < 1e-5
-    # rendering leaves the tracking state alone
-    assert np.allclose(s.read("THETA"), o.get_state()[0]) or True
+    # rendering leaves the tracking state (Theta, Phi, the LM damping) bit for bit alone
+    for f, before in zip(("THETA", "PHI", "LAMBDA"), state):
+        assert np.array_equal(s.read(f), before), f
 
 
 def _assert_offsets_close(phi, phi_ref):
-    """Free-running offsets: 0.05 mm except at vertices whose pixels changed owner at an association
-    tie (distances within 1e-5 m) in one of the shape iterations: their shape step sees a residual that
-    differs by the flipped pixel's offset (or it enters / leaves A), so its step can differ by up to the
-    association cutoff.  Those are at most 1 % of the mesh; the 99th percentile stays within 0.05 mm."""
+    """Free-running offsets.  The frame-by-frame lockstep tests (test_gpu_sequence.py) hold every vertex
+    to 0.05 mm; here the two paths may part at a correspondence tie (a pixel whose two nearest vertices
+    lie within ~1e-7 m of each other goes to the other vertex), and the shape step of the vertices around
+    such a pixel then sees a residual that differs by that pixel's offset: up to about one pixel
+    footprint (< 2.5 mm at 2.5 m and 140 px focal length, < 6 mm at 3 m and 525 px).  So: the 99th
+    percentile within 0.05 mm, at most 0.5 % of the vertices beyond it, none beyond 6 mm."""
     d = np.abs(phi - phi_ref).max(axis=1)
     assert np.percentile(d, 99) < 5e-5, np.percentile(d, 99)
-    assert (d > 5e-5).mean() <= 1e-2, (d > 5e-5).sum()
-    assert d.max() < 0.05, d.max()
+    assert (d > 5e-5).mean() <= 5e-3, (d > 5e-5).sum()
+    assert d.max() < 6e-3, d.max()
 
 
 def _track_both(m, o, depth, th0, frames=1):
@@ -253,8 +257,8 @@ def test_energy_per_iteration_at_matched_state():
 
 
 def test_frame_sequence_config2_full_size():
-    """The 50k-vertex / 640x480 workload, two frames of its sequence, through the same graph the
-    benchmark times."""
+    """The 50k-vertex / 640x480 workload, two frames of its sequence, free-running through the same graph
+    the benchmark times (the lockstep comparison of every frame is in test_gpu_sequence.py)."""
     m = synth.make_model(2)
     o = oracle.Oracle(m)
     rng = np.random.default_rng(11)
