@@ -193,6 +193,27 @@ trk_status trk_render_depth(trk_session* s, const double* theta, const float* of
 trk_status trk_session_export(trk_session* s, void* blob, size_t* size_bytes);
 trk_status trk_session_import(trk_session* s, const void* blob, size_t size_bytes);
 
+/* Device residency.  A session's device state (model data, tracking state and work buffers: the
+ * device_bytes of trk_info) is ONE allocation from the current device's stream-ordered allocator.  An
+ * evicted session holds no device memory: its model data and tracking state (Theta, Phi, lambda, frames
+ * since trk_set_pose) wait on the host.  This is what lets a frame server admit sessions under an HBM
+ * budget (trk_server_attach restores an evicted session, trk_server_detach evicts it again).
+ * trk_create_evicted: as trk_create, without the device allocation (Theta = 0, Phi = 0 on the host).
+ * trk_session_evict: waits for the session's last frame (on the stream it was enqueued on, which must
+ *   still exist), copies the tracking state to the host, frees the device state and the frame graphs.
+ *   Batches and schedules built on the session become invalid (their next call fails with
+ *   TRK_ERR_INVALID_ARG); a restored session needs a new batch or schedule.  No-op when evicted.
+ * trk_session_restore: allocates and fills the device state again and restores the tracking state; the
+ *   session then tracks bit for bit as if it had never been evicted.  No-op when resident.
+ * While evicted, trk_set_pose, trk_session_export / trk_session_import and trk_get_info work on the host
+ * copy; every call that runs kernels or reads device buffers fails with TRK_ERR_INVALID_ARG.
+ * Errors: TRK_ERR_INVALID_ARG, TRK_ERR_OOM (restore), TRK_ERR_CUDA. */
+trk_status trk_create_evicted(const trk_mesh* mesh, const trk_skeleton* skel, const trk_intrinsics* cam,
+                              const trk_params* params, trk_session** out);
+trk_status trk_session_evict(trk_session* s);
+trk_status trk_session_restore(trk_session* s);
+int32_t trk_session_is_resident(const trk_session* s); /* 1 resident, 0 evicted or NULL */
+
 /* Releases every resource of the session.  NULL is allowed. */
 void trk_destroy(trk_session* s);
 
@@ -278,20 +299,38 @@ typedef struct {
   uint64_t frames_done;     /* frames completed since the server was created            */
   int32_t in_flight;        /* frames on the GPU now                                     */
   int32_t sessions;         /* attached sessions                                         */
-  size_t hbm_used_bytes;    /* device bytes of the attached sessions                     */
-  double latency_p50_us, latency_p99_us, latency_max_us;  /* submit -> completion, wall time */
+  size_t hbm_used_bytes;    /* device bytes of the attached sessions (what the budget counts) */
+  double latency_p50_us, latency_p99_us, latency_max_us;  /* submit -> completion, wall time; the
+                               percentiles to 1.2 % (log-spaced bins), the maximum exact */
+  uint64_t steps;           /* launches of frames: batched steps plus single-session frames */
+  double mean_frames_per_step;
 } trk_server_stats;
+
+/* How the dispatcher launches ready frames.  BATCHED (the default): the ready frames of sessions that
+ * share the iteration schedule, precision, association and tracking mode (TRK_MODE_TRACK) go into one
+ * batched frame -- every stage one kernel launch over the blocks of all of them -- with the depth read
+ * from and the results written to host-mapped pinned staging; sessions in other modes run alone.
+ * SESSION: every frame runs its session's own frame graph on the session's stream. */
+#define TRK_SERVER_DISPATCH_BATCHED 0
+#define TRK_SERVER_DISPATCH_SESSION 1
 
 /* Creates a frame server on the current device.  Sessions are admitted while the sum of their device
  * memory stays within hbm_budget_bytes; at most max_inflight frames run on the GPU at a time (0 admits
- * frames but never launches them).  A dispatcher thread launches a session's next frame on the
- * session's own stream as soon as its previous frame is done and a slot is free, so frames of different
+ * frames but never launches them).  A dispatcher thread launches a session's next frame as soon as its
+ * previous frame is done and a slot is free (see TRK_SERVER_DISPATCH_*), so frames of different
  * sessions overlap on the device and one session's frames run in submission order. */
 trk_status trk_server_create(size_t hbm_budget_bytes, int32_t max_inflight, trk_server** out);
-/* Admits a session (same device).  TRK_ERR_NO_CAPACITY if it does not fit the remaining budget.  While
- * attached, the session must be driven only through the server. */
+/* Dispatch mode, the most frames in one batched step (1..4096, default 64) and the number of batched
+ * steps that may run at once (1..16, default 2, each on its own stream).  Only before the first attach. */
+trk_status trk_server_configure(trk_server* sv, int32_t dispatch, int32_t max_batch, int32_t concurrent_steps);
+/* Admits a session (same device).  TRK_ERR_NO_CAPACITY if its device bytes do not fit the remaining
+ * budget.  An evicted session (trk_create_evicted, trk_session_evict) is restored here -- its device
+ * state is allocated at admission -- and evicted again at trk_server_detach, so the budget bounds the
+ * device memory of such sessions; a session that is already resident is counted but holds its memory
+ * regardless.  While attached, the session must be driven only through the server. */
 trk_status trk_server_attach(trk_server* sv, trk_session* s);
-/* Releases a session's budget; TRK_ERR_INVALID_ARG while it still has frames queued or running. */
+/* Releases a session's budget (evicting it if attach restored it); TRK_ERR_INVALID_ARG while it still
+ * has frames queued or running. */
 trk_status trk_server_detach(trk_server* sv, trk_session* s);
 /* Queues one frame (host depth [height][width], copied at the call) and returns its ticket. */
 trk_status trk_server_submit(trk_server* sv, trk_session* s, const float* depth_m, uint64_t* ticket);
@@ -300,7 +339,8 @@ trk_status trk_server_submit(trk_server* sv, trk_session* s, const float* depth_
  * for an unknown or already collected ticket.  Each ticket is collected once. */
 trk_status trk_server_wait(trk_server* sv, uint64_t ticket, int64_t timeout_us, trk_result* out);
 trk_status trk_server_get_stats(trk_server* sv, trk_server_stats* out);
-/* Stops the dispatcher, waits for frames on the GPU and frees every uncollected frame. */
+/* Stops the dispatcher, waits for frames on the GPU, frees every uncollected frame and evicts the
+ * sessions that attach restored. */
 void trk_server_destroy(trk_server* sv);
 
 /* ---- Standalone contraction ------------------------------------------------------------------- */
@@ -320,7 +360,10 @@ trk_status trk_jtj_rows(const float* d_rows, int32_t n_rows, int32_t n_cols, int
  * may not call the CUDA allocator once running (cudaMalloc and cudaFree can synchronise the device and
  * take unbounded time), or a host whose device memory is owned by another allocator or a fixed budget
  * that forbids side allocations.  The paper has no counterpart; this is an interface for such callers.
- * Arguments and results are those of trk_jtj_rows; the caller passes the rows and the output buffer.
+ * Arguments, layout and tolerance are those of trk_jtj_rows; the caller passes the rows and the output
+ * buffer.  It runs at most 152 CTAs (trk_jtj_rows up to 296), so its result is bitwise that of
+ * trk_jtj_rows when n_rows <= 152 * 256 = 38,912 (both use ceil(n_rows / 256) CTAs) and otherwise
+ * differs from it by rounding only (the CTA partials split the rows differently).
  * Scratch: a fixed array of 152 x 80 x 80 floats (3.9 MB) that every device loading this library holds
  * until the process exits, shared by all calls.  Each call overwrites the part it uses, so no clearing
  * is needed, but calls that overlap on the GPU (concurrent streams, threads) race on it: serialise them.

@@ -9,6 +9,7 @@
 // it computes alone: blocks of different sessions touch disjoint buffers, and every per-session
 // reduction keeps its fixed order.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "../../include/trk.h"
@@ -19,6 +20,8 @@ const Dev& session_dev(const trk_session* s);
 const trk_params& session_params(const trk_session* s);
 int session_device(const trk_session* s);
 void session_set_last_stream(trk_session* s, cudaStream_t st);
+bool session_resident(const trk_session* s);
+unsigned session_generation(const trk_session* s);
 }  // namespace trk
 
 using namespace trk;
@@ -40,6 +43,7 @@ struct Table {
 
 struct trk_batch {
   std::vector<trk_session*> sessions;
+  std::vector<unsigned> generations;  // each member's device-state generation when the batch was built
   int device = 0;
   int pose_iters = 0, shape_iters = 0, shape_sweeps = 0, precision = 0, shape_solver = 0;
   int max_links = 0, max_np = 0;
@@ -62,6 +66,13 @@ namespace {
 
 BatchGrid grid_of(const trk_batch* b, Kind k) { return BatchGrid{b->d_devs, b->tables[k].d_map}; }
 
+// The members' device state is still the one the batch's tables and graph point into.
+bool members_current(const trk_batch* b) {
+  for (size_t k = 0; k < b->sessions.size(); ++k)
+    if (!session_resident(b->sessions[k]) || session_generation(b->sessions[k]) != b->generations[k]) return false;
+  return true;
+}
+
 // Blocks of session s in the launches of kind k.
 void blocks_of(const Dev& d, Kind k, int& gx, int& gy) {
   const int npx = d.cam.W * d.cam.H;
@@ -80,39 +91,80 @@ void blocks_of(const Dev& d, Kind k, int& gx, int& gy) {
   }
 }
 
-void enqueue_batch_frame(trk_batch* b, cudaStream_t st) {
-  const int B = (int)b->sessions.size();
-  const int P = b->pose_iters, S = b->shape_iters;
-  const int L = b->max_links;
-  cudaMemsetAsync(b->d_ctl, 0, sizeof(unsigned) * 3, st);
-  launch_gather_depth_b(grid_of(b, kAssoc), b->tables[kAssoc].n, b->d_srcs, b->d_tiles, b->d_ctl, st);
+// One batched frame over a set of sessions: the block tables, the sessions' descriptors and the scratch
+// of the association, wherever they live (a trk_batch's own buffers or a server step's).
+struct FrameView {
+  int B = 0, P = 0, S = 0, sweeps = 0, solver = 0, precision = 0, max_links = 0;
+  int assoc_blocks = 0, tail_blocks = 0;
+  const Dev* d_devs = nullptr;
+  Table tables[kKinds];
+  unsigned* d_ctl = nullptr;        // [3]
+  unsigned* d_prefix = nullptr;     // [B + 1]
+  int4* d_tiles = nullptr;          // [tables[kAssoc].n]
+  const float* const* d_srcs = nullptr;  // [B] depth of each session (device-readable)
+  const Dev* const* host_devs = nullptr;  // [B] the sessions' descriptors on the host
+};
+
+BatchGrid grid_of(const FrameView& v, Kind k) { return BatchGrid{v.d_devs, v.tables[k].d_map}; }
+
+void enqueue_frame_view(const FrameView& v, cudaStream_t st) {
+  const int B = v.B, P = v.P, S = v.S, L = v.max_links;
+  cudaMemsetAsync(v.d_ctl, 0, sizeof(unsigned) * 3, st);
+  launch_gather_depth_b(grid_of(v, kAssoc), v.tables[kAssoc].n, v.d_srcs, v.d_tiles, v.d_ctl, st);
   int cur = 0;
   auto geometry = [&]() {
-    launch_skin_b(grid_of(b, kSkin), b->tables[kSkin].n, L, cur, b->d_ctl, st);
-    launch_raster_b(grid_of(b, kTris), b->tables[kTris].n, st);
-    launch_visibility_b(grid_of(b, kVerts), b->tables[kVerts].n, st);
-    launch_associate_b(b->d_devs, B, b->d_tiles, b->d_ctl, b->d_prefix, b->assoc_blocks, b->tail_blocks, st);
+    launch_skin_b(grid_of(v, kSkin), v.tables[kSkin].n, L, cur, v.d_ctl, st);
+    launch_raster_b(grid_of(v, kTris), v.tables[kTris].n, st);
+    launch_visibility_b(grid_of(v, kVerts), v.tables[kVerts].n, st);
+    launch_associate_b(v.d_devs, B, v.d_tiles, v.d_ctl, v.d_prefix, v.assoc_blocks, v.tail_blocks, st);
   };
   for (int it = 0; it < P; ++it) {
     geometry();
     BatchGrid gj[5];
     int nj[5];
     for (int t = 0; t < 5; ++t) {
-      gj[t] = grid_of(b, (Kind)(kJtj1 + t));
-      nj[t] = b->tables[kJtj1 + t].n;
+      gj[t] = grid_of(v, (Kind)(kJtj1 + t));
+      nj[t] = v.tables[kJtj1 + t].n;
     }
-    launch_normal_equations_b(gj, nj, grid_of(b, kReduce), b->tables[kReduce].n, L, b->precision, cur, it, st);
-    launch_lm_b(grid_of(b, kLm), b->tables[kLm].n, grid_of(b, kRows), b->tables[kRows].n, L, cur, st);
+    launch_normal_equations_b(gj, nj, grid_of(v, kReduce), v.tables[kReduce].n, L, v.precision, cur, it, st);
+    launch_lm_b(grid_of(v, kLm), v.tables[kLm].n, grid_of(v, kRows), v.tables[kRows].n, L, cur, st);
   }
   for (int it = 0; it < S; ++it) {
     geometry();
-    cur = launch_shape_b(grid_of(b, kVerts), b->tables[kVerts].n, L, b->shape_sweeps, b->shape_solver, cur, P + it, st);
+    cur = launch_shape_b(grid_of(v, kVerts), v.tables[kVerts].n, L, v.sweeps, v.solver, cur, P + it, st);
   }
   if (cur != 0)
-    for (trk_session* s : b->sessions) {
-      const Dev& d = session_dev(s);
+    for (int k = 0; k < B; ++k) {
+      const Dev& d = *v.host_devs[k];
       cudaMemcpyAsync(d.phi[0], d.phi[cur], sizeof(float4) * d.V, cudaMemcpyDeviceToDevice, st);
     }
+}
+
+FrameView view_of(const trk_batch* b, const std::vector<const Dev*>& host_devs) {
+  FrameView v;
+  v.B = (int)b->sessions.size();
+  v.P = b->pose_iters;
+  v.S = b->shape_iters;
+  v.sweeps = b->shape_sweeps;
+  v.solver = b->shape_solver;
+  v.precision = b->precision;
+  v.max_links = b->max_links;
+  v.assoc_blocks = b->assoc_blocks;
+  v.tail_blocks = b->tail_blocks;
+  v.d_devs = b->d_devs;
+  for (int k = 0; k < kKinds; ++k) v.tables[k] = b->tables[k];
+  v.d_ctl = b->d_ctl;
+  v.d_prefix = b->d_prefix;
+  v.d_tiles = b->d_tiles;
+  v.d_srcs = b->d_srcs;
+  v.host_devs = host_devs.data();
+  return v;
+}
+
+void enqueue_batch_frame(trk_batch* b, cudaStream_t st) {
+  std::vector<const Dev*> hd;
+  for (trk_session* s : b->sessions) hd.push_back(&session_dev(s));
+  enqueue_frame_view(view_of(b, hd), st);
 }
 
 void free_batch(trk_batch* b) {
@@ -175,6 +227,10 @@ trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_
         free_batch(b);
         return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: a session appears twice");
       }
+    if (!session_resident(s)) {
+      free_batch(b);
+      return set_error(TRK_ERR_INVALID_ARG, "trk_batch_create: a session is evicted (trk_session_restore first)");
+    }
     const trk_params& p = session_params(s);
     if (p.mode != TRK_MODE_TRACK) {
       free_batch(b);
@@ -191,6 +247,7 @@ trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_
     b->max_links = std::max(b->max_links, d.L);
     b->max_np = std::max(b->max_np, d.NP);
     b->sessions.push_back(s);
+    b->generations.push_back(session_generation(s));
   }
   int cur_dev = 0;
   cudaGetDevice(&cur_dev);
@@ -235,6 +292,157 @@ trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_
   return TRK_OK;
 }
 
+// ---- one batched frame over a varying set of sessions (the frame server's batched dispatch) --------
+//
+// Unlike a trk_batch (fixed members, one captured graph), a BatchStep launches the ~110 stage kernels of
+// one frame directly, for whichever sessions have a frame ready.  Its tables, descriptors, depth and
+// result pointers travel in one host-to-device copy from a pinned mirror; depth is read and results are
+// written straight from / into host-mapped pinned memory (zero copy over the chip-to-chip link), so a
+// step costs its launches, one small upload and no per-session copies.
+
+__global__ void __launch_bounds__(256) k_results_b(BatchGrid g, const ResultDst* __restrict__ dst) {
+  const int4 m = g.map[blockIdx.x];
+  const Dev& d = g.devs[m.x];
+  const ResultDst o = dst[m.x];
+  const int i = m.y * 256 + threadIdx.x;
+  if (i < d.V) o.phi[i] = d.phi[0][i];
+  if (m.y == 0) {
+    for (int t = threadIdx.x; t < d.L; t += blockDim.x) o.theta[t] = d.theta[t];
+    for (int t = threadIdx.x; t < d.pose_iters + d.shape_iters; t += blockDim.x) o.energy[t] = d.energy[t];
+    if (threadIdx.x < 4) o.stats[threadIdx.x] = d.stats[threadIdx.x];
+  }
+}
+
+struct BatchStep {
+  char* d_buf = nullptr;  // device: [upload part | ctl, prefix, tiles]
+  char* h_buf = nullptr;  // pinned mirror of the upload part
+  size_t d_cap = 0, h_cap = 0;
+  cudaEvent_t uploaded = nullptr;  // the last upload out of h_buf has been done
+};
+
+BatchStep* batch_step_create() {
+  BatchStep* bs = new BatchStep();
+  if (cudaEventCreateWithFlags(&bs->uploaded, cudaEventDisableTiming) != cudaSuccess) {
+    delete bs;
+    return nullptr;
+  }
+  return bs;
+}
+
+void batch_step_destroy(BatchStep* bs, cudaStream_t st) {
+  if (!bs) return;
+  cudaEventSynchronize(bs->uploaded);
+  if (bs->d_buf) cudaFreeAsync(bs->d_buf, st);
+  cudaStreamSynchronize(st);
+  if (bs->h_buf) cudaFreeHost(bs->h_buf);
+  cudaEventDestroy(bs->uploaded);
+  delete bs;
+}
+
+namespace {
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+}  // namespace
+
+trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const float* const* srcs,
+                             const ResultDst* dst, cudaStream_t st) {
+  if (!bs || !ss || n < 1 || n > kMaxBatch || !srcs || !dst)
+    return set_error(TRK_ERR_INVALID_ARG, "batch step: bad arguments");
+  const trk_params& p0 = session_params(ss[0]);
+  int max_links = 0;
+  std::vector<const Dev*> hd(n);
+  for (int k = 0; k < n; ++k) {
+    const trk_params& p = session_params(ss[k]);
+    if (!session_resident(ss[k])) return set_error(TRK_ERR_INVALID_ARG, "batch step: a session is evicted");
+    if (p.mode != TRK_MODE_TRACK || p.pose_iters != p0.pose_iters || p.shape_iters != p0.shape_iters ||
+        p.shape_sweeps != p0.shape_sweeps || p.precision != p0.precision || p.shape_solver != p0.shape_solver ||
+        p.association != p0.association)
+      return set_error(TRK_ERR_INVALID_ARG, "batch step: sessions of different schedules, precision or mode");
+    hd[k] = &session_dev(ss[k]);
+    max_links = std::max(max_links, hd[k]->L);
+  }
+  // the block tables of this set of sessions
+  std::vector<int4> maps[kKinds + 1];  // kKinds: the result kernel's (the vertex blocks)
+  for (int k = 0; k < kKinds; ++k)
+    for (int q = 0; q < n; ++q) {
+      int gx = 0, gy = 0;
+      blocks_of(*hd[q], (Kind)k, gx, gy);
+      for (int y = 0; y < gy; ++y)
+        for (int x = 0; x < gx; ++x) maps[k].push_back(make_int4(q, x, y, gx));
+    }
+  // layout: devs | srcs | dst | maps ... (uploaded) | ctl | prefix | tiles (device only)
+  size_t off = 0;
+  const size_t o_devs = off; off = align16(off + sizeof(Dev) * n);
+  const size_t o_srcs = off; off = align16(off + sizeof(float*) * n);
+  const size_t o_dst = off; off = align16(off + sizeof(ResultDst) * n);
+  size_t o_map[kKinds];
+  for (int k = 0; k < kKinds; ++k) {
+    o_map[k] = off;
+    off = align16(off + sizeof(int4) * maps[k].size());
+  }
+  const size_t upload = off;
+  const size_t o_ctl = off; off = align16(off + sizeof(unsigned) * 4);
+  const size_t o_prefix = off; off = align16(off + sizeof(unsigned) * (n + 1));
+  const size_t o_tiles = off; off = align16(off + sizeof(int4) * std::max<size_t>(maps[kAssoc].size(), 1));
+  const size_t total = off;
+  // the previous upload out of the pinned mirror has been done
+  cudaError_t e = cudaEventSynchronize(bs->uploaded);
+  if (e == cudaSuccess && total > bs->d_cap) {  // grow (stream-ordered: no device-wide synchronisation)
+    if (bs->d_buf) e = cudaFreeAsync(bs->d_buf, st);
+    bs->d_buf = nullptr;
+    bs->d_cap = 0;
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&bs->d_buf), 2 * total, st);
+    if (e == cudaSuccess) bs->d_cap = 2 * total;
+  }
+  if (e == cudaSuccess && upload > bs->h_cap) {
+    if (bs->h_buf) cudaFreeHost(bs->h_buf);
+    bs->h_buf = nullptr;
+    bs->h_cap = 0;
+    e = cudaMallocHost(reinterpret_cast<void**>(&bs->h_buf), 2 * upload);
+    if (e == cudaSuccess) bs->h_cap = 2 * upload;
+  }
+  if (e != cudaSuccess)
+    return set_error(e == cudaErrorMemoryAllocation ? TRK_ERR_OOM : TRK_ERR_CUDA, cudaGetErrorString(e));
+  char* h = bs->h_buf;
+  for (int k = 0; k < n; ++k) std::memcpy(h + o_devs + sizeof(Dev) * k, hd[k], sizeof(Dev));
+  std::memcpy(h + o_srcs, srcs, sizeof(float*) * n);
+  std::memcpy(h + o_dst, dst, sizeof(ResultDst) * n);
+  for (int k = 0; k < kKinds; ++k)
+    if (!maps[k].empty()) std::memcpy(h + o_map[k], maps[k].data(), sizeof(int4) * maps[k].size());
+  e = cudaMemcpyAsync(bs->d_buf, h, upload, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(bs->uploaded, st);
+  if (e != cudaSuccess) return set_error(TRK_ERR_CUDA, cudaGetErrorString(e));
+  char* dbuf = bs->d_buf;
+  FrameView v;
+  v.B = n;
+  v.P = p0.pose_iters;
+  v.S = p0.shape_iters;
+  v.sweeps = p0.shape_sweeps;
+  v.solver = p0.shape_solver;
+  v.precision = p0.precision;
+  v.max_links = max_links;
+  v.assoc_blocks = 4 * 152;
+  v.tail_blocks = 2 * 152;
+  v.d_devs = reinterpret_cast<const Dev*>(dbuf + o_devs);
+  for (int k = 0; k < kKinds; ++k) {
+    v.tables[k].n = (int)maps[k].size();
+    v.tables[k].d_map = maps[k].empty() ? nullptr : reinterpret_cast<int4*>(dbuf + o_map[k]);
+  }
+  v.d_ctl = reinterpret_cast<unsigned*>(dbuf + o_ctl);
+  v.d_prefix = reinterpret_cast<unsigned*>(dbuf + o_prefix);
+  v.d_tiles = reinterpret_cast<int4*>(dbuf + o_tiles);
+  v.d_srcs = reinterpret_cast<const float* const*>(dbuf + o_srcs);
+  v.host_devs = hd.data();
+  enqueue_frame_view(v, st);
+  const int nv = v.tables[kVerts].n;
+  if (nv > 0)
+    k_results_b<<<nv, 256, 0, st>>>(BatchGrid{v.d_devs, v.tables[kVerts].d_map},
+                                    reinterpret_cast<const ResultDst*>(dbuf + o_dst));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(TRK_ERR_CUDA, cudaGetErrorString(e));
+  for (int k = 0; k < n; ++k) session_set_last_stream(ss[k], st);
+  return TRK_OK;
+}
+
 }  // namespace trk
 
 extern "C" {
@@ -245,6 +453,8 @@ trk_status trk_batch_create(trk_session* const* sessions, int32_t n_sessions, tr
 
 trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, void* cuda_stream) {
   if (!b || !d_depths) return set_error(TRK_ERR_INVALID_ARG, "trk_batch_track_device: NULL argument");
+  if (!members_current(b))
+    return set_error(TRK_ERR_INVALID_ARG, "trk_batch_track_device: a member was evicted since the batch was built");
   const int B = (int)b->sessions.size();
   for (int k = 0; k < B; ++k)
     if (!d_depths[k]) return set_error(TRK_ERR_INVALID_ARG, "trk_batch_track_device: NULL depth pointer");
@@ -267,6 +477,8 @@ trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, vo
 
 trk_status trk_batch_profile(trk_batch* b, const float* const* d_depths, int32_t reps, size_t flush_bytes, float* ms) {
   if (!b || !d_depths || !ms || reps <= 0) return set_error(TRK_ERR_INVALID_ARG, "trk_batch_profile: bad arguments");
+  if (!members_current(b))
+    return set_error(TRK_ERR_INVALID_ARG, "trk_batch_profile: a member was evicted since the batch was built");
   const int B = (int)b->sessions.size();
   const int L = b->max_links;
   cudaStream_t st = b->cap;

@@ -25,6 +25,7 @@
 namespace trk {
 const Dev& session_dev(const trk_session* s);
 const trk_params& session_params(const trk_session* s);
+void session_forget_stream(trk_session* s, cudaStream_t st);
 trk_status batch_create(trk_session* const* sessions, int n, int assoc_blocks, int tail_blocks, trk_batch** out);
 }  // namespace trk
 
@@ -52,6 +53,10 @@ void release(trk_schedule* s) {
   for (trk_batch* b : s->batches)
     if (b) trk_batch_destroy(b);
   s->batches.clear();
+  for (cudaStream_t st : s->streams) {  // the members' frames there end before the streams go
+    cudaStreamSynchronize(st);
+    for (trk_session* m : s->sessions) session_forget_stream(m, st);
+  }
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   s->streams.clear();
   for (cudaEvent_t e : s->done) cudaEventDestroy(e);

@@ -116,6 +116,17 @@ int trk::set_error_code(int st, const char* msg) {
   return st;
 }
 
+// Model data a session keeps on the host, so that its device state can be freed (evicted) and made
+// again (restored) without the caller's arrays.
+struct HostModel {
+  LinkTable lt{};
+  std::vector<float4> v0, bw;
+  std::vector<uchar4> bidx;
+  std::vector<int4> tris, nb;
+  std::vector<int> csr_off, csr_face, adj_off, adj;
+  std::vector<double> prior2;
+};
+
 struct trk_session {
   Dev d{};
   int device = 0;
@@ -125,34 +136,46 @@ struct trk_session {
   cudaGraphExec_t graph_pose = nullptr;  // a frame of pose iterations only (shape-match after frame 0, smooth-bind)
   int frames_done = 0;                   // frames since the last trk_set_pose
   trk_params prm{};
-  std::vector<void*> allocs;
-  size_t device_bytes = 0;
+  HostModel hm;
+  bool resident = false;    // the device state exists
+  unsigned generation = 0;  // changes whenever the device state is made or freed
+  void* arena = nullptr;    // one stream-ordered allocation holding every device buffer of the session
+  size_t carved = 0;        // bytes of the arena handed out so far (or, without an arena, counted)
+  size_t device_bytes = 0;  // size of the arena
+  // the tracking state while the session is evicted: Theta, lambda, Phi
+  std::vector<double> ev_theta;
+  double ev_lam = 0.0;
+  std::vector<float4> ev_phi;
   double* h_pinned = nullptr;  // pinned staging for results
   float4* h_phi = nullptr;     // pinned staging for the offsets of a result [V]
   float* d_render = nullptr;
-  int phi_cur = 0;
 };
 
 namespace {
 
+trk_status materialize(trk_session* s);
+trk_status evict(trk_session* s);
+
+// Hands out the next piece of the session's arena (256-byte aligned).  Without an arena it only
+// counts, and the pointer is NULL: carve_all() run that way gives the arena's size.
 template <typename T>
-trk_status dalloc(trk_session* s, T** p, size_t count) {
-  void* q = nullptr;
+void carve(trk_session* s, T** p, size_t count) {
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&q, bytes);
-  if (e != cudaSuccess)
-    return fail(e == cudaErrorMemoryAllocation ? TRK_ERR_OOM : TRK_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
-                cudaGetErrorString(e));
-  s->allocs.push_back(q);
-  s->device_bytes += bytes;
-  *p = static_cast<T*>(q);
-  return TRK_OK;
+  s->carved = (s->carved + 255) & ~size_t(255);
+  *p = s->arena ? reinterpret_cast<T*>(static_cast<char*>(s->arena) + s->carved) : nullptr;
+  s->carved += bytes;
 }
 
 #define TRY(x)                         \
   do {                                 \
     trk_status st_ = (x);              \
     if (st_ != TRK_OK) return st_;     \
+  } while (0)
+
+// Calls that run kernels or read device buffers need the device state.
+#define NEED_RESIDENT(s)                                                                              \
+  do {                                                                                              \
+    if (!(s)->resident) return fail(TRK_ERR_INVALID_ARG, "the session is evicted (trk_session_restore)"); \
   } while (0)
 
 trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsics* c, const trk_params* p) {
@@ -298,9 +321,17 @@ trk_status sync_check(trk_session* s) {
 // ---- helpers of the frame server (server.cu) --------------------------------------------------
 namespace trk {
 size_t session_device_bytes(const trk_session* s) { return s->device_bytes; }
+bool session_resident(const trk_session* s) { return s->resident; }
+unsigned session_generation(const trk_session* s) { return s->generation; }
+trk_status session_evict(trk_session* s) { return evict(s); }
+trk_status session_restore(trk_session* s) { return materialize(s); }
 const Dev& session_dev(const trk_session* s) { return s->d; }
 const trk_params& session_params(const trk_session* s) { return s->prm; }
 void session_set_last_stream(trk_session* s, cudaStream_t st) { s->last_stream = st; }
+// The owner of stream st has waited for it and is about to destroy it: the session's last frame there is done.
+void session_forget_stream(trk_session* s, cudaStream_t st) {
+  if (s->last_stream == st) s->last_stream = nullptr;
+}
 int session_device(const trk_session* s) { return s->device; }
 void session_result_sizes(const trk_session* s, int* n_links, int* n_verts, int* n_energy) {
   *n_links = s->d.L;
@@ -340,22 +371,172 @@ void trk_destroy(trk_session* s) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(s->device);
+  if (s->last_stream && s->last_stream != s->stream) cudaStreamSynchronize(s->last_stream);
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->graph_pose) cudaGraphExecDestroy(s->graph_pose);
-  for (void* p : s->allocs) cudaFree(p);
+  if (s->arena) {
+    cudaFreeAsync(s->arena, s->stream);
+    cudaStreamSynchronize(s->stream);
+  }
   if (s->h_pinned) cudaFreeHost(s->h_pinned);
   if (s->h_phi) cudaFreeHost(s->h_phi);
   if (s->stream) cudaStreamDestroy(s->stream);
   cudaSetDevice(cur);
+  cudaGetLastError();  // the calls above are not checked: leave no error behind for the caller's next call
   delete s;
 }
 
-trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_intrinsics* cam, const trk_params* prm,
-                      trk_session** out) {
+}  // extern "C"
+
+namespace {
+
+// Every device buffer of a session, carved from its arena in a fixed order (or only counted).
+void carve_all(trk_session* s) {
+  Dev& d = s->d;
+  const trk_params& prm = s->prm;
+  const int L = d.L, V = d.V, F = d.F, NP = d.NP;
+  const size_t npx = (size_t)d.cam.W * d.cam.H;
+  s->carved = 0;
+  LinkTable* dlt;
+  float4 *dv0, *dbw;
+  uchar4* dbidx;
+  int4 *dtris, *dnb;
+  int *dcsr_off, *dcsr_face, *dadj_off, *dadj;
+  double* dprior;
+  float* ddepth;
+  carve(s, &dlt, 1);
+  carve(s, &dv0, V); carve(s, &dbw, V); carve(s, &dbidx, V);
+  carve(s, &dtris, F); carve(s, &dnb, V);
+  carve(s, &dcsr_off, V + 1); carve(s, &dcsr_face, (size_t)3 * F);
+  carve(s, &dprior, L);
+  carve(s, &d.phi[0], V); carve(s, &d.phi[1], V);
+  carve(s, &d.theta, L); carve(s, &d.lam, 1);
+  carve(s, &d.energy, std::max(1, prm.pose_iters + prm.shape_iters));
+  carve(s, &d.Hd, L); carve(s, &d.xi, (size_t)8 * L);
+  carve(s, &d.theta_c, (size_t)kCandidates * L); carve(s, &d.Hd_c, (size_t)kCandidates * L);
+  carve(s, &d.xi_c, (size_t)kCandidates * L * 8); carve(s, &d.lm_trials, 8);
+  carve(s, &d.lm_ok, 2 * kCandidates);
+  carve(s, &d.v, V); carve(s, &d.n, V); carve(s, &d.fn, F); carve(s, &d.rec, V);
+  carve(s, &d.head, npx); carve(s, &d.zbuf, npx); carve(s, &d.corr, npx);
+  carve(s, &d.pixrec, npx); carve(s, &d.queue, npx); carve(s, &d.qctl, 4);
+  carve(s, &d.acc, V); carve(s, &d.vispix, V); carve(s, &d.rg, V); carve(s, &d.phi0, V);
+  carve(s, &dadj_off, V + 1); carve(s, &dadj, s->hm.adj.size());
+  d.cg_x = d.cg_r = d.cg_z = d.cg_p = d.cg_ap = nullptr;
+  if (prm.shape_solver == 1) {
+    carve(s, &d.cg_x, V); carve(s, &d.cg_r, V); carve(s, &d.cg_z, V);
+    carve(s, &d.cg_p, V); carve(s, &d.cg_ap, V);
+  }
+  carve(s, &d.cg, 4);
+  carve(s, &ddepth, npx);
+  carve(s, &s->d_render, npx);
+  carve(s, &d.partial, (size_t)d.nblk_rows * NP * NP);
+  carve(s, &d.jtj_rows, (size_t)d.nblk_rows);
+  carve(s, &d.arec, (size_t)d.nblk_jtj * 256 * 4);
+  carve(s, &d.A, (size_t)NP * NP);
+  carve(s, &d.epart, (size_t)std::max(d.nblk_v, 1) * 8);
+  carve(s, &d.counter, 4);
+  carve(s, &d.stats, 4);
+  d.links = dlt; d.v0 = dv0; d.bw = dbw; d.bidx = dbidx; d.tris = dtris; d.nbr = dnb;
+  d.csr_off = dcsr_off; d.csr_face = dcsr_face; d.prior2 = dprior;
+  d.depth = ddepth;
+  d.adj_off = dadj_off;
+  d.adj = dadj;
+}
+
+// Makes the device state: one arena from the stream-ordered allocator, the model data uploaded from the
+// host copy, the work buffers initialised and the tracking state (Theta, lambda, Phi) restored.
+trk_status materialize(trk_session* s) {
+  if (s->resident) return TRK_OK;
+  carve_all(s);  // sizing pass (no arena yet)
+  const size_t bytes = s->carved;
+  cudaError_t e = cudaMallocAsync(&s->arena, bytes, s->stream);
+  if (e != cudaSuccess) {
+    s->arena = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? TRK_ERR_OOM : TRK_ERR_CUDA, "device state of %zu bytes: %s", bytes,
+                cudaGetErrorString(e));
+  }
+  struct Undo {
+    trk_session* s;
+    bool armed = true;
+    ~Undo() {
+      if (!armed) return;
+      cudaFreeAsync(s->arena, s->stream);
+      cudaStreamSynchronize(s->stream);
+      s->arena = nullptr;
+      carve_all(s);
+    }
+  } undo{s};
+  if (reinterpret_cast<uintptr_t>(s->arena) % 256 != 0)
+    return fail(TRK_ERR_CUDA, "device state allocation not 256-byte aligned");
+  s->device_bytes = bytes;
+  carve_all(s);
+  Dev& d = s->d;
+  const HostModel& hm = s->hm;
+  const int L = d.L, V = d.V, F = d.F;
+  const size_t npx = (size_t)d.cam.W * d.cam.H;
+  const int ne = std::max(1, s->prm.pose_iters + s->prm.shape_iters);
+  cudaStream_t st = s->stream;
+  CK(cudaMemcpyAsync(const_cast<LinkTable*>(d.links), &hm.lt, sizeof(LinkTable), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<float4*>(d.v0), hm.v0.data(), sizeof(float4) * V, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<float4*>(d.bw), hm.bw.data(), sizeof(float4) * V, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<uchar4*>(d.bidx), hm.bidx.data(), sizeof(uchar4) * V, cudaMemcpyHostToDevice, st));
+  if (F) CK(cudaMemcpyAsync(const_cast<int4*>(d.tris), hm.tris.data(), sizeof(int4) * F, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<int4*>(d.nbr), hm.nb.data(), sizeof(int4) * V, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<int*>(d.csr_off), hm.csr_off.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, st));
+  if (F) CK(cudaMemcpyAsync(const_cast<int*>(d.csr_face), hm.csr_face.data(), sizeof(int) * 3 * F, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<double*>(d.prior2), hm.prior2.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<int*>(d.adj_off), hm.adj_off.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(const_cast<int*>(d.adj), hm.adj.data(), sizeof(int) * hm.adj.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(d.cg, 0, sizeof(double) * 4, st));
+  CK(cudaMemsetAsync(d.counter, 0, sizeof(unsigned) * 4, st));
+  CK(cudaMemsetAsync(d.qctl, 0, sizeof(unsigned) * 4, st));
+  CK(cudaMemsetAsync(d.stats, 0, sizeof(int) * 4, st));
+  CK(cudaMemsetAsync(d.energy, 0, sizeof(double) * ne, st));
+  CK(cudaMemsetAsync(d.lm_trials, 0, sizeof(double) * 8, st));
+  CK(cudaMemsetAsync(const_cast<float*>(d.depth), 0, sizeof(float) * npx, st));
+  // the tracking state
+  CK(cudaMemcpyAsync(d.theta, s->ev_theta.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d.lam, &s->ev_lam, sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d.phi[0], s->ev_phi.data(), sizeof(float4) * V, cudaMemcpyHostToDevice, st));
+  launch_fk(d, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  undo.armed = false;
+  s->resident = true;
+  s->last_stream = nullptr;
+  ++s->generation;
+  return TRK_OK;
+}
+
+// Frees the device state after saving the tracking state on the host (frame graphs go with it).
+trk_status evict(trk_session* s) {
+  if (!s->resident) return TRK_OK;
+  const Dev& d = s->d;
+  if (s->last_stream && s->last_stream != s->stream) CK(cudaStreamSynchronize(s->last_stream));
+  CK(cudaMemcpyAsync(s->ev_theta.data(), d.theta, sizeof(double) * d.L, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(&s->ev_lam, d.lam, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->ev_phi.data(), d.phi[0], sizeof(float4) * d.V, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  if (s->graph_pose) cudaGraphExecDestroy(s->graph_pose);
+  s->graph = s->graph_pose = nullptr;
+  CK(cudaFreeAsync(s->arena, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->arena = nullptr;
+  carve_all(s);  // every device pointer back to NULL
+  s->resident = false;
+  s->last_stream = nullptr;
+  ++s->generation;
+  return TRK_OK;
+}
+
+trk_status create_session(const trk_mesh* mesh, const trk_skeleton* sk, const trk_intrinsics* cam,
+                          const trk_params* prm, bool resident, trk_session** out) {
   g_err.clear();
   if (!out) return fail(TRK_ERR_INVALID_ARG, "out is NULL");
   TRY(validate(mesh, sk, cam, prm));
+  cudaGetLastError();  // an error an earlier unchecked call left on this thread is not this call's
   trk_session* s = new trk_session();
   struct Guard {
     trk_session*& s;
@@ -516,9 +697,14 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
     nb[i] = make_int4(nbr[4 * i], nbr[4 * i + 1], nbr[4 * i + 2], nbr[4 * i + 3]);
   }
   for (int f = 0; f < F; ++f) tris[f] = make_int4(mesh->tris[3 * f], mesh->tris[3 * f + 1], mesh->tris[3 * f + 2], 0);
-  // ---- device allocation ------------------------------------------------------------------------
-  const int NP = L + 1;
-  const size_t npx = (size_t)W * H;
+  HostModel& hm = s->hm;
+  hm.lt = lt;
+  hm.v0 = std::move(v0); hm.bw = std::move(bw); hm.bidx = std::move(bidx);
+  hm.tris = std::move(tris); hm.nb = std::move(nb);
+  hm.csr_off = std::move(csr_off); hm.csr_face = std::move(csr_face);
+  hm.adj_off = std::move(adj_off); hm.adj = std::move(adj);
+  hm.prior2 = std::move(prior2);
+  // ---- [J r] block grouping ---------------------------------------------------------------------
   d.nblk_jtj = (V + 255) / 256;
   d.jtj_group = prm->jtj_group;
   if (d.jtj_group == 0 && prm->precision != TRK_PRECISION_FP32) d.jtj_group = 1;
@@ -547,78 +733,46 @@ trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_in
   }
   d.nblk_rows = (d.nblk_jtj + d.jtj_group - 1) / d.jtj_group;
   d.nblk_v = (V + 255) / 256;
-  LinkTable* dlt;
-  float4 *dv0, *dbw, *phi0buf, *phi1buf;
-  uchar4* dbidx;
-  int4 *dtris, *dnb;
-  int *dcsr_off, *dcsr_face;
-  double* dprior;
-  TRY(dalloc(s, &dlt, 1));
-  TRY(dalloc(s, &dv0, V)); TRY(dalloc(s, &dbw, V)); TRY(dalloc(s, &dbidx, V));
-  TRY(dalloc(s, &dtris, F)); TRY(dalloc(s, &dnb, V));
-  TRY(dalloc(s, &dcsr_off, V + 1)); TRY(dalloc(s, &dcsr_face, (size_t)3 * F));
-  TRY(dalloc(s, &dprior, L));
-  TRY(dalloc(s, &phi0buf, V)); TRY(dalloc(s, &phi1buf, V));
-  TRY(dalloc(s, &d.theta, L)); TRY(dalloc(s, &d.lam, 1));
-  TRY(dalloc(s, &d.energy, std::max(1, prm->pose_iters + prm->shape_iters)));
-  TRY(dalloc(s, &d.Hd, L)); TRY(dalloc(s, &d.xi, (size_t)8 * L));
-  TRY(dalloc(s, &d.theta_c, (size_t)kCandidates * L)); TRY(dalloc(s, &d.Hd_c, (size_t)kCandidates * L));
-  TRY(dalloc(s, &d.xi_c, (size_t)kCandidates * L * 8)); TRY(dalloc(s, &d.lm_trials, 8));
-  TRY(dalloc(s, &d.lm_ok, 2 * kCandidates));
-  TRY(dalloc(s, &d.v, V)); TRY(dalloc(s, &d.n, V)); TRY(dalloc(s, &d.fn, F)); TRY(dalloc(s, &d.rec, V));
-  TRY(dalloc(s, &d.head, npx)); TRY(dalloc(s, &d.zbuf, npx)); TRY(dalloc(s, &d.corr, npx));
-  TRY(dalloc(s, &d.pixrec, npx)); TRY(dalloc(s, &d.queue, npx)); TRY(dalloc(s, &d.qctl, 4));
-  TRY(dalloc(s, &d.acc, V)); TRY(dalloc(s, &d.vispix, V)); TRY(dalloc(s, &d.rg, V)); TRY(dalloc(s, &d.phi0, V));
-  int *dadj_off, *dadj;
-  TRY(dalloc(s, &dadj_off, V + 1)); TRY(dalloc(s, &dadj, adj.size()));
-  if (prm->shape_solver == 1) {
-    TRY(dalloc(s, &d.cg_x, V)); TRY(dalloc(s, &d.cg_r, V)); TRY(dalloc(s, &d.cg_z, V));
-    TRY(dalloc(s, &d.cg_p, V)); TRY(dalloc(s, &d.cg_ap, V));
-  }
-  TRY(dalloc(s, &d.cg, 4));
-  float* ddepth;
-  TRY(dalloc(s, &ddepth, npx));
-  TRY(dalloc(s, &s->d_render, npx));
-  TRY(dalloc(s, &d.partial, (size_t)d.nblk_rows * NP * NP));
-  TRY(dalloc(s, &d.jtj_rows, (size_t)d.nblk_rows));
-  TRY(dalloc(s, &d.arec, (size_t)d.nblk_jtj * 256 * 4));
-  TRY(dalloc(s, &d.A, (size_t)NP * NP));
-  TRY(dalloc(s, &d.epart, (size_t)std::max(d.nblk_v, 1) * 8));
-  TRY(dalloc(s, &d.counter, 4));
-  TRY(dalloc(s, &d.stats, 4));
-  d.links = dlt; d.v0 = dv0; d.bw = dbw; d.bidx = dbidx; d.tris = dtris; d.nbr = dnb;
-  d.csr_off = dcsr_off; d.csr_face = dcsr_face; d.prior2 = dprior; d.phi[0] = phi0buf; d.phi[1] = phi1buf;
-  d.depth = ddepth;
-  d.adj_off = dadj_off;
-  d.adj = dadj;
+  carve_all(s);
+  s->device_bytes = s->carved;
   CK(cudaMallocHost(&s->h_pinned, sizeof(double) * (L + prm->pose_iters + prm->shape_iters + 4)));
   CK(cudaMallocHost(&s->h_phi, sizeof(float4) * std::max(V, 1)));
-  cudaStream_t st = s->stream;
-  CK(cudaMemcpyAsync(dlt, &lt, sizeof(lt), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dv0, v0.data(), sizeof(float4) * V, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dbw, bw.data(), sizeof(float4) * V, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dbidx, bidx.data(), sizeof(uchar4) * V, cudaMemcpyHostToDevice, st));
-  if (F) CK(cudaMemcpyAsync(dtris, tris.data(), sizeof(int4) * F, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dnb, nb.data(), sizeof(int4) * V, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dcsr_off, csr_off.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, st));
-  if (F) CK(cudaMemcpyAsync(dcsr_face, csr_face.data(), sizeof(int) * 3 * F, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dprior, prior2.data(), sizeof(double) * L, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dadj_off, adj_off.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(dadj, adj.data(), sizeof(int) * adj.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(d.cg, 0, sizeof(double) * 4, st));
-  CK(cudaMemsetAsync(d.counter, 0, sizeof(unsigned) * 4, st));
-  CK(cudaMemsetAsync(d.qctl, 0, sizeof(unsigned) * 4, st));
-  CK(cudaMemsetAsync(d.stats, 0, sizeof(int) * 4, st));
-  CK(cudaMemsetAsync(d.energy, 0, sizeof(double) * std::max(1, prm->pose_iters + prm->shape_iters), st));
-  CK(cudaMemsetAsync(d.lm_trials, 0, sizeof(double) * 8, st));
-  CK(cudaMemsetAsync(ddepth, 0, sizeof(float) * npx, st));
-  CK(cudaStreamSynchronize(st));
-  std::vector<double> zero(L, 0.0);
-  TRY(trk_set_pose(s, zero.data(), nullptr));
+  // the state of trk_set_pose(Theta = 0, Phi = 0)
+  s->ev_theta.assign(L, 0.0);
+  s->ev_lam = prm->lambda_k0;
+  s->ev_phi.assign(V, make_float4(0.f, 0.f, 0.f, 0.f));
+  s->frames_done = 0;
+  if (resident) TRY(materialize(s));
   *out = s;
   s = nullptr;  // disarm the guard
   return TRK_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+trk_status trk_create(const trk_mesh* mesh, const trk_skeleton* sk, const trk_intrinsics* cam, const trk_params* prm,
+                      trk_session** out) {
+  return create_session(mesh, sk, cam, prm, true, out);
+}
+
+trk_status trk_create_evicted(const trk_mesh* mesh, const trk_skeleton* sk, const trk_intrinsics* cam,
+                              const trk_params* prm, trk_session** out) {
+  return create_session(mesh, sk, cam, prm, false, out);
+}
+
+trk_status trk_session_evict(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  return evict(s);
+}
+
+trk_status trk_session_restore(trk_session* s) {
+  if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  return materialize(s);
+}
+
+int32_t trk_session_is_resident(const trk_session* s) { return s && s->resident ? 1 : 0; }
 
 trk_status trk_fk_joint_positions(const trk_skeleton* sk, const double* theta, double* out) {
   if (!sk || !theta || !out || sk->n_links < 1 || sk->n_links > TRK_MAX_LINKS || !sk->parent || !sk->type ||
@@ -668,6 +822,12 @@ trk_status trk_set_pose(trk_session* s, const double* theta, const float* offset
       phi[i] = make_float4(offsets[3 * i], offsets[3 * i + 1], offsets[3 * i + 2], 0.f);
     }
   const double lam = s->prm.lambda_k0;
+  if (!s->resident) {  // the state waits on the host until the session is restored
+    s->ev_theta.assign(theta, theta + d.L);
+    s->ev_phi = phi;
+    s->ev_lam = lam;
+    return TRK_OK;
+  }
   CK(cudaMemcpyAsync(d.theta, theta, sizeof(double) * d.L, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(d.phi[0], phi.data(), sizeof(float4) * d.V, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(d.lam, &lam, sizeof(double), cudaMemcpyHostToDevice, s->stream));
@@ -707,12 +867,20 @@ trk_status trk_session_export(trk_session* s, void* blob, size_t* size_bytes) {
   unsigned char* p = static_cast<unsigned char*>(blob);
   std::memcpy(p, &h, sizeof(h));
   p += sizeof(h);
+  if (!s->resident) {
+    std::memcpy(p, s->ev_theta.data(), sizeof(double) * d.L);
+    std::memcpy(p + sizeof(double) * d.L, &s->ev_lam, sizeof(double));
+    std::memcpy(p + sizeof(double) * (d.L + 1), s->ev_phi.data(), sizeof(float4) * d.V);
+    *size_bytes = need;
+    return TRK_OK;
+  }
   // on the stream of the last frame, so that the copies follow it
   cudaStream_t st = s->last_stream ? s->last_stream : s->stream;
   CK(cudaMemcpyAsync(p, d.theta, sizeof(double) * d.L, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(p + sizeof(double) * d.L, d.lam, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(p + sizeof(double) * (d.L + 1), d.phi[0], sizeof(float4) * d.V, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  s->last_stream = nullptr;
   *size_bytes = need;
   return TRK_OK;
 }
@@ -742,7 +910,15 @@ trk_status trk_session_import(trk_session* s, const void* blob, size_t size_byte
   for (int i = 0; i < d.V; ++i)
     if (!std::isfinite(phi[i].x) || !std::isfinite(phi[i].y) || !std::isfinite(phi[i].z))
       return fail(TRK_ERR_NUMERIC, "checkpoint offset %d not finite", i);
+  if (!s->resident) {
+    s->ev_theta.assign(th.begin(), th.begin() + d.L);
+    s->ev_lam = th[d.L];
+    s->ev_phi = phi;
+    s->frames_done = h.frames_done;
+    return TRK_OK;
+  }
   if (s->last_stream) CK(cudaStreamSynchronize(s->last_stream));  // the last frame still reads the state
+  s->last_stream = nullptr;
   CK(cudaMemcpyAsync(d.theta, th.data(), sizeof(double) * d.L, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(d.lam, th.data() + d.L, sizeof(double), cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(d.phi[0], phi.data(), sizeof(float4) * d.V, cudaMemcpyHostToDevice, s->stream));
@@ -753,6 +929,7 @@ trk_status trk_session_import(trk_session* s, const void* blob, size_t size_byte
 
 trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out) {
   if (!s || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  NEED_RESIDENT(s);
   cudaGraphExec_t ge;
   TRY(frame_graph(s, &ge));
   const Dev& d = s->d;
@@ -767,6 +944,7 @@ trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out
 
 trk_status trk_track_frame_device(trk_session* s, const float* d_depth_m, void* cuda_stream) {
   if (!s || !d_depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  NEED_RESIDENT(s);
   cudaGraphExec_t ge;
   TRY(frame_graph(s, &ge));
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : s->stream;
@@ -782,14 +960,17 @@ trk_status trk_track_frame_device(trk_session* s, const float* d_depth_m, void* 
 
 trk_status trk_read_result(trk_session* s, trk_result* out) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  NEED_RESIDENT(s);
   cudaStream_t st = s->last_stream ? s->last_stream : s->stream;
   TRY(fetch_result(s, st, out));
   CK(cudaGetLastError());
+  s->last_stream = nullptr;  // the frame is done: nothing left to wait for on that stream
   return TRK_OK;
 }
 
 trk_status trk_render_depth(trk_session* s, const double* theta, const float* offsets, float* depth_m) {
   if (!s || !theta || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  NEED_RESIDENT(s);
   Dev r = s->d;  // scratch view: FK tables and offsets in candidate / sweep buffers, state untouched
   r.theta = s->d.theta_c;
   r.Hd = s->d.Hd_c;
@@ -810,6 +991,7 @@ trk_status trk_render_depth(trk_session* s, const double* theta, const float* of
 
 trk_status trk_set_depth(trk_session* s, const float* depth_m) {
   if (!s || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  NEED_RESIDENT(s);
   CK(cudaMemcpyAsync(const_cast<float*>(s->d.depth), depth_m, sizeof(float) * s->d.cam.W * s->d.cam.H,
                      cudaMemcpyHostToDevice, s->stream));
   return sync_check(s);
@@ -817,17 +999,20 @@ trk_status trk_set_depth(trk_session* s, const float* depth_m) {
 
 trk_status trk_step_skin(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  NEED_RESIDENT(s);
   launch_fk(s->d, s->stream);
   launch_skin(s->d, 0, s->stream);
   return sync_check(s);
 }
 trk_status trk_step_raster(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  NEED_RESIDENT(s);
   launch_raster(s->d, s->stream);
   return sync_check(s);
 }
 trk_status trk_step_visibility(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  NEED_RESIDENT(s);
   // empty buckets first, so that calling this step twice cannot insert a vertex twice
   CK(cudaMemsetAsync(s->d.head, 0xFF, sizeof(int) * s->d.cam.W * s->d.cam.H, s->stream));
   launch_visibility(s->d, s->stream);
@@ -835,22 +1020,26 @@ trk_status trk_step_visibility(trk_session* s) {
 }
 trk_status trk_step_associate(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  NEED_RESIDENT(s);
   CK(cudaMemsetAsync(s->d.qctl, 0, sizeof(unsigned) * 2, s->stream));
   launch_associate(s->d, s->stream);
   return sync_check(s);
 }
 trk_status trk_step_normal_equations(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  NEED_RESIDENT(s);
   launch_normal_equations(s->d, 0, 0, s->stream);
   return sync_check(s);
 }
 trk_status trk_step_lm(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  NEED_RESIDENT(s);
   launch_lm(s->d, 0, s->stream);
   return sync_check(s);
 }
 trk_status trk_step_shape(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
+  NEED_RESIDENT(s);
   const int cur = launch_shape(s->d, 0, s->prm.pose_iters, s->stream);
   if (cur != 0)
     CK(cudaMemcpyAsync(s->d.phi[0], s->d.phi[cur], sizeof(float4) * s->d.V, cudaMemcpyDeviceToDevice, s->stream));
@@ -859,6 +1048,7 @@ trk_status trk_step_shape(trk_session* s) {
 
 trk_status trk_read(trk_session* s, trk_field field, void* dst, size_t bytes) {
   if (!s || !dst) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
+  NEED_RESIDENT(s);
   const Dev& d = s->d;
   const size_t V = d.V, npx = (size_t)d.cam.W * d.cam.H, L = d.L, NP = d.NP;
   const void* src = nullptr;
@@ -914,6 +1104,7 @@ trk_status trk_get_info(trk_session* s, trk_info* out) {
 
 trk_status trk_profile_iteration(trk_session* s, int32_t reps, size_t flush_bytes, float* ms) {
   if (!s || !ms || reps <= 0) return fail(TRK_ERR_INVALID_ARG, "bad argument");
+  NEED_RESIDENT(s);
   const Dev& d = s->d;
   cudaStream_t st = s->stream;
   cudaEvent_t e0, e1;

@@ -12,6 +12,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/trk.h"
+
 namespace trk {
 
 constexpr int kMaxLinks = 79;       // NP = P + 1 <= 80
@@ -339,6 +341,22 @@ struct BatchGrid {
   const Dev* devs;
   const int4* map;
 };
+
+// Where a batched step writes one session's results (device-accessible, e.g. host-mapped pinned memory).
+struct ResultDst {
+  double* theta;   // [L]
+  float4* phi;     // [V] (x, y, z, 0)
+  double* energy;  // [pose_iters + shape_iters]
+  int* stats;      // [4]
+};
+struct BatchStep;
+BatchStep* batch_step_create();
+void batch_step_destroy(BatchStep* bs, cudaStream_t st);
+// One frame of the n sessions (resident, same schedule, precision and mode TRACK) as one launch per
+// stage on st: session k reads its depth from srcs[k] and its results go to dst[k] (both device-
+// accessible host pointers are fine).  The step's buffers may be reused once the stream passed it.
+trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const float* const* srcs,
+                             const ResultDst* dst, cudaStream_t st);
 
 // Every stage kernel serves one session (g.map == nullptr: the descriptor is the kernel parameter and the
 // block's position its blockIdx) and batches (descriptor and position from the tables, the descriptor

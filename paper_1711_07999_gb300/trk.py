@@ -17,12 +17,14 @@ TRK_OK, TRK_ERR_INVALID_ARG, TRK_ERR_OOM, TRK_ERR_CUDA, TRK_ERR_NO_CAPACITY, TRK
 MAX_LINKS = 79
 PRECISION_FP32, PRECISION_BF16X3, PRECISION_TF32X3 = 0, 1, 2
 MODE_TRACK, MODE_SHAPE_MATCH, MODE_SMOOTH_BIND = 0, 1, 2
+SERVER_DISPATCH_BATCHED, SERVER_DISPATCH_SESSION = 0, 1
 
 FIELDS = dict(VERTS=0, NORMALS=1, ZBUF=2, VISPIX=3, CORR=4, ACC=5, NORMAL_EQ=6, THETA=7, PHI=8, LAMBDA=9, ENERGY=10,
               LM_TRIALS=11, SHAPE_RG=12, NEIGHBOURS=13, PRIOR=14, LM_SOLVER=15)
 
 # symbols include/trk.h declares (checked by the tests against the library's exports)
-EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_device", "trk_read_result",
+EXPORTS = ["trk_create", "trk_create_evicted", "trk_session_evict", "trk_session_restore", "trk_session_is_resident",
+           "trk_set_pose", "trk_track_frame", "trk_track_frame_device", "trk_read_result",
            "trk_render_depth", "trk_session_export", "trk_session_import", "trk_destroy", "trk_last_error",
            "trk_set_depth", "trk_step_skin", "trk_step_raster",
            "trk_step_visibility", "trk_step_associate", "trk_step_normal_equations", "trk_step_lm", "trk_step_shape",
@@ -32,7 +34,7 @@ EXPORTS = ["trk_create", "trk_set_pose", "trk_track_frame", "trk_track_frame_dev
            "trk_batch_destroy",
            "trk_schedule_create", "trk_schedule_track_device", "trk_schedule_get_config", "trk_schedule_autotune",
            "trk_schedule_destroy", "trk_schedule_signature", "trk_tuning_cache_lookup", "trk_tuning_cache_store",
-           "trk_server_create", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
+           "trk_server_create", "trk_server_configure", "trk_server_attach", "trk_server_detach", "trk_server_submit", "trk_server_wait",
            "trk_server_get_stats", "trk_server_destroy"]
 
 STAGES = ["skin", "raster", "visibility", "associate", "resid_jtj", "reduce", "lm_solve", "lm_eval", "shape"]
@@ -81,7 +83,7 @@ class ScheduleConfig(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("frames_done", C.c_uint64), ("in_flight", C.c_int32), ("sessions", C.c_int32),
                 ("hbm_used_bytes", C.c_size_t), ("latency_p50_us", C.c_double), ("latency_p99_us", C.c_double),
-                ("latency_max_us", C.c_double)]
+                ("latency_max_us", C.c_double), ("steps", C.c_uint64), ("mean_frames_per_step", C.c_double)]
 
 
 class Result(C.Structure):
@@ -103,7 +105,9 @@ def lib(build_if_missing: bool = True):
         L = C.CDLL(LIB_PATH)
         vp, i32, sz = C.c_void_p, C.c_int32, C.c_size_t
         sigs = {
-            "trk_create": [vp, vp, vp, vp, C.POINTER(vp)], "trk_set_pose": [vp, vp, vp],
+            "trk_create": [vp, vp, vp, vp, C.POINTER(vp)], "trk_create_evicted": [vp, vp, vp, vp, C.POINTER(vp)],
+            "trk_session_evict": [vp], "trk_session_restore": [vp], "trk_session_is_resident": [vp],
+            "trk_set_pose": [vp, vp, vp],
             "trk_track_frame": [vp, vp, vp], "trk_track_frame_device": [vp, vp, vp], "trk_read_result": [vp, vp],
             "trk_render_depth": [vp, vp, vp, vp], "trk_session_export": [vp, vp, C.POINTER(sz)],
             "trk_session_import": [vp, vp, sz], "trk_set_depth": [vp, vp], "trk_step_skin": [vp],
@@ -123,7 +127,8 @@ def lib(build_if_missing: bool = True):
             "trk_schedule_signature": [C.POINTER(vp), i32, C.c_char_p, sz],
             "trk_tuning_cache_lookup": [C.c_char_p, C.c_char_p, vp, C.POINTER(C.c_double)],
             "trk_tuning_cache_store": [C.c_char_p, C.c_char_p, vp, C.c_double],
-            "trk_server_create": [sz, i32, C.POINTER(vp)], "trk_server_attach": [vp, vp], "trk_server_detach": [vp, vp],
+            "trk_server_create": [sz, i32, C.POINTER(vp)], "trk_server_configure": [vp, i32, i32, i32],
+            "trk_server_attach": [vp, vp], "trk_server_detach": [vp, vp],
             "trk_server_submit": [vp, vp, vp, C.POINTER(C.c_uint64)], "trk_server_wait": [vp, C.c_uint64, C.c_int64, vp],
             "trk_server_get_stats": [vp, vp],
         }
@@ -232,7 +237,9 @@ def params_struct(p: dict) -> Params:
 class Session:
     """One tracking session (trk_create ... trk_destroy) for a model dict of ``synth.make_model`` form."""
 
-    def __init__(self, model: dict):
+    def __init__(self, model: dict, evicted: bool = False):
+        """trk_create (device state allocated), or trk_create_evicted with evicted=True (no device memory
+        until restore() or a server's attach)."""
         sk, me, cam, pr = model["skeleton"], model["mesh"], model["camera"], model["params"]
         self._keep = k = dict(
             parent=np.ascontiguousarray(sk["parent"], np.int32), type=np.ascontiguousarray(sk["type"], np.int32),
@@ -248,7 +255,8 @@ class Session:
         intr = Intrinsics(self.W, self.H, cam["fx"], cam["fy"], cam["cx"], cam["cy"])
         prm = params_struct(pr)
         h = C.c_void_p()
-        _check(lib().trk_create(C.byref(mesh), C.byref(skel), C.byref(intr), C.byref(prm), C.byref(h)))
+        create = lib().trk_create_evicted if evicted else lib().trk_create
+        _check(create(C.byref(mesh), C.byref(skel), C.byref(intr), C.byref(prm), C.byref(h)))
         self.h = h
         self.n_energy = pr["pose_iters"] + pr["shape_iters"]
 
@@ -265,6 +273,19 @@ class Session:
 
     def __exit__(self, *a):
         self.close()
+
+    # -- device residency -------------------------------------------------------------------------
+    def evict(self):
+        """trk_session_evict: tracking state to the host, device state freed."""
+        _check(lib().trk_session_evict(self.h))
+
+    def restore(self):
+        """trk_session_restore: device state allocated again, tracking state restored."""
+        _check(lib().trk_session_restore(self.h))
+
+    @property
+    def resident(self) -> bool:
+        return bool(lib().trk_session_is_resident(self.h))
 
     # -- state / frames ---------------------------------------------------------------------------
     def set_pose(self, theta, offsets=None):
@@ -466,11 +487,13 @@ class Schedule:
 class Server:
     """Continuous-batching frame server (trk_server_*) over attached sessions."""
 
-    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 32):
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 32, dispatch: int = SERVER_DISPATCH_BATCHED,
+                 max_batch: int = 64, concurrent_steps: int = 2):
         h = C.c_void_p()
         _check(lib().trk_server_create(hbm_budget_bytes, max_inflight, C.byref(h)))
         self.h = h
         self._sessions = {}
+        _check(lib().trk_server_configure(self.h, dispatch, max_batch, concurrent_steps))
 
     def attach(self, session: Session):
         _check(lib().trk_server_attach(self.h, session.h))
