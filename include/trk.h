@@ -320,9 +320,13 @@ typedef struct {
  * previous frame is done and a slot is free (see TRK_SERVER_DISPATCH_*), so frames of different
  * sessions overlap on the device and one session's frames run in submission order. */
 trk_status trk_server_create(size_t hbm_budget_bytes, int32_t max_inflight, trk_server** out);
-/* Dispatch mode, the most frames in one batched step (1..4096, default 64) and the number of batched
- * steps that may run at once (1..16, default 2, each on its own stream).  Only before the first attach. */
-trk_status trk_server_configure(trk_server* sv, int32_t dispatch, int32_t max_batch, int32_t concurrent_steps);
+/* Dispatch mode, the most frames in one batched step (1..4096, default 64), the number of batched steps
+ * that may run at once (1..16, default 2, each on its own stream) and max_wait_us (default 2000): while
+ * a batched step runs, ready frames wait for a fuller step until they are (compatible sessions /
+ * concurrent_steps) or the oldest has waited max_wait_us; with no step running they go at once.  Only
+ * before the first attach. */
+trk_status trk_server_configure(trk_server* sv, int32_t dispatch, int32_t max_batch, int32_t concurrent_steps,
+                                int64_t max_wait_us);
 /* Admits a session (same device).  TRK_ERR_NO_CAPACITY if its device bytes do not fit the remaining
  * budget.  An evicted session (trk_create_evicted, trk_session_evict) is restored here -- its device
  * state is allocated at admission -- and evicted again at trk_server_detach, so the budget bounds the

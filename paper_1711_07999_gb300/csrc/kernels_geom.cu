@@ -50,6 +50,7 @@ __device__ __forceinline__ void skin_impl(const Dev& d, BlockPos bp, int phi_buf
     d.stats[1] = 0;
     d.qctl[0] = 0;
     d.qctl[1] = 0;
+    d.qctl[3] = 0;  // the association's next tile (the tile list itself is the frame's)
   }
   const float4* phi = d.phi[phi_buf];
   for (int i = tid; i < d.V; i += stride) {
@@ -336,20 +337,23 @@ __device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
   } else if (dep > 0.f) {
     p = back_project(c, px, py, dep);
     open = true;
-    for (int r = 0; r <= min(c.R, kRingsPerThread); ++r) {
-      if (r == 0) {
-        const int q0[1] = {k};
-        scan_group<1>(d, q0, p, tau2, best, bd2);
-      } else {
-        for (int t0 = 0; t0 < 8 * r; t0 += 4) {  // 4 buckets in flight: 64 registers, 4 blocks per SM
-          int q[4];
+    if (c.R == 0) {
+      const int q0[1] = {k};
+      scan_group<1>(d, q0, p, tau2, best, bd2);
+      open = false;
+    } else {
+      // rings 0 and 1 (9 buckets) in two rounds of independent loads: the pixel's own bucket with the
+      // first four of ring 1, then the other four; the ring-1 bound decides whether the search goes on
+      int q[5];
+      q[0] = k;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) q[u] = ring_bucket(px, py, r, t0 + u, c.W, c.H);
-          scan_group<4>(d, q, p, tau2, best, bd2);
-        }
-      }
-      const float lb = dep * ((float)r + 0.499f) * c.kappa;
-      if (lb > c.tau || (best >= 0 && lb * lb > bd2) || r == c.R) { open = false; break; }
+      for (int u = 0; u < 4; ++u) q[1 + u] = ring_bucket(px, py, 1, u, c.W, c.H);
+      scan_group<5>(d, q, p, tau2, best, bd2);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] = ring_bucket(px, py, 1, 4 + u, c.W, c.H);
+      scan_group<4>(d, q, p, tau2, best, bd2);
+      const float lb = dep * (1.0f + 0.499f) * c.kappa;
+      if (lb > c.tau || (best >= 0 && lb * lb > bd2) || c.R == 1) open = false;
     }
   }
   // queue the open pixels (one atomic per warp)
@@ -387,13 +391,19 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
   unsigned long long key = key_of(e.y, __int_as_float(e.z));
   int wb = -1;
   float wd2 = 0.f;
-  for (int r = kRingsPerThread + 1; r <= c.R; ++r) {
-    for (int t0 = 0; t0 < 8 * r; t0 += GL * kTailPerLane) {
+  // rings r0..r1 at a time, as many whole rings as the group's load slots hold (at least one): scanning
+  // rings past the one whose bound ends the search only confirms the argmin, so the result is the same
+  constexpr int kSlots = GL * kTailPerLane;
+  for (int r0 = kRingsPerThread + 1; r0 <= c.R;) {
+    int r1 = r0, nb = 8 * r0;
+    while (r1 < c.R && nb + 8 * (r1 + 1) <= kSlots) nb += 8 * ++r1;
+    for (int t0 = 0; t0 < nb; t0 += kSlots) {
       int q[kTailPerLane];
 #pragma unroll
       for (int u = 0; u < kTailPerLane; ++u) {
-        const int t = t0 + gl + GL * u;
-        q[u] = t < 8 * r ? ring_bucket(px, py, r, t, c.W, c.H) : -1;
+        int t = t0 + gl + GL * u, r = r0;
+        while (t < nb && t >= 8 * r) t -= 8 * r++;  // bucket t of the group: ring r, position t
+        q[u] = t0 + gl + GL * u < nb ? ring_bucket(px, py, r, t, c.W, c.H) : -1;
       }
       scan_group<kTailPerLane>(d, q, p, tau2, wb, wd2);
     }
@@ -405,8 +415,9 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
       kk = other < kk ? other : kk;
     }
     key = kk;
-    const float lb = dep * ((float)r + 0.499f) * c.kappa;
+    const float lb = dep * ((float)r1 + 0.499f) * c.kappa;
     if (lb > c.tau || (key != ~0ull && lb * lb > __uint_as_float((unsigned)(key >> 32)))) break;
+    r0 = r1 + 1;
   }
   const int best = key == ~0ull ? -1 : (int)(unsigned)(key & 0xffffffffu);
   if (gl == 0) {
@@ -420,12 +431,22 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
 // (listed by the depth gather) from a shared counter, reloading the session descriptor when the session
 // changes; pixels of empty tiles keep the "no correspondence" the skinning pass wrote.
 __global__ void __launch_bounds__(kBlock, 4) k_associate(const Dev* devs, const int4* tiles, unsigned* ctl, Dev d0) {
-  if (devs == nullptr) {
-    associate_impl(d0, grid_pos());
-    return;
+  __shared__ int4 s_t;
+  if (devs == nullptr) {  // one session: persistent blocks over the frame's occupied tiles
+    const unsigned n = d0.qctl[2];
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned i = atomicAdd(&d0.qctl[3], 1u);
+        s_t = i < n ? d0.tiles[i] : make_int4(-1, 0, 0, 0);
+      }
+      __syncthreads();
+      const int4 t = s_t;
+      if (t.x < 0) return;
+      associate_impl(d0, BlockPos{t.y, t.z, t.w});
+    }
   }
   __shared__ Dev sd;
-  __shared__ int4 s_t;
   int cur = -1;
   const unsigned n = ctl[0];
   for (;;) {
@@ -514,9 +535,30 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const 
 }
 
 void launch_associate(const Dev& d, cudaStream_t st) {
-  dim3 g((d.cam.W + 15) / 16, (d.cam.H + 15) / 16);
-  k_associate<<<g, kBlock, 0, st>>>(nullptr, nullptr, nullptr, d);
+  const int ntiles = ((d.cam.W + 15) / 16) * ((d.cam.H + 15) / 16);
+  k_associate<<<min(ntiles, 4 * 152), kBlock, 0, st>>>(nullptr, nullptr, nullptr, d);
   k_associate_tail<<<2 * 152, 32 * kTailWarps, 0, st>>>(d);
+}
+
+// One 16 x 16 tile per block: copies the frame's depth into the session's buffer and appends the tile
+// to the list if it holds a valid pixel.
+__global__ void __launch_bounds__(kBlock) k_tiles(Dev d, const float* __restrict__ src) {
+  const int gx = (d.cam.W + 15) / 16;
+  const int tx = blockIdx.x % gx, ty = blockIdx.x / gx;
+  const int px = tx * 16 + (threadIdx.x & 15), py = ty * 16 + (threadIdx.x >> 4);
+  bool valid = false;
+  if (px < d.cam.W && py < d.cam.H) {
+    const int k = py * d.cam.W + px;
+    const float z = src[k];
+    const_cast<float*>(d.depth)[k] = z;
+    valid = z > 0.f;
+  }
+  if (__syncthreads_or(valid) && threadIdx.x == 0) d.tiles[atomicAdd(&d.qctl[2], 1u)] = make_int4(0, tx, ty, gx);
+}
+
+void launch_tiles(const Dev& d, const float* src, cudaStream_t st) {
+  cudaMemsetAsync(d.qctl + 2, 0, sizeof(unsigned), st);
+  k_tiles<<<((d.cam.W + 15) / 16) * ((d.cam.H + 15) / 16), kBlock, 0, st>>>(d, src);
 }
 
 // ---- batched launches (one launch over the blocks of all sessions of a batch) ---------------------

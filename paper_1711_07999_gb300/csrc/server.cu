@@ -128,6 +128,9 @@ struct trk_server {
   int max_inflight = 0, device = 0;
   int dispatch = TRK_SERVER_DISPATCH_BATCHED;
   int max_batch = 64, n_slots = 2;
+  int64_t max_wait_us = 2000;       // longest a ready frame waits for a fuller step while another runs
+  clk::time_point wake{};           // when the dispatcher must look again (a waiting frame's deadline)
+  bool wake_set = false;
   std::mutex mu;                    // sessions, requests, counters (held while launching)
   std::condition_variable cv_done;  // a frame completed
   std::mutex sig_mu;                // finished steps and the work flag (never held across a CUDA call)
@@ -329,6 +332,21 @@ void launch_ready(trk_server* sv) {
     std::vector<trk_session*> take;
     for (const auto& rd : ready)
       if ((int)take.size() < room && sv->sessions[rd.second].key == key) take.push_back(rd.second);
+    // While another step runs, a small step waits for company: it goes once it holds its share of the
+    // attached sessions (sessions / concurrent steps) or its oldest frame has waited max_wait_us; with
+    // no step running it goes at once.  Eager small steps would keep the batches small.
+    int running = 0, batchable = 0;
+    for (Step* s2 : sv->slots) running += s2->busy;
+    for (auto& kv : sv->sessions) batchable += kv.second.batchable && kv.second.key == key;
+    const int share = std::min(room, (batchable + sv->n_slots - 1) / sv->n_slots);
+    const clk::time_point due = ready[0].first + std::chrono::microseconds(sv->max_wait_us);
+    if (running > 0 && (int)take.size() < share && clk::now() < due) {
+      if (!sv->wake_set || due < sv->wake) {
+        sv->wake = due;
+        sv->wake_set = true;
+      }
+      return;
+    }
     launch_batched(sv, slot, take);
   }
 }
@@ -338,9 +356,20 @@ void worker_loop(trk_server* sv) {
   for (;;) {
     std::vector<Step*> fin;
     bool stop = false;
+    clk::time_point wake{};
+    bool timed = false;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      timed = sv->wake_set;
+      wake = sv->wake;
+    }
     {
       std::unique_lock<std::mutex> l(sv->sig_mu);
-      sv->cv_sig.wait(l, [&] { return !sv->finished.empty() || sv->work || sv->stop; });
+      auto pred = [&] { return !sv->finished.empty() || sv->work || sv->stop; };
+      if (timed)
+        sv->cv_sig.wait_until(l, wake, pred);
+      else
+        sv->cv_sig.wait(l, pred);
       fin.swap(sv->finished);
       sv->work = false;
       stop = sv->stop;
@@ -348,6 +377,7 @@ void worker_loop(trk_server* sv) {
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       for (Step* st : fin) complete(sv, st);
+      sv->wake_set = false;
       if (!stop) launch_ready(sv);
     }
     if (!fin.empty()) sv->cv_done.notify_all();
@@ -377,9 +407,10 @@ trk_status trk_server_create(size_t hbm_budget_bytes, int32_t max_inflight, trk_
   return TRK_OK;
 }
 
-trk_status trk_server_configure(trk_server* sv, int32_t dispatch, int32_t max_batch, int32_t concurrent_steps) {
+trk_status trk_server_configure(trk_server* sv, int32_t dispatch, int32_t max_batch, int32_t concurrent_steps,
+                                int64_t max_wait_us) {
   if (!sv || (dispatch != TRK_SERVER_DISPATCH_BATCHED && dispatch != TRK_SERVER_DISPATCH_SESSION) || max_batch < 1 ||
-      max_batch > 4096 || concurrent_steps < 1 || concurrent_steps > 16)
+      max_batch > 4096 || concurrent_steps < 1 || concurrent_steps > 16 || max_wait_us < 0)
     return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_configure: bad arguments");
   std::lock_guard<std::mutex> lk(sv->mu);
   if (!sv->sessions.empty() || !sv->attaching.empty() || !sv->slots.empty())
@@ -387,6 +418,7 @@ trk_status trk_server_configure(trk_server* sv, int32_t dispatch, int32_t max_ba
   sv->dispatch = dispatch;
   sv->max_batch = max_batch;
   sv->n_slots = concurrent_steps;
+  sv->max_wait_us = max_wait_us;
   return TRK_OK;
 }
 

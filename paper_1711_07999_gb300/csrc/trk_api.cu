@@ -344,6 +344,7 @@ trk_status session_enqueue_frame(trk_session* s, const float* host_depth, cudaSt
   TRY(frame_graph(s, &ge));
   CK(cudaMemcpyAsync(const_cast<float*>(s->d.depth), host_depth, sizeof(float) * s->d.cam.W * s->d.cam.H,
                      cudaMemcpyHostToDevice, s->stream));
+  launch_tiles(s->d, s->d.depth, s->stream);  // the frame's occupied tiles (the graph's association reads them)
   CK(cudaGraphLaunch(ge, s->stream));
   ++s->frames_done;
   s->last_stream = s->stream;
@@ -420,6 +421,7 @@ void carve_all(trk_session* s) {
   carve(s, &d.v, V); carve(s, &d.n, V); carve(s, &d.fn, F); carve(s, &d.rec, V);
   carve(s, &d.head, npx); carve(s, &d.zbuf, npx); carve(s, &d.corr, npx);
   carve(s, &d.pixrec, npx); carve(s, &d.queue, npx); carve(s, &d.qctl, 4);
+  carve(s, &d.tiles, (size_t)((d.cam.W + 15) / 16) * ((d.cam.H + 15) / 16));
   carve(s, &d.acc, V); carve(s, &d.vispix, V); carve(s, &d.rg, V); carve(s, &d.phi0, V);
   carve(s, &dadj_off, V + 1); carve(s, &dadj, s->hm.adj.size());
   d.cg_x = d.cg_r = d.cg_z = d.cg_p = d.cg_ap = nullptr;
@@ -935,6 +937,7 @@ trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out
   const Dev& d = s->d;
   CK(cudaMemcpyAsync(const_cast<float*>(d.depth), depth_m, sizeof(float) * d.cam.W * d.cam.H, cudaMemcpyHostToDevice,
                      s->stream));
+  launch_tiles(d, d.depth, s->stream);  // the frame's occupied tiles (the graph's association reads them)
   CK(cudaGraphLaunch(ge, s->stream));
   ++s->frames_done;
   s->last_stream = s->stream;
@@ -948,9 +951,7 @@ trk_status trk_track_frame_device(trk_session* s, const float* d_depth_m, void* 
   cudaGraphExec_t ge;
   TRY(frame_graph(s, &ge));
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : s->stream;
-  const Dev& d = s->d;
-  CK(cudaMemcpyAsync(const_cast<float*>(d.depth), d_depth_m, sizeof(float) * d.cam.W * d.cam.H,
-                     cudaMemcpyDeviceToDevice, st));
+  launch_tiles(s->d, d_depth_m, st);  // copies the caller's depth and lists its occupied tiles: no memcpy
   CK(cudaGraphLaunch(ge, st));
   ++s->frames_done;
   CK(cudaGetLastError());
@@ -994,6 +995,7 @@ trk_status trk_set_depth(trk_session* s, const float* depth_m) {
   NEED_RESIDENT(s);
   CK(cudaMemcpyAsync(const_cast<float*>(s->d.depth), depth_m, sizeof(float) * s->d.cam.W * s->d.cam.H,
                      cudaMemcpyHostToDevice, s->stream));
+  launch_tiles(s->d, s->d.depth, s->stream);
   return sync_check(s);
 }
 
@@ -1022,6 +1024,7 @@ trk_status trk_step_associate(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
   NEED_RESIDENT(s);
   CK(cudaMemsetAsync(s->d.qctl, 0, sizeof(unsigned) * 2, s->stream));
+  CK(cudaMemsetAsync(s->d.qctl + 3, 0, sizeof(unsigned), s->stream));  // from the first occupied tile
   launch_associate(s->d, s->stream);
   return sync_check(s);
 }
@@ -1096,7 +1099,7 @@ trk_status trk_get_info(trk_session* s, trk_info* out) {
   out->height = d.cam.H;
   const int per_assoc = (d.F > 0 ? 5 : 4);  // skin, raster, visibility, associate (2 kernels)
   const int shape_k = s->prm.shape_solver == 1 ? 3 * s->prm.shape_sweeps + 1 : s->prm.shape_sweeps;
-  out->kernels_per_frame = s->prm.pose_iters * (per_assoc + 5) + s->prm.shape_iters * (per_assoc + shape_k);
+  out->kernels_per_frame = 1 + s->prm.pose_iters * (per_assoc + 5) + s->prm.shape_iters * (per_assoc + shape_k);
   out->device_bytes = s->device_bytes;
   out->jtj_group = s->d.jtj_group;
   return TRK_OK;

@@ -219,6 +219,9 @@ void launch_skin(const Dev& d, int phi_buf, cudaStream_t st);
 void launch_raster(const Dev& d, cudaStream_t st);
 void launch_visibility(const Dev& d, cudaStream_t st);
 void launch_associate(const Dev& d, cudaStream_t st);  // two kernels: thread-owned rings, then the queue
+// Copies the frame's depth from src into d.depth (src == d.depth: in place) and lists the 16 x 16 tiles
+// that hold a valid pixel (the single-session association takes its tiles from that list).
+void launch_tiles(const Dev& d, const float* src, cudaStream_t st);
 // residual + Jacobian + [J r]^T [J r]; writes E_pose to energy[slot] (slot < 0: not recorded)
 void launch_normal_equations(const Dev& d, int phi_buf, int slot, cudaStream_t st);
 void launch_lm(const Dev& d, int phi_buf, cudaStream_t st);
@@ -279,7 +282,8 @@ struct Dev {
   float4* pixrec;  // [W*H] first vertex inserted into each pixel's bucket: x, y, z, index bits
   int* head;
   int4* queue;     // [W*H] pixels whose association search continues past the thread-owned rings
-  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take
+  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take, [2] occupied tiles, [3] next tile
+  int4* tiles;     // [ceil(W/16) ceil(H/16)] 16 x 16 tiles holding a valid depth pixel (0, x, y, tiles per row)
   unsigned long long* zbuf;
   int* corr;
   Acc4* acc;

@@ -127,7 +127,7 @@ def lib(build_if_missing: bool = True):
             "trk_schedule_signature": [C.POINTER(vp), i32, C.c_char_p, sz],
             "trk_tuning_cache_lookup": [C.c_char_p, C.c_char_p, vp, C.POINTER(C.c_double)],
             "trk_tuning_cache_store": [C.c_char_p, C.c_char_p, vp, C.c_double],
-            "trk_server_create": [sz, i32, C.POINTER(vp)], "trk_server_configure": [vp, i32, i32, i32],
+            "trk_server_create": [sz, i32, C.POINTER(vp)], "trk_server_configure": [vp, i32, i32, i32, C.c_int64],
             "trk_server_attach": [vp, vp], "trk_server_detach": [vp, vp],
             "trk_server_submit": [vp, vp, vp, C.POINTER(C.c_uint64)], "trk_server_wait": [vp, C.c_uint64, C.c_int64, vp],
             "trk_server_get_stats": [vp, vp],
@@ -488,12 +488,12 @@ class Server:
     """Continuous-batching frame server (trk_server_*) over attached sessions."""
 
     def __init__(self, hbm_budget_bytes: int, max_inflight: int = 32, dispatch: int = SERVER_DISPATCH_BATCHED,
-                 max_batch: int = 64, concurrent_steps: int = 2):
+                 max_batch: int = 64, concurrent_steps: int = 2, max_wait_us: int = 2000):
         h = C.c_void_p()
         _check(lib().trk_server_create(hbm_budget_bytes, max_inflight, C.byref(h)))
         self.h = h
         self._sessions = {}
-        _check(lib().trk_server_configure(self.h, dispatch, max_batch, concurrent_steps))
+        _check(lib().trk_server_configure(self.h, dispatch, max_batch, concurrent_steps, max_wait_us))
 
     def attach(self, session: Session):
         _check(lib().trk_server_attach(self.h, session.h))
