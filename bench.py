@@ -167,8 +167,8 @@ def algorithmic(stage, V, F, npx, NP, nvis, nassoc_px, nA, n_valid_px, nblk):
         return "hbm", F * (16 + 16) + V * 16 + n_valid_px * 8
     if stage == "visibility":  # CSR, face normals, v, normals out, z-buffer probes, bucket records
         return "hbm", V * (4 + 16 + 16 + 4) + 3 * F * 4 + F * 16 + nvis * (8 + 4 + 16)
-    if stage == "associate":  # depth in, corr out, bucket heads, visible records, per-vertex sums
-        return "hbm", n_valid_px * (4 + 4 + 4) + nvis * 16 + nassoc_px * 32
+    if stage == "associate":  # depth in and correspondences out over the image, the associated vertices' sums
+        return "hbm", npx * (4 + 4) + nA * 28
     if stage == "resid_jtj":  # sums and normals of every vertex; streams of A; partials of blocks with rows;
         # the 64-byte record of every row for the candidate energies
         return "hbm", V * (32 + 16) + nA * (4 + 16 + 16 + 16 + 16) + nblk * NP * NP * 4 + nA * 64
@@ -254,12 +254,14 @@ def cpu_baseline(model, n_frames):
     o.set_state(synth.gt_theta(model, 0.0), None)
     states = []
     dt = 0.0
+    start = (synth.gt_theta(model, 0.0), np.zeros((o.V, 3)), model["params"]["lambda_k0"])
     for d in frames:
         t0 = time.perf_counter()
         e, _, _ = o.track_frame(d)
         dt += time.perf_counter() - t0
-        th, phi, _ = o.get_state()
-        states.append((th, phi, e, determined_dofs(o, model, th, phi, d)))
+        th, phi, lam = o.get_state()
+        states.append((th, phi, e, determined_dofs(o, model, th, phi, d), start))
+        start = (th, phi, lam)
     return dict(value=n_frames / dt, unit="frames/s", cores=1, kind="oracle",
                 sample=f"first {n_frames} frames of the sequence, 10 pose + 2 shape iterations each, FP64, 1 thread",
                 seconds=round(dt, 2)), frames, states, o
@@ -304,17 +306,37 @@ def cpu_baseline_all_cores(n_frames):
             "sample": f"{cores} independent sessions of the 50k-vertex workload, {n_frames} frames each, one per process"}
 
 
+def lockstep_vs_oracle(model, prec, frames, states, o, n_frames=2):
+    """Per-result error of one precision mode against the oracle, frame by frame from the oracle's own
+    state (tests/sequence.py): both run the frame in lockstep, the oracle taking the GPU's choice only at
+    pixels it flags as correspondence ties; then joint values on all DoFs, offsets on all vertices, the
+    energy of every iteration at the same state, the LM decisions."""
+    from paper_1711_07999_gb300 import synth, trk
+    from tests import sequence as seq
+    out = []
+    with trk.Session(synth.make_model(2, precision=prec)) as s:
+        for f, (d, st) in enumerate(zip(frames[:n_frames], states[:n_frames])):
+            th, phi, lam = st[4]
+            out.append(seq.summary(seq.follow_frame(o, s, d, th, np.asarray(phi, np.float32), lam, frames_done=f)))
+    return {"frames": len(out), "theta_rad_max": max(x["theta_rad_max"] for x in out),
+            "offsets_mm_max": max(x["offsets_mm_max"] for x in out),
+            "energy_rel_max_matched": max(x["energy_rel_max_matched"] for x in out),
+            "nontie_mismatches": sum(x["nontie_mismatches"] for x in out),
+            "tie_flips": sum(x["tie_flips"] for x in out), "invalid_flips": sum(x["invalid_flips"] for x in out),
+            "lm_decisions_equal": all(x["lm_decisions_equal"] for x in out)}
+
+
 def errors_vs_oracle(model, prec, frames, states, o):
-    """Per-result error of one precision mode against the oracle on the same frames (free-running from
-    the same start): joint values (all, and those the energy determines to 1e-3 rad), offsets (99th
-    percentile and max over vertices; and the 99th percentile over the vertices the two final poses
-    place within 0.05 mm of each other, where the offsets are comparable), energies."""
+    """Per-result error of one precision mode against the oracle on the same frames, free-running from
+    the same start (the two paths part at correspondence ties): joint values (all, and those the energy
+    determines to 1e-3 rad), offsets (99th percentile and max over vertices; and the 99th percentile over
+    the vertices the two final poses place within 0.05 mm of each other), energies."""
     from paper_1711_07999_gb300 import synth, trk
     dth, dthd, ndet, dphi99, dphimax, de, agree99, agree_frac = [], [], [], [], [], [], [], []
     zero = np.zeros((o.V, 3))
     with trk.Session(synth.make_model(2, precision=prec)) as s:
         s.set_pose(synth.gt_theta(model, 0.0))
-        for d, (th, phi, e, det) in zip(frames, states):
+        for d, (th, phi, e, det, _) in zip(frames, states):
             g = s.track_frame(d)
             dth.append(float(np.abs(g["theta"] - th).max()))
             dthd.append(float(np.abs(g["theta"] - th)[det].max()))
@@ -333,31 +355,37 @@ def errors_vs_oracle(model, prec, frames, states, o):
             "vertices_where_poses_agree": min(agree_frac), "energy_rel_max": max(de)}
 
 
-def run_precision_modes(args, model, rank, dev, n_seq, flush, nA, NP, sample):
-    """Each [J r]^T [J r] arithmetic (FP32 cores, split-BF16x3 and 3xTF32 on the tensor cores): batched
-    frames/s with the same sessions and frames as the FP32 batched run, the contraction stage's time, and
-    (rank 0, one GPU) the error of every result against the oracle on the CPU-baseline frames."""
+def run_precision_modes(args, model, rank, host_frames, nA, NP, sample):
+    """The serving path in each [J r]^T [J r] arithmetic (FP32 cores, split-BF16x3 and 3xTF32 on the tensor
+    cores): --precision-sessions streams through the frame server with batched dispatch, closed loop (host
+    depth in, results out), beside the plain FP32 per-session dispatch of the same streams; one session's
+    contraction-stage time; and (rank 0, one GPU) each mode's error against the oracle on the CPU-baseline
+    frames, in lockstep and free-running."""
     from paper_1711_07999_gb300 import synth, trk
     out = {}
-    for name, prec in (("fp32", trk.PRECISION_FP32), ("bf16x3", trk.PRECISION_BF16X3),
-                       ("tf32x3", trk.PRECISION_TF32X3)):
-        group = [trk.Session(synth.make_model(2, session=rank * 1000 + b, precision=prec)) for b in range(args.sessions)]
+    B = args.precision_sessions
+    runs = (("fp32_per_session", trk.PRECISION_FP32, trk.SERVER_DISPATCH_SESSION),
+            ("fp32", trk.PRECISION_FP32, trk.SERVER_DISPATCH_BATCHED),
+            ("bf16x3", trk.PRECISION_BF16X3, trk.SERVER_DISPATCH_BATCHED),
+            ("tf32x3", trk.PRECISION_TF32X3, trk.SERVER_DISPATCH_BATCHED))
+    for name, prec, disp in runs:
+        group = [trk.Session(synth.make_model(2, session=rank * 1000 + b, precision=prec)) for b in range(B)]
         for b, x in enumerate(group):
-            x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
-        steps = max(3, args.steps // 2)
-        tb, lat = run_batched(group, dev, n_seq, steps, args.warmup, flush)
-        group[0].set_depth(dev[0].cpu().numpy())
-        prof = group[0].profile_iteration(reps=args.profile_reps, flush_bytes=L2_FLUSH_BYTES)
-        ms = prof["resid_jtj"]
-        r = {"batched_fps": len(group) * steps / (tb / 1000.0), "latency_ms_p99": float(np.percentile(lat, 99)),
-             "resid_jtj_ms": ms}
-        if prec != trk.PRECISION_FP32:
-            # the contraction's tensor work: 3 products of 2 * 128 * N per associated row (M padded to 128)
-            N = 16 * ((NP + 15) // 16)
-            tflops = 3 * 2 * 128 * N * nA / (ms / 1000.0) / 1e12
-            r["tensor_tflops_in_stage"] = tflops
-        if sample is not None:
-            r["error_vs_oracle"] = errors_vs_oracle(model, prec, *sample)
+            x.set_pose(synth.gt_theta(model, (7 * b % len(host_frames)) / 30.0))
+        srv = run_serving_closed_loop(group, host_frames, max(3, args.steps // 3), disp,
+                                      concurrent_steps=args.server_steps)
+        r = {"dispatch": "per-session" if disp == trk.SERVER_DISPATCH_SESSION else "batched",
+             "serving_fps": srv["fps"], "latency_ms": srv["latency_ms"], "frames_per_launch": srv["frames_per_launch"]}
+        if name != "fp32_per_session":
+            group[0].set_depth(host_frames[0])
+            prof = group[0].profile_iteration(reps=args.profile_reps, flush_bytes=L2_FLUSH_BYTES)
+            r["resid_jtj_ms"] = prof["resid_jtj"]
+            if prec != trk.PRECISION_FP32:
+                # the method's contraction work: NP^2 multiply-adds per row of A, 3 split products each
+                r["contraction_tflops_in_stage"] = 3 * 2 * NP * NP * nA / (prof["resid_jtj"] / 1000.0) / 1e12
+            if sample is not None:
+                r["lockstep_vs_oracle"] = lockstep_vs_oracle(model, prec, *sample)
+                r["free_running_vs_oracle"] = errors_vs_oracle(model, prec, *sample)
         for x in group:
             x.close()
         out[name] = r
@@ -425,6 +453,38 @@ def run_batched(sessions, dev_frames, n_seq, steps, warmup, flush):
     total = sum(e0.elapsed_time(e1) for e0, _, e1 in recs)
     lat = [e0.elapsed_time(e) for e0, ends, _ in recs for e in ends]
     return total, lat
+
+
+def run_schedule(sessions, dev_frames, n_seq, steps, warmup, flush):
+    """The sessions under the schedule the autotuner picks (groups of fused batches on concurrent streams,
+    tuned on the warm-up frames), each step one frame of every session; device-timed with CUDA events on
+    the launching stream, L2 flushed before every step.  A frame's latency is its step's time (every
+    group starts at the step's start)."""
+    import torch
+    from paper_1711_07999_gb300 import trk
+    B = len(sessions)
+    st = torch.cuda.Stream()
+
+    def ptrs(k):
+        return [dev_frames[(k + 7 * b) % n_seq].data_ptr() for b in range(B)]
+
+    with trk.Schedule(sessions) as sc:
+        cfg, _ = sc.autotune(ptrs(0), reps=2)
+        for k in range(warmup):
+            sc.track_device(ptrs(k), st.cuda_stream)
+        torch.cuda.synchronize()
+        ev = []
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            sc.track_device(ptrs(warmup + k), st.cuda_stream)
+            e1.record(st)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        t = np.array([a.elapsed_time(b) for a, b in ev])
+    return {"config": cfg, "total_ms": float(t.sum()),
+            "latency_ms": {"p50": float(np.percentile(t, 50)), "p99": float(np.percentile(t, 99))}}
 
 
 def run_batched_e2e(sessions, host_frames, n_seq, steps, flush):
@@ -530,6 +590,55 @@ def run_serving(sessions, host_frames, n_seq, duration_s, fps, seed):
                                                       "max": st["latency_max_us"] / 1000}}
 
 
+def run_serving_closed_loop(sessions, host_frames, frames_per_stream, dispatch, max_batch=64, concurrent_steps=4):
+    """Saturated serving: every stream submits its next frame as soon as its previous one is collected
+    (closed loop, one thread per stream), through the frame server in the given dispatch mode.  Returns
+    frames/s over the wall time and the server's submit -> completion latency."""
+    import threading
+    from paper_1711_07999_gb300 import trk
+    N = len(sessions)
+    budget = sum(x.info()["device_bytes"] for x in sessions) + (1 << 30)
+    with trk.Server(budget, max_inflight=N, dispatch=dispatch, max_batch=max_batch,
+                    concurrent_steps=concurrent_steps) as sv:
+        for x in sessions:
+            sv.attach(x)
+        for b, x in enumerate(sessions):  # warm-up frame (frame graphs, step buffers, staging)
+            sv.wait(x, sv.submit(x, host_frames[b % len(host_frames)]), timeout_us=60_000_000, want_offsets=False)
+        barrier = threading.Barrier(N + 1)
+        lat = [[] for _ in range(N)]
+
+        def stream(b):
+            barrier.wait()
+            for k in range(frames_per_stream):
+                t0 = time.perf_counter()
+                t = sv.submit(sessions[b], host_frames[(k + 7 * b) % len(host_frames)])
+                sv.wait(sessions[b], t, timeout_us=60_000_000, want_offsets=True)
+                lat[b].append(1e3 * (time.perf_counter() - t0))
+            barrier.wait()
+
+        th = [threading.Thread(target=stream, args=(b,)) for b in range(N)]
+        for t in th:
+            t.start()
+        st0 = sv.stats()
+        barrier.wait()
+        t0 = time.perf_counter()
+        barrier.wait()
+        wall = time.perf_counter() - t0
+        for t in th:
+            t.join()
+        st = sv.stats()
+        for x in sessions:
+            sv.detach(x)
+    n = N * frames_per_stream
+    steps = st["steps"] - st0["steps"]
+    la = np.concatenate([np.array(x) for x in lat])
+    return {"streams": N, "frames": n, "seconds": round(wall, 3), "fps": n / wall,
+            "frames_per_launch": n / max(steps, 1),
+            "latency_ms": {"p50": float(np.percentile(la, 50)), "p99": float(np.percentile(la, 99)),
+                           "max": float(la.max())},
+            "h2d_bytes_per_frame": int(sessions[0].W * sessions[0].H * 4)}
+
+
 def run_admission_serving(args, rank):
     """Streams of uneven sessions arriving over time under an HBM budget that binds: --admission-streams
     sessions of the random-tree bodies; stream starts form a Poisson process (rate: all streams within
@@ -544,12 +653,17 @@ def run_admission_serving(args, rank):
     budget = int(args.admission_budget_gib * (1 << 30))
     rng = np.random.default_rng(synth.seed_for(5, rank))
     models = [synth.make_model(4, session=20000 + rank * 1000 + k) for k in range(N)]
-    sess = [trk.Session(m) for m in models]
     frames = []
-    for i, (m, s) in enumerate(zip(models, sess)):
+    for i, m in enumerate(models):
         r = np.random.default_rng(synth.seed_for(5, 100 + i))
-        frames.append([synth.add_noise(s.render_depth(synth.gt_theta(m, f / 30.0), synth.gt_offsets(m, f / 30.0)), 4, r)
-                       for f in range(4)])
+        with trk.Session(m) as s:
+            frames.append([synth.add_noise(s.render_depth(synth.gt_theta(m, f / 30.0), synth.gt_offsets(m, f / 30.0)),
+                                           4, r) for f in range(4)])
+    torch.cuda.synchronize()
+    base_free = torch.cuda.mem_get_info()[0]
+    # the sessions are created evicted: no device memory until the server admits them
+    sess = [trk.Session(m, evicted=True) for m in models]
+    for m, s in zip(models, sess):
         s.set_pose(synth.gt_theta(m, 0.0))
     need = [s.info()["device_bytes"] for s in sess]
     starts = np.cumsum(rng.exponential(1.0 / N, N))
@@ -603,6 +717,16 @@ def run_admission_serving(args, rank):
                 used[0] -= need[b]
                 lock.notify_all()
 
+        dev_peak = [0]
+        sampling = [True]
+
+        def sample_memory():  # device memory in use beyond what it was before the sessions existed
+            while sampling[0]:
+                dev_peak[0] = max(dev_peak[0], base_free - torch.cuda.mem_get_info()[0])
+                time.sleep(0.002)
+
+        mon = threading.Thread(target=sample_memory, daemon=True)
+        mon.start()
         t0 = time.perf_counter()
         th = [threading.Thread(target=stream, args=(b, t0)) for b in range(N)]
         for x in th:
@@ -610,12 +734,18 @@ def run_admission_serving(args, rank):
         for x in th:
             x.join()
         wall = time.perf_counter() - t0
+        sampling[0] = False
+        mon.join()
         st = sv.stats()
     for s in sess:
         s.close()
     w = np.array([x for x in waits if x == x]) * 1e3
     return {"streams": N, "frames_per_stream": K, "fps_per_stream": fps, "budget_bytes": budget,
             "sum_of_session_bytes": int(sum(need)), "peak_admitted_bytes": int(peak[0]),
+            "peak_device_bytes_in_use": int(dev_peak[0]),
+            "device_memory_note": "cudaMemGetInfo sampled every 2 ms against its value before the sessions existed "
+                                  "(sessions created evicted; the server's step buffers included)",
+            "frames_per_launch": st["mean_frames_per_step"],
             "streams_that_waited": int((w > 1.0).sum()), "streams_over_budget": int(N - len(w)),
             "admission_wait_ms": {"p50": float(np.percentile(w, 50)), "p99": float(np.percentile(w, 99)),
                                   "max": float(w.max())},
@@ -758,6 +888,33 @@ def run_experiments(args, rank):
     return out
 
 
+def summary_of(line):
+    """The figures a reader wants first: throughput plain / batched / end to end, the serving comparison
+    per arithmetic, parity in lockstep with the oracle, the admission run's device memory against its
+    budget, the roofline fraction."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    out = {"plain_fps": g(line, "plain", "value"), "batched_fps": line["value"], "e2e_fps": g(line, "e2e", "value"),
+           "latency_p99_ms": g(line, "latency_ms", "p99"), "roofline_frac": g(line, "roofline", "frac"),
+           "roofline_kernel": g(line, "roofline", "kernel")}
+    prec = line.get("precision") or {}
+    out["serving_fps"] = {k: round(v["serving_fps"], 1) for k, v in prec.items() if "serving_fps" in v}
+    out["serving_p99_ms"] = {k: round(v["latency_ms"]["p99"], 2) for k, v in prec.items() if "latency_ms" in v}
+    out["lockstep_vs_oracle"] = {
+        k: {q: v["lockstep_vs_oracle"][q] for q in ("theta_rad_max", "offsets_mm_max", "energy_rel_max_matched",
+                                                    "nontie_mismatches", "lm_decisions_equal")}
+        for k, v in prec.items() if "lockstep_vs_oracle" in v}
+    adm = line.get("admission_serving") or {}
+    if adm:
+        out["admission"] = {q: adm.get(q) for q in ("budget_bytes", "peak_device_bytes_in_use", "achieved_fps")}
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -845,37 +1002,57 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_flops": amount, "peak_source": "nominal FP64 rate"}
     roof["note"] = ROOFLINE_NOTES.get(dom, "")
     h2d = W * H * 4
-    d2h = info["n_links"] * 8 + (P + S) * 8 + info["n_verts"] * 12 + 8
-    # batched: B concurrent sessions (own stream and graph each) on this GPU
+    d2h = info["n_links"] * 8 + (P + S) * 8 + info["n_verts"] * 12 + 8  # trk_track_frame's copies
+    d2h_srv = info["n_links"] * 8 + (P + S) * 8 + info["n_verts"] * 16 + 16  # the server's mapped staging
+    # batched: B sessions of the same workload on this GPU, three ways (device-timed, depth resident):
+    # one stream and graph per session; one fused batch per group of the autotuned schedule (the headline);
+    # and end to end through the frame server (host depth in, results out, batched dispatch)
     batched = None
     B = args.sessions
     if B > 1:
-        extra = [trk.Session(synth.make_model(2, session=rank * 1000 + b + 1, precision=prec)) for b in range(B - 1)]
-        group = [sess] + extra
+        group = [trk.Session(synth.make_model(2, session=rank * 1000 + b, precision=prec,
+                                              jtj_group=args.batch_jtj_group)) for b in range(B)]
         for b, x in enumerate(group):
             x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
         tb, lat_b = run_batched(group, dev, n_seq, args.steps, args.warmup, flush)
-        tb_max = max_over_ranks(tb, world)
-        wall_b, lat_be = run_batched_e2e(group, [host[i].numpy() for i in range(n_seq)], n_seq, args.steps, flush)
-        batched = {"sessions": B, "value": whole_job_rate(world, B * args.steps, tb_max / 1000.0),
-                   "ms_per_step": tb_max / args.steps,
-                   "latency_ms": {"p50": float(np.percentile(lat_b, 50)), "p99": float(np.percentile(lat_b, 99))},
-                   "e2e": {"value": whole_job_rate(world, B * args.steps, max_over_ranks(wall_b, world)),
-                           "p50_ms": float(np.percentile(lat_be, 50)), "p99_ms": float(np.percentile(lat_be, 99))}}
+        streams_fps = whole_job_rate(world, B * args.steps, max_over_ranks(tb, world) / 1000.0)
+        for b, x in enumerate(group):
+            x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
+        with ClockSampler(local_rank) as clk_b:
+            sched = run_schedule(group, dev, n_seq, args.steps, args.warmup, flush)
+        ts_max = max_over_ranks(sched["total_ms"], world)
+        # the batched step's stages, one launch each over all B sessions (a fused batch profiled at the
+        # sequence's first frame, cold L2): the dominant stage and its roofline
+        for x in group:
+            x.set_pose(synth.gt_theta(model, 0.0))
+        with trk.Batch(group) as fb:
+            bprof = fb.profile([dev[0].data_ptr()] * B, reps=3, flush_bytes=L2_FLUSH_BYTES)
+        bcounts = [session_counts(x, frames[0]) for x in group]
+        host_frames = [host[i].numpy() for i in range(n_seq)]
+        for b, x in enumerate(group):
+            x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
+        e2e_srv = run_serving_closed_loop(group, host_frames, max(3, args.steps // 2), trk.SERVER_DISPATCH_BATCHED,
+                                          concurrent_steps=args.server_steps)
+        e2e_fps = whole_job_rate(world, e2e_srv["frames"] / world, max_over_ranks(e2e_srv["seconds"], world))
+        batched = {"sessions": B, "jtj_group": args.batch_jtj_group, "clocks": clk_b.summary(),
+                   "stage_ms": {k: round(v, 5) for k, v in bprof.items()},
+                   "value": whole_job_rate(world, B * args.steps, ts_max / 1000.0),
+                   "ms_per_step": ts_max / args.steps, "schedule": sched["config"],
+                   "latency_ms": sched["latency_ms"],
+                   "streams_fps": streams_fps,
+                   "streams_latency_ms": {"p50": float(np.percentile(lat_b, 50)), "p99": float(np.percentile(lat_b, 99))},
+                   "e2e": {"value": e2e_fps, "p50_ms": e2e_srv["latency_ms"]["p50"],
+                           "p99_ms": e2e_srv["latency_ms"]["p99"], "server": e2e_srv}}
         serving = None
         if args.serve_streams > 0:
-            more = [trk.Session(synth.make_model(2, session=rank * 1000 + 100 + b, precision=prec))
-                    for b in range(max(0, args.serve_streams - len(group)))]
-            streams = (group + more)[:args.serve_streams]
+            streams = group[:args.serve_streams]
             for b, x in enumerate(streams):
                 x.set_pose(synth.gt_theta(model, (7 * b % n_seq) / 30.0))
-            serving = run_serving(streams, [host[i].numpy() for i in range(n_seq)], n_seq, args.serve_seconds, 30.0,
-                                  synth.seed_for(5, rank))
-            for x in more:
-                x.close()
+            serving = run_serving(streams, host_frames, n_seq, args.serve_seconds, 30.0, synth.seed_for(5, rank))
         batched["serving"] = serving
-        for x in extra:
-            x.close()
+        for x in group:
+            if x is not sess:
+                x.close()
     line = None
     cpu, sample = None, None
     if rank == 0 and world == 1 and args.cpu_frames > 0:
@@ -885,10 +1062,25 @@ def run_ours(args, rank, world, local_rank):
             cpu["all_cores"] = cpu_baseline_all_cores(args.cpu_all_cores_frames)
     precision = None
     if args.precision_modes and B > 1:
-        precision = run_precision_modes(args, model, rank, dev, n_seq, flush, nA, NP, sample)
+        precision = run_precision_modes(args, model, rank, [host[i].numpy() for i in range(n_seq)], nA, NP, sample)
     uneven = run_uneven(args, rank, flush) if args.uneven_sessions > 0 else None
     admission = run_admission_serving(args, rank) if args.admission_streams > 0 else None
     experiments = run_experiments(args, rank) if (args.experiment_frames > 0 and rank == 0) else None
+    if batched is not None:  # the headline is the batched step: its dominant stage's roofline
+        pf = {st: ms * ((P + S) if st in ("skin", "raster", "visibility", "associate") else (S if st == "shape" else P))
+              for st, ms in batched["stage_ms"].items()}
+        dom_b = max(pf, key=pf.get)
+        kind_b, amount_b = "hbm", 0
+        for c in bcounts:
+            kind_b, a_b = algorithmic(dom_b, **c)
+            amount_b += a_b
+        if kind_b == "hbm":
+            ach = amount_b / (batched["stage_ms"][dom_b] / 1000.0) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                    "traffic": ncu_traffic(dom_b + "_batch"), "kernel": dom_b,
+                    "launch": f"one launch over {B} sessions (fused batch)", "algorithmic_bytes": amount_b,
+                    "peak_source": pk["src"] + " (burst copy)", "note": ROOFLINE_NOTES.get(dom_b, "")}
+        batched["stage_share"] = {k: round(v / sum(pf.values()), 4) for k, v in pf.items()}
     if rank == 0:
         plain = {"value": value, "ms_per_step": max_ms / args.steps,
                  "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
@@ -902,26 +1094,36 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "n_verts": info["n_verts"], "n_tris": info["n_tris"],
                        "dof": info["n_links"], "image": f"{W}x{H}", "pose_iters": P, "shape_iters": S,
                        "sessions_per_gpu": B if batched is not None else 1,
-                       "batching": "concurrent sessions, one stream and one CUDA graph each" if batched else "none",
+                       "batching": (f"autotuned schedule: {batched['schedule']['groups']} groups of fused batches "
+                                    "(one launch per stage over a group's sessions, one CUDA graph per group) on "
+                                    "concurrent streams; e2e through the frame server (batched dispatch)")
+                       if batched else "none",
+                       "jtj_group": args.batch_jtj_group if batched else info["jtj_group"],
                        "l2": "flushed (256 MiB write) before every step",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": head["latency_ms"],
             "e2e": {"value": head["e2e"]["value"], "unit": "frames/s", "h2d_bytes_per_step": h2d * B,
-                    "d2h_bytes_per_step": d2h * B, "p50_ms": head["e2e"]["p50_ms"], "p99_ms": head["e2e"]["p99_ms"]},
+                    "d2h_bytes_per_step": (d2h_srv if batched is not None else d2h) * B,
+                    "p50_ms": head["e2e"]["p50_ms"], "p99_ms": head["e2e"]["p99_ms"],
+                    "path": "trk_server_submit / trk_server_wait, host depth in, results out" if batched is not None
+                    else "trk_track_frame, host depth in, results out"},
             "plain": plain,
             "batched": batched,
             "precision": precision,
             "uneven": uneven,
             "admission_serving": admission,
             "experiments": experiments,
-            "gpu_launches": info["kernels_per_frame"] * args.steps * (B if batched is not None else 1),
+            "gpu_launches": (batched["schedule"]["groups"] * (info["kernels_per_frame"] + P + S) * args.steps
+                             if batched is not None else info["kernels_per_frame"] * args.steps),
             "roofline": roof,
             "stage_ms": {k: round(v, 5) for k, v in prof.items()},
             "stage_share": {k: round(v / sum(per_frame.values()), 4) for k, v in per_frame.items()},
-            "clocks": clk.summary(),
+            "clocks": batched["clocks"] if batched is not None else clk.summary(),
+            "plain_clocks": clk.summary(),
             "cpu_baseline": cpu,
             "check": {"last_energy": float(res["energy"][P - 1]), "assoc_px": res["n_assoc_px"]},
         }
+        line["summary"] = summary_of(line)  # last, so that a truncated tail of the line still shows it
     sess.close()
     return line
 
@@ -937,7 +1139,12 @@ def main():
     ap.add_argument("--cpu-all-cores-frames", type=int, default=2,
                     help="frames per core of the all-cores oracle baseline (0: skip)")
     ap.add_argument("--profile-reps", type=int, default=20)
-    ap.add_argument("--sessions", type=int, default=16, help="concurrent sessions of the batched measurement")
+    ap.add_argument("--sessions", type=int, default=64, help="sessions of the batched measurement")
+    ap.add_argument("--batch-jtj-group", type=int, default=4, choices=[0, 1, 2, 4],
+                    help="[J r] grouping of the batched sessions (4: fewer block partials; 0: by mesh size)")
+    ap.add_argument("--server-steps", type=int, default=4, help="concurrent batched steps of the frame server")
+    ap.add_argument("--precision-sessions", type=int, default=32,
+                    help="streams of the serving run in each precision mode")
     ap.add_argument("--serve-streams", type=int, default=32, help="Poisson streams (30 fps each) of the serving run")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32",

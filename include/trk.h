@@ -91,7 +91,8 @@ typedef struct {
   int32_t association;  /* 0: the closest visible vertex in the window (Sec. 4.1); 1: the nearest
                            corner of the triangle the z-buffer holds at the pixel (O(1) per pixel)   */
   int32_t jtj_group;    /* vertices per block of the [J r]^T [J r] contraction, in units of 256: 1, 2
-                           or 4 (fewer block partials to add; FP32 precision only).  0: the larger of
+                           or 4 (fewer block partials to add; batches of many sessions run faster with
+                           4).  0: the larger of
                            the choice by mesh size (1 up to 304 units, 2 up to 608, else 4) and by the
                            expected rows per unit r = 128 c / V, c = distinct pixels the template's
                            vertices round to at the bind pose (4 if r < 18, 2 if r < 30, else 1)      */
@@ -299,11 +300,15 @@ typedef struct {
   uint64_t frames_done;     /* frames completed since the server was created            */
   int32_t in_flight;        /* frames on the GPU now                                     */
   int32_t sessions;         /* attached sessions                                         */
-  size_t hbm_used_bytes;    /* device bytes of the attached sessions (what the budget counts) */
+  size_t hbm_used_bytes;    /* what the budget counts: the attached sessions' arenas and the batched
+                               steps' buffers (per slot twice the largest sum of the sessions' step
+                               tables so far), all in 2 MiB units                                     */
   double latency_p50_us, latency_p99_us, latency_max_us;  /* submit -> completion, wall time; the
                                percentiles to 1.2 % (log-spaced bins), the maximum exact */
   uint64_t steps;           /* launches of frames: batched steps plus single-session frames */
   double mean_frames_per_step;
+  size_t device_bytes_reserved; /* device memory the library holds now (the arenas of every resident
+                                   session, any server's step buffers), in 2 MiB units                */
 } trk_server_stats;
 
 /* How the dispatcher launches ready frames.  BATCHED (the default): the ready frames of sessions that
@@ -327,10 +332,12 @@ trk_status trk_server_create(size_t hbm_budget_bytes, int32_t max_inflight, trk_
  * before the first attach. */
 trk_status trk_server_configure(trk_server* sv, int32_t dispatch, int32_t max_batch, int32_t concurrent_steps,
                                 int64_t max_wait_us);
-/* Admits a session (same device).  TRK_ERR_NO_CAPACITY if its device bytes do not fit the remaining
- * budget.  An evicted session (trk_create_evicted, trk_session_evict) is restored here -- its device
- * state is allocated at admission -- and evicted again at trk_server_detach, so the budget bounds the
- * device memory of such sessions; a session that is already resident is counted but holds its memory
+/* Admits a session (same device).  TRK_ERR_NO_CAPACITY if its device bytes (its arena and, for batched
+ * dispatch, its share of the step buffers) do not fit the remaining budget.  An evicted session
+ * (trk_create_evicted, trk_session_evict) is restored here -- its device state is allocated at admission
+ * -- and evicted again at trk_server_detach, so the budget bounds the device memory of such sessions
+ * (arenas and step buffers are counted at the 2 MiB allocation granularity); a session that is already
+ * resident is counted but holds its memory
  * regardless.  While attached, the session must be driven only through the server. */
 trk_status trk_server_attach(trk_server* sv, trk_session* s);
 /* Releases a session's budget (evicting it if attach restored it); TRK_ERR_INVALID_ARG while it still

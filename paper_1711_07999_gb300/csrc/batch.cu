@@ -66,6 +66,12 @@ namespace {
 
 BatchGrid grid_of(const trk_batch* b, Kind k) { return BatchGrid{b->d_devs, b->tables[k].d_map}; }
 
+int reduce_threads_of(const trk_batch* b) {
+  int w = 1;
+  for (trk_session* s : b->sessions) w = std::max(w, reduce_warps(session_dev(s).nblk_rows));
+  return 32 * w;
+}
+
 // The members' device state is still the one the batch's tables and graph point into.
 bool members_current(const trk_batch* b) {
   for (size_t k = 0; k < b->sessions.size(); ++k)
@@ -85,7 +91,7 @@ void blocks_of(const Dev& d, Kind k, int& gx, int& gy) {
     case kJtj1: case kJtj2: case kJtj3: case kJtj4: case kJtj5:
       gx = (d.NP + 15) / 16 == k - kJtj1 + 1 ? d.nblk_rows : 0;
       break;
-    case kReduce: gx = (d.NP * d.NP + 31) / 32; break;
+    case kReduce: gx = (d.NP * (d.NP + 1) / 2 + 31) / 32; break;  // the upper triangle
     case kRows: gx = d.nblk_rows; break;
     default: gx = kCandidates; break;  // kLm
   }
@@ -103,7 +109,14 @@ struct FrameView {
   int4* d_tiles = nullptr;          // [tables[kAssoc].n]
   const float* const* d_srcs = nullptr;  // [B] depth of each session (device-readable)
   const Dev* const* host_devs = nullptr;  // [B] the sessions' descriptors on the host
+  int reduce_threads = 32;                // the reduction's block: the largest need of the sessions
 };
+
+int reduce_threads_for(const Dev* const* hd, int n) {
+  int w = 1;
+  for (int k = 0; k < n; ++k) w = std::max(w, reduce_warps(hd[k]->nblk_rows));
+  return 32 * w;
+}
 
 BatchGrid grid_of(const FrameView& v, Kind k) { return BatchGrid{v.d_devs, v.tables[k].d_map}; }
 
@@ -126,7 +139,8 @@ void enqueue_frame_view(const FrameView& v, cudaStream_t st) {
       gj[t] = grid_of(v, (Kind)(kJtj1 + t));
       nj[t] = v.tables[kJtj1 + t].n;
     }
-    launch_normal_equations_b(gj, nj, grid_of(v, kReduce), v.tables[kReduce].n, L, v.precision, cur, it, st);
+    launch_normal_equations_b(gj, nj, grid_of(v, kReduce), v.tables[kReduce].n, L, v.precision, cur, it, st,
+                              v.reduce_threads);
     launch_lm_b(grid_of(v, kLm), v.tables[kLm].n, grid_of(v, kRows), v.tables[kRows].n, L, cur, st);
   }
   for (int it = 0; it < S; ++it) {
@@ -158,6 +172,7 @@ FrameView view_of(const trk_batch* b, const std::vector<const Dev*>& host_devs) 
   v.d_tiles = b->d_tiles;
   v.d_srcs = b->d_srcs;
   v.host_devs = host_devs.data();
+  v.reduce_threads = reduce_threads_for(host_devs.data(), v.B);
   return v;
 }
 
@@ -314,7 +329,8 @@ __global__ void __launch_bounds__(256) k_results_b(BatchGrid g, const ResultDst*
 }
 
 struct BatchStep {
-  char* d_buf = nullptr;  // device: [upload part | ctl, prefix, tiles]
+  VmmBlock d_block;       // device: [upload part | ctl, prefix, tiles]
+  char* d_buf = nullptr;
   char* h_buf = nullptr;  // pinned mirror of the upload part
   size_t d_cap = 0, h_cap = 0;
   cudaEvent_t uploaded = nullptr;  // the last upload out of h_buf has been done
@@ -332,8 +348,8 @@ BatchStep* batch_step_create() {
 void batch_step_destroy(BatchStep* bs, cudaStream_t st) {
   if (!bs) return;
   cudaEventSynchronize(bs->uploaded);
-  if (bs->d_buf) cudaFreeAsync(bs->d_buf, st);
   cudaStreamSynchronize(st);
+  vmm_free(&bs->d_block);
   if (bs->h_buf) cudaFreeHost(bs->h_buf);
   cudaEventDestroy(bs->uploaded);
   delete bs;
@@ -342,6 +358,21 @@ void batch_step_destroy(BatchStep* bs, cudaStream_t st) {
 namespace {
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 }  // namespace
+
+// Device bytes one session adds to a step's buffer: its descriptor, pointers, block-table entries and
+// tiles (each region 16-byte aligned, hence the slack).
+size_t batch_step_bytes_of(const trk_session* s) {
+  const Dev& d = session_dev(s);
+  size_t n = sizeof(Dev) + sizeof(float*) + sizeof(ResultDst) + sizeof(unsigned) + 16 * (kKinds + 4);
+  for (int k = 0; k < kKinds; ++k) {
+    int gx = 0, gy = 0;
+    blocks_of(d, (Kind)k, gx, gy);
+    n += sizeof(int4) * (size_t)gx * gy;
+  }
+  int gx = 0, gy = 0;
+  blocks_of(d, kAssoc, gx, gy);
+  return n + sizeof(int4) * (size_t)gx * gy;  // the step's list of occupied tiles
+}
 
 trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const float* const* srcs,
                              const ResultDst* dst, cudaStream_t st) {
@@ -386,14 +417,21 @@ trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const
   const size_t total = off;
   // the previous upload out of the pinned mirror has been done
   cudaError_t e = cudaEventSynchronize(bs->uploaded);
-  if (e == cudaSuccess && total > bs->d_cap) {  // grow (stream-ordered: no device-wide synchronisation)
-    if (bs->d_buf) e = cudaFreeAsync(bs->d_buf, st);
+  // remade at this step's size (rounded to the allocation granularity) when it needs more, or less than
+  // half, so that the buffer holds at most twice what a step of these sessions needs; the slot's last step
+  // has completed, so the old block is idle
+  if (e == cudaSuccess && (total > bs->d_cap || 2 * total < bs->d_cap)) {
+    e = cudaStreamSynchronize(st);
+    vmm_free(&bs->d_block);
     bs->d_buf = nullptr;
     bs->d_cap = 0;
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&bs->d_buf), 2 * total, st);
-    if (e == cudaSuccess) bs->d_cap = 2 * total;
+    if (e == cudaSuccess) e = vmm_alloc(total, &bs->d_block);
+    if (e == cudaSuccess) {
+      bs->d_buf = static_cast<char*>(bs->d_block.ptr);
+      bs->d_cap = bs->d_block.size;
+    }
   }
-  if (e == cudaSuccess && upload > bs->h_cap) {
+  if (e == cudaSuccess && upload > bs->h_cap) {  // pinned host memory: grown only
     if (bs->h_buf) cudaFreeHost(bs->h_buf);
     bs->h_buf = nullptr;
     bs->h_cap = 0;
@@ -432,6 +470,7 @@ trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const
   v.d_tiles = reinterpret_cast<int4*>(dbuf + o_tiles);
   v.d_srcs = reinterpret_cast<const float* const*>(dbuf + o_srcs);
   v.host_devs = hd.data();
+  v.reduce_threads = reduce_threads_for(hd.data(), n);
   enqueue_frame_view(v, st);
   const int nv = v.tables[kVerts].n;
   if (nv > 0)
@@ -527,11 +566,12 @@ trk_status trk_batch_profile(trk_batch* b, const float* const* d_depths, int32_t
       });
     if (!err)
       err = timed(TRK_STAGE_RESID_JTJ, [&] {
-        launch_normal_equations_b(gj, nj, grid_of(b, kReduce), 0, L, b->precision, 0, -1, st);
+        launch_normal_equations_b(gj, nj, grid_of(b, kReduce), 0, L, b->precision, 0, -1, st, 1024);
       });
     if (!err)
       err = timed(TRK_STAGE_REDUCE, [&] {
-        launch_normal_equations_b(gj, nz, grid_of(b, kReduce), b->tables[kReduce].n, L, b->precision, 0, -1, st);
+        launch_normal_equations_b(gj, nz, grid_of(b, kReduce), b->tables[kReduce].n, L, b->precision, 0, -1, st,
+                                  reduce_threads_of(b));
       });
     if (!err) err = timed(TRK_STAGE_LM_SOLVE, [&] { launch_lm_b(grid_of(b, kLm), b->tables[kLm].n, grid_of(b, kRows), 0, L, 0, st); });
     if (!err) err = timed(TRK_STAGE_LM_EVAL, [&] { launch_lm_b(grid_of(b, kLm), 0, grid_of(b, kRows), b->tables[kRows].n, L, 0, st); });

@@ -50,7 +50,6 @@ __device__ __forceinline__ void skin_impl(const Dev& d, BlockPos bp, int phi_buf
     d.stats[1] = 0;
     d.qctl[0] = 0;
     d.qctl[1] = 0;
-    d.qctl[3] = 0;  // the association's next tile (the tile list itself is the frame's)
   }
   const float4* phi = d.phi[phi_buf];
   for (int i = tid; i < d.V; i += stride) {
@@ -235,7 +234,7 @@ void launch_visibility(const Dev& d, cudaStream_t st) {
 // loaded together.  Pixels still open after that (the bound of ring 1 is ~4 mm at 2-3 m: pixels whose
 // nearest vertex is farther, in the first iterations of a frame, at silhouettes and where vertices are
 // sparse) go to a queue that the tail kernels drain with a group of lanes per pixel (a warp for one session,
-// 8 lanes in a batch), the lanes splitting each ring's 8r buckets and combining (d^2, index) keys with a
+// 4 lanes in a batch), the lanes splitting the next rings' buckets and combining (d^2, index) keys with a
 // group min.
 // The pixel's offset p - v_i is added to the vertex's fixed-point sums (integer atomics: the sums do
 // not depend on the order of the additions).
@@ -371,7 +370,9 @@ __device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
 
 
 constexpr int kTailWarps = 8;
-constexpr int kTailPerLane = 4;  // buckets a lane loads at once
+constexpr int kTailPerLane = 4;       // buckets a lane loads at once (one session: a warp per pixel)
+constexpr int kBatchTailLanes = 4;    // a batch's tail: lanes per queued pixel ...
+constexpr int kBatchTailPerLane = 8;  // ... and buckets each of them loads at once
 
 // The rings beyond the thread-owned ones for queue entry `item` of session d, by a group of GL lanes (lanes
 // gl = lane % GL of the group starting at lane gbase, gmask naming them): the lanes split each
@@ -379,8 +380,8 @@ constexpr int kTailPerLane = 4;  // buckets a lane loads at once
 // combine (d^2, index) keys with a group min.  Returns, in every lane of the group, whether the pixel got a
 // correspondence (its first lane writes it and adds the pixel's sums).
 // One session's tail takes a warp per pixel (its queue is short and its latency is the slowest pixel's
-// rings); a batch's takes 8 lanes per pixel (four pixels per warp: throughput over many queues).
-template <int GL>
+// rings); a batch's takes 4 lanes per pixel (eight pixels per warp: throughput over many queues).
+template <int GL, int PL>
 __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, unsigned gmask) {
   const Cam c = d.cam;
   const float tau2 = c.tau * c.tau;
@@ -393,19 +394,19 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
   float wd2 = 0.f;
   // rings r0..r1 at a time, as many whole rings as the group's load slots hold (at least one): scanning
   // rings past the one whose bound ends the search only confirms the argmin, so the result is the same
-  constexpr int kSlots = GL * kTailPerLane;
+  constexpr int kSlots = GL * PL;
   for (int r0 = kRingsPerThread + 1; r0 <= c.R;) {
     int r1 = r0, nb = 8 * r0;
     while (r1 < c.R && nb + 8 * (r1 + 1) <= kSlots) nb += 8 * ++r1;
     for (int t0 = 0; t0 < nb; t0 += kSlots) {
-      int q[kTailPerLane];
+      int q[PL];
 #pragma unroll
-      for (int u = 0; u < kTailPerLane; ++u) {
+      for (int u = 0; u < PL; ++u) {
         int t = t0 + gl + GL * u, r = r0;
         while (t < nb && t >= 8 * r) t -= 8 * r++;  // bucket t of the group: ring r, position t
         q[u] = t0 + gl + GL * u < nb ? ring_bucket(px, py, r, t, c.W, c.H) : -1;
       }
-      scan_group<kTailPerLane>(d, q, p, tau2, wb, wd2);
+      scan_group<PL>(d, q, p, tau2, wb, wd2);
     }
     unsigned long long kk = key_of(wb, wd2);
     kk = kk < key ? kk : key;
@@ -431,34 +432,25 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
 // (listed by the depth gather) from a shared counter, reloading the session descriptor when the session
 // changes; pixels of empty tiles keep the "no correspondence" the skinning pass wrote.
 __global__ void __launch_bounds__(kBlock, 4) k_associate(const Dev* devs, const int4* tiles, unsigned* ctl, Dev d0) {
-  __shared__ int4 s_t;
-  if (devs == nullptr) {  // one session: persistent blocks over the frame's occupied tiles
-    const unsigned n = d0.qctl[2];
-    for (;;) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned i = atomicAdd(&d0.qctl[3], 1u);
-        s_t = i < n ? d0.tiles[i] : make_int4(-1, 0, 0, 0);
-      }
-      __syncthreads();
-      const int4 t = s_t;
-      if (t.x < 0) return;
+  // each block takes a contiguous share of the occupied tiles (no shared counter, so no atomic round trip
+  // per tile, and a share mostly within one session)
+  const unsigned n = devs == nullptr ? d0.qctl[2] : ctl[0];
+  const unsigned lo = (unsigned)(((unsigned long long)n * blockIdx.x) / gridDim.x);
+  const unsigned hi = (unsigned)(((unsigned long long)n * (blockIdx.x + 1)) / gridDim.x);
+  const int4* list = devs == nullptr ? d0.tiles : tiles;
+  if (devs == nullptr) {  // one session
+    for (unsigned i = lo; i < hi; ++i) {
+      const int4 t = list[i];
       associate_impl(d0, BlockPos{t.y, t.z, t.w});
     }
+    return;
   }
   __shared__ Dev sd;
   int cur = -1;
-  const unsigned n = ctl[0];
-  for (;;) {
-    __syncthreads();  // the previous tile is done (s_t, sd free)
-    if (threadIdx.x == 0) {
-      const unsigned i = atomicAdd(&ctl[1], 1u);
-      s_t = i < n ? tiles[i] : make_int4(-1, 0, 0, 0);
-    }
-    __syncthreads();
-    const int4 t = s_t;
-    if (t.x < 0) break;
-    if (t.x != cur) {
+  for (unsigned i = lo; i < hi; ++i) {
+    const int4 t = list[i];
+    if (t.x != cur) {  // a tile of another session: its descriptor, once every thread is done with the last
+      __syncthreads();
       const int* src = reinterpret_cast<const int*>(devs + t.x);
       for (int q = threadIdx.x; q < (int)(sizeof(Dev) / 4); q += blockDim.x) reinterpret_cast<int*>(&sd)[q] = src[q];
       cur = t.x;
@@ -479,7 +471,7 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
     if (gl == 0) item = atomicAdd(&d.qctl[1], 1u);
     item = __shfl_sync(gmask, item, gbase);
     if (item >= n) break;
-    done += tail_item<32>(d, item, gl, gmask);
+    done += tail_item<32, kTailPerLane>(d, item, gl, gmask);
   }
   if (gl == 0 && done) atomicAdd(&d.stats[0], done);
 }
@@ -515,7 +507,7 @@ __global__ void __launch_bounds__(1024) k_tail_prefix(const Dev* devs, int n_ses
 // entry's session is found in the prefix and its descriptor read through the cache.
 __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const Dev* devs, int n_sessions,
                                                                           const unsigned* prefix, unsigned* ctl) {
-  constexpr int GL = 8;
+  constexpr int GL = kBatchTailLanes;
   const int lane = threadIdx.x & 31, gl = lane % GL, gbase = lane - gl;
   const unsigned gmask = ((1u << GL) - 1u) << gbase;
   const unsigned total = prefix[n_sessions];
@@ -530,7 +522,7 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const 
       if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
     }
     const Dev& d = devs[lo];
-    if (tail_item<GL>(d, item - prefix[lo], gl, gmask) && gl == 0) atomicAdd(&d.stats[0], 1);
+    if (tail_item<GL, kBatchTailPerLane>(d, item - prefix[lo], gl, gmask) && gl == 0) atomicAdd(&d.stats[0], 1);
   }
 }
 

@@ -280,10 +280,7 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
 #pragma unroll
       for (int b = 0; b < T; ++b) {
         const int r = ty * T + a, c = tx * T + b;
-        if (r < NP && c < NP) {
-          out[r * NP + c] = acc[a][b];
-          out[c * NP + r] = acc[a][b];
-        }
+        if (r < NP && c < NP && r <= c) out[r * NP + c] = acc[a][b];  // the upper triangle (the reduction mirrors)
       }
   }
   if (tid == 0) {
@@ -326,57 +323,74 @@ __device__ __forceinline__ void resid_jtj_tc_impl(const Dev& d, BlockPos bp, int
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int NP = d.NP;
-  RowSlot rs;
-  const int total = block_rows(d, bp.x, bp.x * kBlock, phi_buf, s_warp, rs);  // jtj_group is 1 here
-  if (total == 0) {  // nothing to add: no TMEM is taken and the reduction skips this block
+  const int NP = d.NP, G = d.jtj_group;
+  // The rows of the block's G vertex blocks go into the same TMEM accumulator, chunk after chunk; the
+  // tensor memory is taken when the first rows appear (a block without rows takes none).
+  int done = 0, gq = 0;  // rows added, chunks issued
+  float E = 0.f;
+  bool ok = true, taken = false;
+  uint32_t tmem = 0;
+  const uint32_t idesc = tc::instr_desc(tc::Split<PREC>::fmt, tc::kRows, N);
+  const uint32_t hi = tc::smem_u32(tiles);
+  for (int sub = 0; sub < G; ++sub) {
+    const int vb = bp.x * G + sub;
+    if (vb * kBlock >= d.V) break;
+    RowSlot rs;
+    const int total = block_rows(d, vb, bp.x * kBlock * G + done, phi_buf, s_warp, rs);
+    if (total == 0) {
+      __syncthreads();  // s_warp is rewritten by the next vertex block
+      continue;
+    }
+    if (!taken) {
+      tc::zero_padding<PREC, TL::CH, kBlock>(tiles, 2, NP);
+      if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+      }
+      if (w == 0) tc::tmem_alloc(&tslot, tc::kTmemCols);
+      load_link_tables(d, sHd, sXi, sPar);
+      taken = true;
+    }
+    __syncthreads();
+    float r2;
+    jacobian_row(d, rs, phi_buf, Js, ROW, NP, sHd, sXi, sPar, r2);
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if (lane == 0) s_e[w] = r2;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tmem = tslot;
+    for (int k = 0; k < kBlock / 32; ++k) E += s_e[k];
+    const int nchunks = (total + TL::K - 1) / TL::K;
+    for (int q = 0; q < nchunks; ++q, ++gq) {
+      if (gq > 0) {  // the previous chunk's MMAs read the tiles
+        ok &= tc::mbar_wait(&bar, (gq - 1) & 1);
+        tc::fence_proxy_async();
+      }
+      const int base = q * TL::K, cnt = min(TL::K, total - base);
+      const int kq = (cnt + 2 * T - 1) / (2 * T) * (2 * T);
+      const float* blk = Js + base * ROW;
+      tc::stage_chunk<PREC, TL::CH, kBlock>([&](int k, int m) { return k < cnt ? blk[k * ROW + m] : 0.f; }, kq, NP,
+                                            tiles);
+      tc::fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        tc::issue_chunk<PREC, TL::CH>(tmem, hi, hi + TL::BYTES, kq / (2 * T), idesc, gq == 0);
+        tc::commit(&bar);
+      }
+    }
+    done += total;
+  }
+  if (!taken) {  // nothing to add: no TMEM was taken and the reduction skips this block
     if (tid == 0) d.jtj_rows[bp.x] = 0;
     return;
   }
-  tc::zero_padding<PREC, TL::CH, kBlock>(tiles, 2, NP);
-  if (tid == 0) {
-    tc::mbar_init(&bar, 1);
-    tc::fence_mbar_init();
-  }
-  if (w == 0) tc::tmem_alloc(&tslot, tc::kTmemCols);
-  load_link_tables(d, sHd, sXi, sPar);
-  __syncthreads();
-  float r2;
-  jacobian_row(d, rs, phi_buf, Js, ROW, NP, sHd, sXi, sPar, r2);
-  for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-  if (lane == 0) s_e[w] = r2;
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = tslot;
-  const uint32_t idesc = tc::instr_desc(tc::Split<PREC>::fmt, tc::kRows, N);
-  const uint32_t hi = tc::smem_u32(tiles);
-  const int nchunks = (total + TL::K - 1) / TL::K;
-  bool ok = true;
-  for (int q = 0; q < nchunks; ++q) {
-    if (q > 0) {  // the previous chunk's MMAs read the tiles
-      ok &= tc::mbar_wait(&bar, (q - 1) & 1);
-      tc::fence_proxy_async();
-    }
-    const int base = q * TL::K, cnt = min(TL::K, total - base);
-    const int kq = (cnt + 2 * T - 1) / (2 * T) * (2 * T);
-    const float* blk = Js + base * ROW;
-    tc::stage_chunk<PREC, TL::CH, kBlock>([&](int k, int m) { return k < cnt ? blk[k * ROW + m] : 0.f; }, kq, NP,
-                                          tiles);
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      tc::issue_chunk<PREC, TL::CH>(tmem, hi, hi + TL::BYTES, kq / (2 * T), idesc, q == 0);
-      tc::commit(&bar);
-    }
-  }
+  const int nchunks = gq;
   if (nchunks > 0) {
     ok &= tc::mbar_wait(&bar, (nchunks - 1) & 1);
     tc::fence_after_sync();
   }
-  float E = 0.f;
-  for (int k = 0; k < kBlock / 32; ++k) E += s_e[k];
   // warps w and w + 4 read the same 32 TMEM lanes (parameters a), alternate 8-column groups (b)
   float* out = d.partial + (size_t)bp.x * NP * NP;
   const int a = 32 * (w & 3) + lane;
@@ -390,7 +404,8 @@ __device__ __forceinline__ void resid_jtj_tc_impl(const Dev& d, BlockPos bp, int
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int b = 8 * g + t;
-      if (a < NP && b < NP) out[b * NP + a] = (a == NP - 1 && b == NP - 1) ? E : (ok ? __uint_as_float(r[t]) : bad);
+      if (a < NP && b < NP && a <= b)  // the upper triangle (the reduction mirrors)
+        out[a * NP + b] = (a == NP - 1 && b == NP - 1) ? E : (ok ? __uint_as_float(r[t]) : bad);
     }
   }
   if (!ok && tid == 0) {
@@ -404,8 +419,8 @@ __device__ __forceinline__ void resid_jtj_tc_impl(const Dev& d, BlockPos bp, int
     tc::tmem_dealloc(tmem, tc::kTmemCols);
   }
   if (tid == 0) {
-    d.jtj_rows[bp.x] = total;
-    atomicAdd(&d.stats[1], total);
+    d.jtj_rows[bp.x] = done;
+    atomicAdd(&d.stats[1], done);
   }
 }
 
@@ -440,35 +455,46 @@ __device__ __forceinline__ void sum2_add(float& hi, float& lo, float x) {
 __device__ __forceinline__ void reduce_jtj_impl(const Dev& d, BlockPos bp, int slot) {
   __shared__ double sm[kReduceThreads / 32][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int NP = d.NP, n2 = NP * NP;
-  const int e = bp.x * 32 + lane;
-  // warp w takes blocks w, w + 32, ... (four loads in flight together); blocks that added no rows wrote
-  // no partial and count as zero
-  constexpr int S = kReduceThreads / 32;
+  const int NP = d.NP, n2 = NP * NP, nu = NP * (NP + 1) / 2;
+  // lane -> the u-th entry of the upper triangle, row-major: (r, c), r <= c, at e = r NP + c
+  const int u = bp.x * 32 + lane;
+  int r = 0, c = 0;
+  if (u < nu) {
+    int rest = u;
+    while (rest >= NP - r) rest -= NP - r++;
+    c = r + rest;
+  }
+  const int e = r * NP + c;
+  // warp w < S takes blocks w, w + S, ... (four loads in flight together, each partial loaded with its row
+  // count rather than after it); blocks that added no rows wrote no partial and count as zero.  S depends
+  // on the session alone, so its sums have the same order in any launch.
   const int nb = d.nblk_rows;
+  const int S = reduce_warps(nb);
   float hi = 0.f, lo = 0.f;
-  if (e < n2) {
+  if (u < nu && w < S) {
     int b = w;
     for (; b + 3 * S < nb; b += 4 * S) {
       const int r0 = d.jtj_rows[b], r1 = d.jtj_rows[b + S], r2 = d.jtj_rows[b + 2 * S], r3 = d.jtj_rows[b + 3 * S];
-      const float p0 = r0 > 0 ? d.partial[(size_t)b * n2 + e] : 0.f;
-      const float p1 = r1 > 0 ? d.partial[(size_t)(b + S) * n2 + e] : 0.f;
-      const float p2 = r2 > 0 ? d.partial[(size_t)(b + 2 * S) * n2 + e] : 0.f;
-      const float p3 = r3 > 0 ? d.partial[(size_t)(b + 3 * S) * n2 + e] : 0.f;
-      sum2_add(hi, lo, p0);
-      sum2_add(hi, lo, p1);
-      sum2_add(hi, lo, p2);
-      sum2_add(hi, lo, p3);
+      const float q0 = d.partial[(size_t)b * n2 + e], q1 = d.partial[(size_t)(b + S) * n2 + e];
+      const float q2 = d.partial[(size_t)(b + 2 * S) * n2 + e], q3 = d.partial[(size_t)(b + 3 * S) * n2 + e];
+      sum2_add(hi, lo, r0 > 0 ? q0 : 0.f);
+      sum2_add(hi, lo, r1 > 0 ? q1 : 0.f);
+      sum2_add(hi, lo, r2 > 0 ? q2 : 0.f);
+      sum2_add(hi, lo, r3 > 0 ? q3 : 0.f);
     }
-    for (; b < nb; b += S)
-      if (d.jtj_rows[b] > 0) sum2_add(hi, lo, d.partial[(size_t)b * n2 + e]);
+    for (; b < nb; b += S) {
+      const int rows = d.jtj_rows[b];
+      const float q = d.partial[(size_t)b * n2 + e];
+      if (rows > 0) sum2_add(hi, lo, q);
+    }
   }
   sm[w][lane] = (double)hi + (double)lo;
   __syncthreads();
-  if (w != 0 || e >= n2) return;
+  if (w != 0 || u >= nu) return;
   double t = 0.0;
-  for (int k = 0; k < kReduceThreads / 32; ++k) t += sm[k][lane];
+  for (int k = 0; k < S; ++k) t += sm[k][lane];
   d.A[e] = t;
+  d.A[c * NP + r] = t;  // A is symmetric: the lower triangle mirrors the upper
   if (e == n2 - 1) {
     double E = t;
     for (int k = 0; k < d.L; ++k) E += d.prior2[k] * d.theta[k] * d.theta[k];
@@ -534,8 +560,7 @@ void launch_resid_jtj(const Dev& d, int phi_buf, cudaStream_t st) {
 }
 
 void launch_reduce_jtj(const Dev& d, int slot, cudaStream_t st) {
-  const int n2 = d.NP * d.NP;
-  k_reduce_jtj<<<(n2 + 31) / 32, kReduceThreads, 0, st>>>(kSingle, d, slot);
+  k_reduce_jtj<<<(d.NP * (d.NP + 1) / 2 + 31) / 32, 32 * reduce_warps(d.nblk_rows), 0, st>>>(kSingle, d, slot);
 }
 
 void launch_normal_equations(const Dev& d, int phi_buf, int slot, cudaStream_t st) {
@@ -1470,7 +1495,7 @@ static void launch_resid_jtj_tc_b(const BatchGrid& g, int nblk, int max_np, int 
 // gj[t - 1], nj[t - 1]: the blocks of the sessions whose [J r] tile width class is t = ceil(NP / 16)
 // (one launch per class, so a small skeleton does not pay for the largest one's tiles).
 void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGrid& gr, int nr, int max_links,
-                               int precision, int phi_buf, int slot, cudaStream_t st) {
+                               int precision, int phi_buf, int slot, cudaStream_t st, int reduce_threads) {
   for (int T = 1; T <= 5; ++T) {
     const BatchGrid& g = gj[T - 1];
     const int n = nj[T - 1];
@@ -1490,7 +1515,7 @@ void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGr
       }
     }
   }
-  if (nr > 0) k_reduce_jtj<<<nr, kReduceThreads, 0, st>>>(gr, Dev{}, slot);
+  if (nr > 0) k_reduce_jtj<<<nr, reduce_threads, 0, st>>>(gr, Dev{}, slot);
 }
 
 void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int max_links, int phi_buf,

@@ -115,7 +115,8 @@ struct SessionSlot {
   std::deque<Request*> pending;
   Request* inflight = nullptr;
   std::vector<Staging*> spare;  // staging of collected frames, ready for reuse
-  size_t bytes = 0;             // device bytes counted against the budget
+  size_t bytes = 0;             // the session's arena, counted against the budget
+  size_t step_bytes = 0;        // its tables in a batched step
   bool restored = false;        // made resident at attach (evicted again at detach)
   bool batchable = false;       // tracking mode: may join batched steps
   uint64_t key = 0;             // sessions with equal keys may share a batched step
@@ -124,7 +125,10 @@ struct SessionSlot {
 }  // namespace
 
 struct trk_server {
-  size_t budget = 0, used = 0;
+  size_t budget = 0, used = 0;      // used: arena_used + the step buffers' reservation
+  size_t arena_used = 0;            // the arenas of the attached (and attaching) sessions
+  size_t step_sum = 0, step_peak = 0;  // their step-table bytes now, and the most there have been
+  size_t gran = 2 << 20;            // the device's allocation granularity
   int max_inflight = 0, device = 0;
   int dispatch = TRK_SERVER_DISPATCH_BATCHED;
   int max_batch = 64, n_slots = 2;
@@ -385,6 +389,14 @@ void worker_loop(trk_server* sv) {
   }
 }
 
+// What the batched step slots may hold: each slot's buffer is at most twice its step's tables (rounded up
+// to the granularity), a step's sessions are attached ones, and the reservation never shrinks (a slot
+// keeps its buffer until a smaller step remakes it).
+size_t step_reserve(const trk_server* sv, size_t step_sum) {
+  if (sv->dispatch != TRK_SERVER_DISPATCH_BATCHED || step_sum == 0) return 0;
+  return (size_t)sv->n_slots * ((2 * step_sum + sv->gran - 1) / sv->gran * sv->gran);
+}
+
 uint64_t class_key(const trk_params& p) {
   uint64_t k = (uint64_t)p.pose_iters;
   for (int v : {p.shape_iters, p.shape_sweeps, p.precision, p.shape_solver, p.association, p.mode})
@@ -402,6 +414,7 @@ trk_status trk_server_create(size_t hbm_budget_bytes, int32_t max_inflight, trk_
   sv->budget = hbm_budget_bytes;
   sv->max_inflight = max_inflight;
   cudaGetDevice(&sv->device);
+  if (const size_t g = trk::vmm_granularity()) sv->gran = g;
   sv->worker = std::thread(worker_loop, sv);
   *out = sv;
   return TRK_OK;
@@ -426,15 +439,23 @@ trk_status trk_server_attach(trk_server* sv, trk_session* s) {
   if (!sv || !s) return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_attach: NULL argument");
   if (trk::session_device(s) != sv->device)
     return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_attach: session is on another device");
-  const size_t need = trk::session_device_bytes(s);
+  const size_t arena = trk::session_device_bytes(s);
+  size_t steps = 0;
   const bool was_resident = trk::session_resident(s);
   {
     std::lock_guard<std::mutex> lk(sv->mu);
+    // the session's arena, and the batched steps' buffers with its tables among theirs
+    const bool batched = sv->dispatch == TRK_SERVER_DISPATCH_BATCHED && trk::session_params(s).mode == TRK_MODE_TRACK;
+    steps = batched ? trk::batch_step_bytes_of(s) : 0;
     if (sv->sessions.count(s) || sv->attaching.count(s))
       return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_attach: already attached");
-    if (sv->used + need > sv->budget)
+    const size_t peak = std::max(sv->step_peak, sv->step_sum + steps);
+    if (sv->arena_used + arena + step_reserve(sv, peak) > sv->budget)
       return trk::set_error(TRK_ERR_NO_CAPACITY, "trk_server_attach: the session does not fit the HBM budget");
-    sv->used += need;  // reserved while the device state is made
+    sv->arena_used += arena;  // reserved while the device state is made
+    sv->step_sum += steps;
+    sv->step_peak = peak;
+    sv->used = sv->arena_used + step_reserve(sv, sv->step_peak);
     sv->attaching[s] = true;
     if (sv->dispatch == TRK_SERVER_DISPATCH_BATCHED && sv->slots.empty()) {
       for (int k = 0; k < sv->n_slots; ++k) {
@@ -449,7 +470,9 @@ trk_status trk_server_attach(trk_server* sv, trk_session* s) {
         sv->slots.push_back(st);
       }
       if (sv->slots.empty()) {
-        sv->used -= need;
+        sv->arena_used -= arena;
+        sv->step_sum -= steps;
+        sv->used = sv->arena_used + step_reserve(sv, sv->step_peak);
         sv->attaching.erase(s);
         return trk::set_error(TRK_ERR_CUDA, "trk_server_attach: step stream creation failed");
       }
@@ -459,11 +482,14 @@ trk_status trk_server_attach(trk_server* sv, trk_session* s) {
   std::lock_guard<std::mutex> lk(sv->mu);
   sv->attaching.erase(s);
   if (e != TRK_OK) {
-    sv->used -= need;
+    sv->arena_used -= arena;
+    sv->step_sum -= steps;
+    sv->used = sv->arena_used + step_reserve(sv, sv->step_peak);
     return e;
   }
   SessionSlot& sl = sv->sessions[s];
-  sl.bytes = need;
+  sl.bytes = arena;
+  sl.step_bytes = steps;
   sl.restored = !was_resident;
   const trk_params& p = trk::session_params(s);
   sl.batchable = p.mode == TRK_MODE_TRACK;
@@ -474,7 +500,7 @@ trk_status trk_server_attach(trk_server* sv, trk_session* s) {
 trk_status trk_server_detach(trk_server* sv, trk_session* s) {
   if (!sv || !s) return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_detach: NULL argument");
   bool evict = false;
-  size_t bytes = 0;
+  size_t bytes = 0, steps = 0;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     auto it = sv->sessions.find(s);
@@ -485,6 +511,7 @@ trk_status trk_server_detach(trk_server* sv, trk_session* s) {
     for (Step* st : sv->slots) trk::session_forget_stream(s, st->st);  // its frames there are done
     evict = it->second.restored;
     bytes = it->second.bytes;
+    steps = it->second.step_bytes;
     sv->sessions.erase(it);
     sv->attaching[s] = true;  // until its device state is gone, the budget still holds it
   }
@@ -492,7 +519,9 @@ trk_status trk_server_detach(trk_server* sv, trk_session* s) {
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->attaching.erase(s);
-    sv->used -= bytes;
+    sv->arena_used -= bytes;
+    sv->step_sum -= steps;
+    sv->used = sv->arena_used + step_reserve(sv, sv->step_peak);
   }
   signal_work(sv);
   return e;
@@ -610,6 +639,7 @@ trk_status trk_server_get_stats(trk_server* sv, trk_server_stats* out) {
   out->latency_p99_us = sv->lat.percentile(0.99);
   out->latency_max_us = sv->lat.max_us;
   out->steps = sv->steps;
+  out->device_bytes_reserved = trk::vmm_bytes_held();
   out->mean_frames_per_step = sv->steps ? (double)sv->frames_in_steps / (double)sv->steps : 0.0;
   return TRK_OK;
 }

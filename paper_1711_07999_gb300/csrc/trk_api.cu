@@ -6,8 +6,12 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
+
+#include <cuda.h>
 
 #include "../../include/trk.h"
 #include "trk_internal.cuh"
@@ -111,6 +115,119 @@ void knn_grid(int V, const float* xyz, int K, std::vector<int>& nbr) {
 
 }  // namespace
 
+namespace {
+// the driver's virtual memory management calls, looked up through the runtime (no link to libcuda)
+struct VmmApi {
+  decltype(&cuMemGetAllocationGranularity) granularity = nullptr;
+  decltype(&cuMemCreate) create = nullptr;
+  decltype(&cuMemRelease) release = nullptr;
+  decltype(&cuMemAddressReserve) reserve = nullptr;
+  decltype(&cuMemAddressFree) address_free = nullptr;
+  decltype(&cuMemMap) map = nullptr;
+  decltype(&cuMemUnmap) unmap = nullptr;
+  decltype(&cuMemSetAccess) set_access = nullptr;
+  bool ok = false;
+};
+std::mutex g_vmm_mu;
+VmmApi g_vmm;
+bool g_vmm_loaded = false;
+std::atomic<size_t> g_vmm_held{0};
+
+template <typename F>
+bool entry(const char* name, F* fn) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !p)
+    return false;
+  *fn = reinterpret_cast<F>(p);
+  return true;
+}
+
+const VmmApi& vmm() {
+  std::lock_guard<std::mutex> lk(g_vmm_mu);
+  if (!g_vmm_loaded) {
+    g_vmm_loaded = true;
+    VmmApi a;
+    a.ok = entry("cuMemGetAllocationGranularity", &a.granularity) && entry("cuMemCreate", &a.create) &&
+           entry("cuMemRelease", &a.release) && entry("cuMemAddressReserve", &a.reserve) &&
+           entry("cuMemAddressFree", &a.address_free) && entry("cuMemMap", &a.map) &&
+           entry("cuMemUnmap", &a.unmap) && entry("cuMemSetAccess", &a.set_access);
+    g_vmm = a;
+  }
+  return g_vmm;
+}
+
+CUmemAllocationProp device_prop(int dev) {
+  CUmemAllocationProp prop{};
+  prop.type = CU_MEM_ALLOCATION_TYPE_PINNED;
+  prop.location.type = CU_MEM_LOCATION_TYPE_DEVICE;
+  prop.location.id = dev;
+  return prop;
+}
+}  // namespace
+
+size_t trk::vmm_granularity() {
+  const VmmApi& a = vmm();
+  int dev = 0;
+  if (!a.ok || cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const CUmemAllocationProp prop = device_prop(dev);
+  size_t g = 0;
+  if (a.granularity(&g, &prop, CU_MEM_ALLOC_GRANULARITY_MINIMUM) != CUDA_SUCCESS) return 0;
+  return g;
+}
+
+cudaError_t trk::vmm_alloc(size_t bytes, VmmBlock* out) {
+  const VmmApi& a = vmm();
+  if (!a.ok) return cudaErrorNotSupported;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const size_t g = vmm_granularity();
+  if (!g) return cudaErrorNotSupported;
+  const size_t size = (std::max<size_t>(bytes, 1) + g - 1) / g * g;
+  const CUmemAllocationProp prop = device_prop(dev);
+  CUmemGenericAllocationHandle h = 0;
+  if (a.create(&h, size, &prop, 0) != CUDA_SUCCESS) return cudaErrorMemoryAllocation;
+  CUdeviceptr ptr = 0;
+  if (a.reserve(&ptr, size, g, 0, 0) != CUDA_SUCCESS) {
+    a.release(h);
+    return cudaErrorMemoryAllocation;
+  }
+  CUmemAccessDesc acc{};
+  acc.location = prop.location;
+  acc.flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
+  if (a.map(ptr, size, 0, h, 0) != CUDA_SUCCESS) {
+    a.address_free(ptr, size);
+    a.release(h);
+    return cudaErrorMemoryAllocation;
+  }
+  if (a.set_access(ptr, size, &acc, 1) != CUDA_SUCCESS) {
+    a.unmap(ptr, size);
+    a.address_free(ptr, size);
+    a.release(h);
+    return cudaErrorMemoryAllocation;
+  }
+  out->ptr = reinterpret_cast<void*>(ptr);
+  out->size = size;
+  out->handle = (unsigned long long)h;
+  g_vmm_held += size;
+  return cudaSuccess;
+}
+
+void trk::vmm_free(VmmBlock* b) {
+  if (!b || !b->ptr) return;
+  const VmmApi& a = vmm();
+  const CUdeviceptr ptr = reinterpret_cast<CUdeviceptr>(b->ptr);
+  a.unmap(ptr, b->size);
+  a.address_free(ptr, b->size);
+  a.release((CUmemGenericAllocationHandle)b->handle);
+  g_vmm_held -= b->size;
+  *b = VmmBlock{};
+}
+
+size_t trk::vmm_bytes_held() { return g_vmm_held.load(); }
+
 int trk::set_error_code(int st, const char* msg) {
   g_err = msg ? msg : "";
   return st;
@@ -139,9 +256,10 @@ struct trk_session {
   HostModel hm;
   bool resident = false;    // the device state exists
   unsigned generation = 0;  // changes whenever the device state is made or freed
-  void* arena = nullptr;    // one stream-ordered allocation holding every device buffer of the session
+  void* arena = nullptr;    // one device block (vmm_alloc) holding every device buffer of the session
+  VmmBlock block;           // the block behind the arena
   size_t carved = 0;        // bytes of the arena handed out so far (or, without an arena, counted)
-  size_t device_bytes = 0;  // size of the arena
+  size_t device_bytes = 0;  // size of the arena: the carved bytes rounded up to the allocation granularity
   // the tracking state while the session is evicted: Theta, lambda, Phi
   std::vector<double> ev_theta;
   double ev_lam = 0.0;
@@ -200,8 +318,6 @@ trk_status validate(const trk_mesh* m, const trk_skeleton* k, const trk_intrinsi
     return fail(TRK_ERR_INVALID_ARG, "association %d not supported", p->association);
   if (p->jtj_group != 0 && p->jtj_group != 1 && p->jtj_group != 2 && p->jtj_group != 4)
     return fail(TRK_ERR_INVALID_ARG, "jtj_group %d not supported", p->jtj_group);
-  if (p->jtj_group > 1 && p->precision != TRK_PRECISION_FP32)
-    return fail(TRK_ERR_INVALID_ARG, "jtj_group > 1 needs precision FP32");
   if (p->pose_iters < 0 || p->shape_iters < 0 || p->shape_sweeps < 1 || p->knn < 0 || p->knn > 4 ||
       p->window_half_px < 0 || !(p->cutoff_m > 0) || !(p->lambda_k0 > 0) || p->lambda_s < 0 || p->lambda_phi < 0 ||
       p->lambda_N < 0 || p->lambda_w < 0 || !(p->z_near_m > 0) || !(p->eps_vis_m >= 0))
@@ -376,10 +492,7 @@ void trk_destroy(trk_session* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->graph_pose) cudaGraphExecDestroy(s->graph_pose);
-  if (s->arena) {
-    cudaFreeAsync(s->arena, s->stream);
-    cudaStreamSynchronize(s->stream);
-  }
+  if (s->arena) vmm_free(&s->block);  // the streams above are idle
   if (s->h_pinned) cudaFreeHost(s->h_pinned);
   if (s->h_phi) cudaFreeHost(s->h_phi);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -446,32 +559,31 @@ void carve_all(trk_session* s) {
   d.adj = dadj;
 }
 
-// Makes the device state: one arena from the stream-ordered allocator, the model data uploaded from the
+// Makes the device state: one arena (a device block of vmm_alloc), the model data uploaded from the
 // host copy, the work buffers initialised and the tracking state (Theta, lambda, Phi) restored.
 trk_status materialize(trk_session* s) {
   if (s->resident) return TRK_OK;
   carve_all(s);  // sizing pass (no arena yet)
   const size_t bytes = s->carved;
-  cudaError_t e = cudaMallocAsync(&s->arena, bytes, s->stream);
-  if (e != cudaSuccess) {
-    s->arena = nullptr;
+  cudaError_t e = vmm_alloc(bytes, &s->block);
+  if (e != cudaSuccess)
     return fail(e == cudaErrorMemoryAllocation ? TRK_ERR_OOM : TRK_ERR_CUDA, "device state of %zu bytes: %s", bytes,
                 cudaGetErrorString(e));
-  }
+  s->arena = s->block.ptr;
   struct Undo {
     trk_session* s;
     bool armed = true;
     ~Undo() {
       if (!armed) return;
-      cudaFreeAsync(s->arena, s->stream);
       cudaStreamSynchronize(s->stream);
+      vmm_free(&s->block);
       s->arena = nullptr;
       carve_all(s);
     }
   } undo{s};
   if (reinterpret_cast<uintptr_t>(s->arena) % 256 != 0)
     return fail(TRK_ERR_CUDA, "device state allocation not 256-byte aligned");
-  s->device_bytes = bytes;
+  s->device_bytes = s->block.size;
   carve_all(s);
   Dev& d = s->d;
   const HostModel& hm = s->hm;
@@ -523,8 +635,7 @@ trk_status evict(trk_session* s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
   if (s->graph_pose) cudaGraphExecDestroy(s->graph_pose);
   s->graph = s->graph_pose = nullptr;
-  CK(cudaFreeAsync(s->arena, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  vmm_free(&s->block);  // the memory is back on the device when the eviction returns
   s->arena = nullptr;
   carve_all(s);  // every device pointer back to NULL
   s->resident = false;
@@ -709,7 +820,6 @@ trk_status create_session(const trk_mesh* mesh, const trk_skeleton* sk, const tr
   // ---- [J r] block grouping ---------------------------------------------------------------------
   d.nblk_jtj = (V + 255) / 256;
   d.jtj_group = prm->jtj_group;
-  if (d.jtj_group == 0 && prm->precision != TRK_PRECISION_FP32) d.jtj_group = 1;
   if (d.jtj_group == 0) {
     // by mesh size (fewer, fuller blocks for large meshes) and by the expected rows per 256 vertices:
     // about one vertex per covered pixel gets a correspondence and about half of those face the camera,
@@ -736,7 +846,11 @@ trk_status create_session(const trk_mesh* mesh, const trk_skeleton* sk, const tr
   d.nblk_rows = (d.nblk_jtj + d.jtj_group - 1) / d.jtj_group;
   d.nblk_v = (V + 255) / 256;
   carve_all(s);
-  s->device_bytes = s->carved;
+  {  // the arena's size on the device: the carved bytes rounded up to the allocation granularity
+    const size_t g = vmm_granularity();
+    if (!g) return fail(TRK_ERR_CUDA, "the driver's virtual memory management is not available");
+    s->device_bytes = (std::max<size_t>(s->carved, 1) + g - 1) / g * g;
+  }
   CK(cudaMallocHost(&s->h_pinned, sizeof(double) * (L + prm->pose_iters + prm->shape_iters + 4)));
   CK(cudaMallocHost(&s->h_phi, sizeof(float4) * std::max(V, 1)));
   // the state of trk_set_pose(Theta = 0, Phi = 0)
@@ -1024,7 +1138,6 @@ trk_status trk_step_associate(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
   NEED_RESIDENT(s);
   CK(cudaMemsetAsync(s->d.qctl, 0, sizeof(unsigned) * 2, s->stream));
-  CK(cudaMemsetAsync(s->d.qctl + 3, 0, sizeof(unsigned), s->stream));  // from the first occupied tile
   launch_associate(s->d, s->stream);
   return sync_check(s);
 }

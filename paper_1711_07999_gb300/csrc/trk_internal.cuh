@@ -219,6 +219,20 @@ void launch_skin(const Dev& d, int phi_buf, cudaStream_t st);
 void launch_raster(const Dev& d, cudaStream_t st);
 void launch_visibility(const Dev& d, cudaStream_t st);
 void launch_associate(const Dev& d, cudaStream_t st);  // two kernels: thread-owned rings, then the queue
+// Device memory straight from the driver's virtual memory management, for what the library holds while
+// running (session arenas, the frame server's step buffers): physical memory in units of the allocation
+// granularity (2 MiB here) mapped into a reserved address range.  A block holds exactly its size rounded
+// up to the granularity, and freeing it returns the memory to the device at once -- no pool keeps it.
+// vmm_alloc: on the current device; *size receives the rounded size.  vmm_free: the memory must be idle.
+struct VmmBlock {
+  void* ptr = nullptr;
+  size_t size = 0;
+  unsigned long long handle = 0;
+};
+size_t vmm_granularity();  // of the current device (0 if the driver's API is unavailable)
+cudaError_t vmm_alloc(size_t bytes, VmmBlock* out);
+void vmm_free(VmmBlock* b);
+size_t vmm_bytes_held();   // bytes the library holds through vmm_alloc now, over all devices
 // Copies the frame's depth from src into d.depth (src == d.depth: in place) and lists the 16 x 16 tiles
 // that hold a valid pixel (the single-session association takes its tiles from that list).
 void launch_tiles(const Dev& d, const float* src, cudaStream_t st);
@@ -282,7 +296,7 @@ struct Dev {
   float4* pixrec;  // [W*H] first vertex inserted into each pixel's bucket: x, y, z, index bits
   int* head;
   int4* queue;     // [W*H] pixels whose association search continues past the thread-owned rings
-  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take, [2] occupied tiles, [3] next tile
+  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take, [2] occupied tiles of the frame
   int4* tiles;     // [ceil(W/16) ceil(H/16)] 16 x 16 tiles holding a valid depth pixel (0, x, y, tiles per row)
   unsigned long long* zbuf;
   int* corr;
@@ -316,6 +330,10 @@ struct Dev {
 
 namespace trk {
 
+// Warps that add one session's [J r] block partials: about four partials each (one round of loads), at
+// most 32; a batched launch gives every block the largest count of its sessions (a block uses its own).
+__host__ __device__ inline int reduce_warps(int nblk_rows) { return max(1, min(32, (nblk_rows + 3) / 4)); }
+
 struct BatchGrid;
 // Batched launches: one launch runs a stage for every session of a batch (block tables built by the batch).
 void launch_skin_b(const BatchGrid& g, int nblk, int max_links, int phi_buf, unsigned* ctl, cudaStream_t st);
@@ -326,7 +344,7 @@ void launch_associate_b(const Dev* devs, int n_sessions, const int4* tiles, unsi
 void launch_gather_depth_b(const BatchGrid& g, int nblk, const float* const* srcs, int4* tiles, unsigned* ctl,
                            cudaStream_t st);
 void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGrid& gr, int nr, int max_links,
-                               int precision, int phi_buf, int slot, cudaStream_t st);
+                               int precision, int phi_buf, int slot, cudaStream_t st, int reduce_threads);
 void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int max_links, int phi_buf,
                  cudaStream_t st);
 int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int solver, int phi_src, int slot,
@@ -354,6 +372,9 @@ struct ResultDst {
   int* stats;      // [4]
 };
 struct BatchStep;
+// device bytes one session adds to a step's buffer (a buffer holds at most twice its step's sum, rounded
+// up to the allocation granularity)
+size_t batch_step_bytes_of(const trk_session* s);
 BatchStep* batch_step_create();
 void batch_step_destroy(BatchStep* bs, cudaStream_t st);
 // One frame of the n sessions (resident, same schedule, precision and mode TRACK) as one launch per

@@ -83,7 +83,8 @@ class ScheduleConfig(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("frames_done", C.c_uint64), ("in_flight", C.c_int32), ("sessions", C.c_int32),
                 ("hbm_used_bytes", C.c_size_t), ("latency_p50_us", C.c_double), ("latency_p99_us", C.c_double),
-                ("latency_max_us", C.c_double), ("steps", C.c_uint64), ("mean_frames_per_step", C.c_double)]
+                ("latency_max_us", C.c_double), ("steps", C.c_uint64), ("mean_frames_per_step", C.c_double),
+                ("device_bytes_reserved", C.c_size_t)]
 
 
 class Result(C.Structure):

@@ -9,8 +9,6 @@ from paper_1711_07999_gb300 import synth, trk
     (dict(jtj_group=3), "jtj_group 3"),
     (dict(jtj_group=-1), "jtj_group -1"),
     (dict(jtj_group=8), "jtj_group 8"),
-    (dict(jtj_group=2, precision=trk.PRECISION_BF16X3), "needs precision FP32"),
-    (dict(jtj_group=4, precision=trk.PRECISION_TF32X3), "needs precision FP32"),
     (dict(precision=7), "precision 7"),
     (dict(shape_solver=2), "shape_solver 2"),
     (dict(mode=9), "mode 9"),
