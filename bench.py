@@ -369,7 +369,10 @@ def run_precision_modes(args, model, rank, host_frames, nA, NP, sample):
             ("bf16x3", trk.PRECISION_BF16X3, trk.SERVER_DISPATCH_BATCHED),
             ("tf32x3", trk.PRECISION_TF32X3, trk.SERVER_DISPATCH_BATCHED))
     for name, prec, disp in runs:
-        group = [trk.Session(synth.make_model(2, session=rank * 1000 + b, precision=prec)) for b in range(B)]
+        # per-session dispatch: the grouping chosen for one session; batched: the batches' grouping
+        G = 0 if disp == trk.SERVER_DISPATCH_SESSION else args.batch_jtj_group
+        group = [trk.Session(synth.make_model(2, session=rank * 1000 + b, precision=prec, jtj_group=G))
+                 for b in range(B)]
         for b, x in enumerate(group):
             x.set_pose(synth.gt_theta(model, (7 * b % len(host_frames)) / 30.0))
         srv = run_serving_closed_loop(group, host_frames, max(3, args.steps // 3), disp,
@@ -532,7 +535,7 @@ def run_serving(sessions, host_frames, n_seq, duration_s, fps, seed):
             arrivals.append((t, b))
             t += rng.exponential(1.0 / fps)
     arrivals.sort()
-    budget = sum(x.info()["device_bytes"] for x in sessions)
+    budget = sum(x.info()["device_bytes"] for x in sessions) + (1 << 30)  # not binding here (admission: below)
     tickets = [[] for _ in range(N)]
     done = [0] * N
     with trk.Server(budget, max_inflight=N) as sv:
@@ -924,6 +927,20 @@ def run_ours(args, rank, world, local_rank):
     if args.only == "uneven":  # the uneven batch alone (a diagnostic line, not the benchmark line)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         return {"uneven": run_uneven(args, rank, flush)} if rank == 0 else None
+    if args.only == "schedule":  # the headline's batched step alone, for profilers (a diagnostic line)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        m0 = synth.make_model(2, session=rank)
+        group = [trk.Session(synth.make_model(2, session=rank * 1000 + b, jtj_group=args.batch_jtj_group))
+                 for b in range(args.sessions)]
+        fr = render_sequence(m0, group[0], max(args.frames, 1), seed=synth.seed_for(2, 500 + rank))
+        dev = torch.from_numpy(fr).cuda()
+        for b, x in enumerate(group):
+            x.set_pose(synth.gt_theta(m0, (7 * b % len(fr)) / 30.0))
+        sched = run_schedule(group, dev, len(fr), args.steps, args.warmup, flush)
+        for x in group:
+            x.close()
+        return {"schedule": sched["config"], "sessions": args.sessions,
+                "fps": args.sessions * args.steps / (sched["total_ms"] / 1000.0)} if rank == 0 else None
     prec = PRECISIONS[args.precision]
     model = synth.make_model(2, session=rank, precision=prec)
     sess = trk.Session(model)
@@ -1143,14 +1160,15 @@ def main():
     ap.add_argument("--batch-jtj-group", type=int, default=4, choices=[0, 1, 2, 4],
                     help="[J r] grouping of the batched sessions (4: fewer block partials; 0: by mesh size)")
     ap.add_argument("--server-steps", type=int, default=4, help="concurrent batched steps of the frame server")
-    ap.add_argument("--precision-sessions", type=int, default=32,
+    ap.add_argument("--precision-sessions", type=int, default=64,
                     help="streams of the serving run in each precision mode")
     ap.add_argument("--serve-streams", type=int, default=32, help="Poisson streams (30 fps each) of the serving run")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp32",
                     help="arithmetic of [J r]^T [J r] in the plain and batched sessions")
-    ap.add_argument("--only", choices=["all", "plain", "uneven"], default="all",
-                    help="plain: the one-session and batched measurements only; uneven: the uneven batch only")
+    ap.add_argument("--only", choices=["all", "plain", "uneven", "schedule"], default="all",
+                    help="plain: the one-session and batched measurements only; uneven: the uneven batch only; "
+                         "schedule: the batched step alone (for profilers)")
     ap.add_argument("--uneven-modes", default="one_by_one,streams,fused,schedule")
     ap.add_argument("--admission-streams", type=int, default=32,
                     help="streams of uneven sessions arriving under an HBM budget (0: skip)")

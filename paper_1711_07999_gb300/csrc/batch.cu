@@ -126,6 +126,7 @@ void enqueue_frame_view(const FrameView& v, cudaStream_t st) {
   launch_gather_depth_b(grid_of(v, kAssoc), v.tables[kAssoc].n, v.d_srcs, v.d_tiles, v.d_ctl, st);
   int cur = 0;
   auto geometry = [&]() {
+    NvtxRange nv("skin, z-buffer, visibility, association");
     launch_skin_b(grid_of(v, kSkin), v.tables[kSkin].n, L, cur, v.d_ctl, st);
     launch_raster_b(grid_of(v, kTris), v.tables[kTris].n, st);
     launch_visibility_b(grid_of(v, kVerts), v.tables[kVerts].n, st);
@@ -139,12 +140,14 @@ void enqueue_frame_view(const FrameView& v, cudaStream_t st) {
       gj[t] = grid_of(v, (Kind)(kJtj1 + t));
       nj[t] = v.tables[kJtj1 + t].n;
     }
+    NvtxRange nv("normal equations, LM step");
     launch_normal_equations_b(gj, nj, grid_of(v, kReduce), v.tables[kReduce].n, L, v.precision, cur, it, st,
                               v.reduce_threads);
     launch_lm_b(grid_of(v, kLm), v.tables[kLm].n, grid_of(v, kRows), v.tables[kRows].n, L, cur, st);
   }
   for (int it = 0; it < S; ++it) {
     geometry();
+    NvtxRange nv("shape step");
     cur = launch_shape_b(grid_of(v, kVerts), v.tables[kVerts].n, L, v.sweeps, v.solver, cur, P + it, st);
   }
   if (cur != 0)
@@ -376,6 +379,7 @@ size_t batch_step_bytes_of(const trk_session* s) {
 
 trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const float* const* srcs,
                              const ResultDst* dst, cudaStream_t st) {
+  NvtxRange range("server batched step");
   if (!bs || !ss || n < 1 || n > kMaxBatch || !srcs || !dst)
     return set_error(TRK_ERR_INVALID_ARG, "batch step: bad arguments");
   const trk_params& p0 = session_params(ss[0]);
@@ -491,6 +495,7 @@ trk_status trk_batch_create(trk_session* const* sessions, int32_t n_sessions, tr
 }
 
 trk_status trk_batch_track_device(trk_batch* b, const float* const* d_depths, void* cuda_stream) {
+  NvtxRange nv("trk_batch_track_device");
   if (!b || !d_depths) return set_error(TRK_ERR_INVALID_ARG, "trk_batch_track_device: NULL argument");
   if (!members_current(b))
     return set_error(TRK_ERR_INVALID_ARG, "trk_batch_track_device: a member was evicted since the batch was built");

@@ -50,6 +50,7 @@ __device__ __forceinline__ void skin_impl(const Dev& d, BlockPos bp, int phi_buf
     d.stats[1] = 0;
     d.qctl[0] = 0;
     d.qctl[1] = 0;
+    d.qctl[3] = 0;  // the association's next tile (the tile list itself is the frame's)
   }
   const float4* phi = d.phi[phi_buf];
   for (int i = tid; i < d.V; i += stride) {
@@ -371,8 +372,8 @@ __device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
 
 constexpr int kTailWarps = 8;
 constexpr int kTailPerLane = 4;       // buckets a lane loads at once (one session: a warp per pixel)
-constexpr int kBatchTailLanes = 4;    // a batch's tail: lanes per queued pixel ...
-constexpr int kBatchTailPerLane = 8;  // ... and buckets each of them loads at once
+constexpr int kBatchTailLanes = 8;    // a batch's tail: lanes per queued pixel ...
+constexpr int kBatchTailPerLane = 4;  // ... and buckets each of them loads at once
 
 // The rings beyond the thread-owned ones for queue entry `item` of session d, by a group of GL lanes (lanes
 // gl = lane % GL of the group starting at lane gbase, gmask naming them): the lanes split each
@@ -380,7 +381,7 @@ constexpr int kBatchTailPerLane = 8;  // ... and buckets each of them loads at o
 // combine (d^2, index) keys with a group min.  Returns, in every lane of the group, whether the pixel got a
 // correspondence (its first lane writes it and adds the pixel's sums).
 // One session's tail takes a warp per pixel (its queue is short and its latency is the slowest pixel's
-// rings); a batch's takes 4 lanes per pixel (eight pixels per warp: throughput over many queues).
+// rings); a batch's takes 8 lanes per pixel (four pixels per warp: throughput over many queues).
 template <int GL, int PL>
 __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, unsigned gmask) {
   const Cam c = d.cam;
@@ -428,29 +429,39 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
   return best >= 0;
 }
 
-// One session: one 16 x 16 tile per block.  A batch: persistent blocks take the frame's occupied tiles
-// (listed by the depth gather) from a shared counter, reloading the session descriptor when the session
-// changes; pixels of empty tiles keep the "no correspondence" the skinning pass wrote.
+// Persistent blocks take the frame's occupied tiles (one session's from k_tiles, a batch's from the depth
+// gather) from a shared counter -- a counter, not fixed shares, because tiles of dense sessions cost far
+// more than others -- reloading the session descriptor when the session changes; pixels of empty tiles
+// keep the "no correspondence" the skinning pass wrote.
 __global__ void __launch_bounds__(kBlock, 4) k_associate(const Dev* devs, const int4* tiles, unsigned* ctl, Dev d0) {
-  // each block takes a contiguous share of the occupied tiles (no shared counter, so no atomic round trip
-  // per tile, and a share mostly within one session)
-  const unsigned n = devs == nullptr ? d0.qctl[2] : ctl[0];
-  const unsigned lo = (unsigned)(((unsigned long long)n * blockIdx.x) / gridDim.x);
-  const unsigned hi = (unsigned)(((unsigned long long)n * (blockIdx.x + 1)) / gridDim.x);
-  const int4* list = devs == nullptr ? d0.tiles : tiles;
-  if (devs == nullptr) {  // one session
-    for (unsigned i = lo; i < hi; ++i) {
-      const int4 t = list[i];
+  __shared__ int4 s_t;
+  if (devs == nullptr) {  // one session: persistent blocks over the frame's occupied tiles
+    const unsigned n = d0.qctl[2];
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned i = atomicAdd(&d0.qctl[3], 1u);
+        s_t = i < n ? d0.tiles[i] : make_int4(-1, 0, 0, 0);
+      }
+      __syncthreads();
+      const int4 t = s_t;
+      if (t.x < 0) return;
       associate_impl(d0, BlockPos{t.y, t.z, t.w});
     }
-    return;
   }
   __shared__ Dev sd;
   int cur = -1;
-  for (unsigned i = lo; i < hi; ++i) {
-    const int4 t = list[i];
-    if (t.x != cur) {  // a tile of another session: its descriptor, once every thread is done with the last
-      __syncthreads();
+  const unsigned n = ctl[0];
+  for (;;) {
+    __syncthreads();  // the previous tile is done (s_t, sd free)
+    if (threadIdx.x == 0) {
+      const unsigned i = atomicAdd(&ctl[1], 1u);
+      s_t = i < n ? tiles[i] : make_int4(-1, 0, 0, 0);
+    }
+    __syncthreads();
+    const int4 t = s_t;
+    if (t.x < 0) break;
+    if (t.x != cur) {
       const int* src = reinterpret_cast<const int*>(devs + t.x);
       for (int q = threadIdx.x; q < (int)(sizeof(Dev) / 4); q += blockDim.x) reinterpret_cast<int*>(&sd)[q] = src[q];
       cur = t.x;

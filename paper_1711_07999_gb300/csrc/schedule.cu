@@ -283,6 +283,7 @@ trk_status trk_schedule_create(trk_session* const* sessions, int32_t n, const tr
 }
 
 trk_status trk_schedule_track_device(trk_schedule* s, const float* const* d_depths, void* cuda_stream) {
+  NvtxRange nv("trk_schedule_track_device");
   if (!s || !d_depths) return set_error(TRK_ERR_INVALID_ARG, "trk_schedule_track_device: NULL argument");
   return step(s, d_depths, (cudaStream_t)cuda_stream);
 }

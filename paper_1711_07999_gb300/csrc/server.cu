@@ -528,6 +528,7 @@ trk_status trk_server_detach(trk_server* sv, trk_session* s) {
 }
 
 trk_status trk_server_submit(trk_server* sv, trk_session* s, const float* depth_m, uint64_t* ticket) {
+  trk::NvtxRange nv("trk_server_submit");
   if (!sv || !s || !depth_m || !ticket) return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_submit: NULL argument");
   int L = 0, V = 0, ne = 0;
   trk::session_result_sizes(s, &L, &V, &ne);
@@ -579,6 +580,7 @@ trk_status trk_server_submit(trk_server* sv, trk_session* s, const float* depth_
 }
 
 trk_status trk_server_wait(trk_server* sv, uint64_t ticket, int64_t timeout_us, trk_result* out) {
+  trk::NvtxRange nv("trk_server_wait");
   if (!sv) return trk::set_error(TRK_ERR_INVALID_ARG, "trk_server_wait: NULL server");
   std::unique_lock<std::mutex> lk(sv->mu);
   const auto deadline = clk::now() + std::chrono::microseconds(std::max<int64_t>(timeout_us, 0));

@@ -359,6 +359,7 @@ void enqueue_frame(trk_session* s, cudaStream_t st, bool with_shape) {
   // a frame without shape iterations reports NaN for their energies (all-ones bytes are a NaN)
   if (!with_shape && s->prm.shape_iters > 0) cudaMemsetAsync(d.energy + P, 0xFF, sizeof(double) * s->prm.shape_iters, st);
   for (int it = 0; it < P; ++it) {
+    NvtxRange nv("pose iteration");
     launch_skin(d, cur, st);
     launch_raster(d, st);
     launch_visibility(d, st);
@@ -367,6 +368,7 @@ void enqueue_frame(trk_session* s, cudaStream_t st, bool with_shape) {
     launch_lm(d, cur, st);
   }
   for (int it = 0; it < S; ++it) {
+    NvtxRange nv("shape iteration");
     launch_skin(d, cur, st);
     launch_raster(d, st);
     launch_visibility(d, st);
@@ -879,11 +881,13 @@ trk_status trk_create_evicted(const trk_mesh* mesh, const trk_skeleton* sk, cons
 }
 
 trk_status trk_session_evict(trk_session* s) {
+  NvtxRange nv("trk_session_evict");
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
   return evict(s);
 }
 
 trk_status trk_session_restore(trk_session* s) {
+  NvtxRange nv("trk_session_restore");
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
   return materialize(s);
 }
@@ -1044,6 +1048,7 @@ trk_status trk_session_import(trk_session* s, const void* blob, size_t size_byte
 }
 
 trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out) {
+  NvtxRange nv("trk_track_frame");
   if (!s || !depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
   NEED_RESIDENT(s);
   cudaGraphExec_t ge;
@@ -1060,6 +1065,7 @@ trk_status trk_track_frame(trk_session* s, const float* depth_m, trk_result* out
 }
 
 trk_status trk_track_frame_device(trk_session* s, const float* d_depth_m, void* cuda_stream) {
+  NvtxRange nv("trk_track_frame_device");
   if (!s || !d_depth_m) return fail(TRK_ERR_INVALID_ARG, "NULL argument");
   NEED_RESIDENT(s);
   cudaGraphExec_t ge;
@@ -1138,6 +1144,7 @@ trk_status trk_step_associate(trk_session* s) {
   if (!s) return fail(TRK_ERR_INVALID_ARG, "NULL session");
   NEED_RESIDENT(s);
   CK(cudaMemsetAsync(s->d.qctl, 0, sizeof(unsigned) * 2, s->stream));
+  CK(cudaMemsetAsync(s->d.qctl + 3, 0, sizeof(unsigned), s->stream));  // from the first occupied tile
   launch_associate(s->d, s->stream);
   return sync_check(s);
 }

@@ -11,6 +11,7 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/trk.h"
 
@@ -296,7 +297,7 @@ struct Dev {
   float4* pixrec;  // [W*H] first vertex inserted into each pixel's bucket: x, y, z, index bits
   int* head;
   int4* queue;     // [W*H] pixels whose association search continues past the thread-owned rings
-  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take, [2] occupied tiles of the frame
+  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take, [2] occupied tiles, [3] next tile
   int4* tiles;     // [ceil(W/16) ceil(H/16)] 16 x 16 tiles holding a valid depth pixel (0, x, y, tiles per row)
   unsigned long long* zbuf;
   int* corr;
@@ -329,6 +330,15 @@ struct Dev {
 }  // namespace trk
 
 namespace trk {
+
+// A named range on the host timeline of a profiler (NVTX; costs nothing when no profiler is attached):
+// the C entry points and the stages a frame enqueues.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Warps that add one session's [J r] block partials: about four partials each (one round of loads), at
 // most 32; a batched launch gives every block the largest count of its sessions (a block uses its own).
