@@ -39,10 +39,9 @@ __device__ __forceinline__ void skin_impl(const Dev& d, BlockPos bp, int phi_buf
   const int tid = bp.x * blockDim.x + threadIdx.x;
   const int stride = bp.gx * blockDim.x;
   const int npx = d.cam.W * d.cam.H;
-  for (int k = tid; k < npx; k += stride) {
+  for (int k = tid; k < npx; k += stride) {  // (corr: set once per frame with the depth, see k_tiles)
     d.zbuf[k] = ~0ull;
     d.head[k] = -1;
-    d.corr[k] = -1;
   }
   for (int k = tid; k < d.V; k += stride) d.acc[k] = Acc4{0, 0, 0, 0};
   if (tid == 0) {
@@ -50,7 +49,6 @@ __device__ __forceinline__ void skin_impl(const Dev& d, BlockPos bp, int phi_buf
     d.stats[1] = 0;
     d.qctl[0] = 0;
     d.qctl[1] = 0;
-    d.qctl[3] = 0;  // the association's next tile (the tile list itself is the frame's)
   }
   const float4* phi = d.phi[phi_buf];
   for (int i = tid; i < d.V; i += stride) {
@@ -311,11 +309,12 @@ __device__ __forceinline__ float3 back_project(const Cam& c, int px, int py, flo
                      (float)((double)dep - (double)c.oz));
 }
 
-__device__ __forceinline__ void associate_impl(const Dev& d, BlockPos bp) {
+// One warp's unit: the 32 pixels of rows py0, py0 + 1 and columns px0 .. px0 + 15 (a lane each).
+__device__ __forceinline__ void associate_impl(const Dev& d, int px0, int py0) {
   const Cam c = d.cam;
   const int lane = threadIdx.x & 31;
-  const int px = bp.x * 16 + (threadIdx.x & 15);
-  const int py = bp.y * 16 + (threadIdx.x >> 4);
+  const int px = px0 + (lane & 15);
+  const int py = py0 + (lane >> 4);
   const bool inimg = px < c.W && py < c.H;
   const int k = py * c.W + px;
   const float dep = inimg ? d.depth[k] : 0.f;
@@ -429,60 +428,51 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
   return best >= 0;
 }
 
-// Persistent blocks take the frame's occupied tiles (one session's from k_tiles, a batch's from the depth
-// gather) from a shared counter -- a counter, not fixed shares, because tiles of dense sessions cost far
-// more than others -- reloading the session descriptor when the session changes; pixels of empty tiles
-// keep the "no correspondence" the skinning pass wrote.
-__global__ void __launch_bounds__(kBlock, 4) k_associate(const Dev* devs, const int4* tiles, unsigned* ctl, Dev d0) {
-  __shared__ int4 s_t;
-  if (devs == nullptr) {  // one session: persistent blocks over the frame's occupied tiles
-    const unsigned n = d0.qctl[2];
-    for (;;) {
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned i = atomicAdd(&d0.qctl[3], 1u);
-        s_t = i < n ? d0.tiles[i] : make_int4(-1, 0, 0, 0);
-      }
-      __syncthreads();
-      const int4 t = s_t;
-      if (t.x < 0) return;
-      associate_impl(d0, BlockPos{t.y, t.z, t.w});
-    }
-  }
-  __shared__ Dev sd;
+// Persistent warps take the frame's occupied units (16 x 2 pixels with a valid depth; one session's from
+// k_tiles, a batch's from the depth gather), warp w the units w, w + (warps in the grid), ...: no counter
+// and no block barrier, so a warp whose pixels are cheap goes on to its next unit at once, and the
+// interleaving spreads the units of costly sessions over all warps.  In a batch each warp keeps its own
+// copy of its unit's session descriptor in shared memory (reloaded when the session changes).  Pixels
+// outside the units keep the "no correspondence" the frame's depth copy wrote.
+__global__ void __launch_bounds__(kBlock, 4) k_associate(const Dev* devs, const int4* units, const unsigned* ctl, Dev d0) {
+  __shared__ Dev sd[kBlock / 32];
+  const bool single = devs == nullptr;
+  const unsigned n = single ? d0.qctl[2] : ctl[0];
+  const int4* list = single ? d0.tiles : units;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned nw = gridDim.x * (kBlock / 32);
   int cur = -1;
-  const unsigned n = ctl[0];
-  for (;;) {
-    __syncthreads();  // the previous tile is done (s_t, sd free)
-    if (threadIdx.x == 0) {
-      const unsigned i = atomicAdd(&ctl[1], 1u);
-      s_t = i < n ? tiles[i] : make_int4(-1, 0, 0, 0);
+  for (unsigned u = blockIdx.x * (kBlock / 32) + w; u < n; u += nw) {
+    const int4 t = list[u];  // (session, x0, y0, 0)
+    if (single) {
+      associate_impl(d0, t.y, t.z);
+      continue;
     }
-    __syncthreads();
-    const int4 t = s_t;
-    if (t.x < 0) break;
     if (t.x != cur) {
+      __syncwarp();  // every lane is done with the previous descriptor
       const int* src = reinterpret_cast<const int*>(devs + t.x);
-      for (int q = threadIdx.x; q < (int)(sizeof(Dev) / 4); q += blockDim.x) reinterpret_cast<int*>(&sd)[q] = src[q];
+      for (int q = lane; q < (int)(sizeof(Dev) / 4); q += 32) reinterpret_cast<int*>(&sd[w])[q] = src[q];
+      __syncwarp();
       cur = t.x;
-      __syncthreads();
     }
-    associate_impl(sd, BlockPos{t.y, t.z, t.w});
+    associate_impl(sd[w], t.y, t.z);
   }
 }
 
-// One session: the warps of all blocks take its queue entries from the session's counter.
+// One session: the warps of all blocks take its queue entries, warp w the w-th, then the rest from the
+// session's counter (no counter traffic when the queue is no longer than the grid's warps).
 __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
   const int lane = threadIdx.x & 31, gl = lane, gbase = 0;
   const unsigned gmask = 0xffffffffu;
   const unsigned n = *(volatile unsigned*)&d.qctl[0];
+  const unsigned warps = gridDim.x * kTailWarps;  // warp w takes entry w first, then the counter's
   int done = 0;
-  for (;;) {
-    unsigned item = 0;
-    if (gl == 0) item = atomicAdd(&d.qctl[1], 1u);
-    item = __shfl_sync(gmask, item, gbase);
-    if (item >= n) break;
+  for (unsigned item = blockIdx.x * kTailWarps + (threadIdx.x >> 5); item < n;) {
     done += tail_item<32, kTailPerLane>(d, item, gl, gmask);
+    if (warps >= n) break;
+    unsigned next = 0;
+    if (gl == 0) next = warps + atomicAdd(&d.qctl[1], 1u);
+    item = __shfl_sync(gmask, next, gbase);
   }
   if (gl == 0 && done) atomicAdd(&d.stats[0], done);
 }
@@ -514,19 +504,17 @@ __global__ void __launch_bounds__(1024) k_tail_prefix(const Dev* devs, int n_ses
   if (t == 1023) prefix[n_sessions] = part[t];
 }
 
-// A batch: the warps take entries of the concatenated queues of all sessions from one counter; an
-// entry's session is found in the prefix and its descriptor read through the cache.
+// A batch: the lane groups take entries of the concatenated queues of all sessions, group g the g-th, then
+// the rest from one counter; an entry's session is found in the prefix and its descriptor read through
+// the cache.
 __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const Dev* devs, int n_sessions,
                                                                           const unsigned* prefix, unsigned* ctl) {
   constexpr int GL = kBatchTailLanes;
   const int lane = threadIdx.x & 31, gl = lane % GL, gbase = lane - gl;
   const unsigned gmask = ((1u << GL) - 1u) << gbase;
   const unsigned total = prefix[n_sessions];
-  for (;;) {
-    unsigned item = 0;
-    if (gl == 0) item = atomicAdd(&ctl[2], 1u);
-    item = __shfl_sync(gmask, item, gbase);
-    if (item >= total) break;
+  const unsigned groups = gridDim.x * (blockDim.x / GL);  // group g takes entry g first, then the counter's
+  for (unsigned item = (blockIdx.x * blockDim.x + threadIdx.x) / GL; item < total;) {
     int lo = 0, hi = n_sessions - 1;  // the last session whose prefix is <= item
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
@@ -534,17 +522,36 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const 
     }
     const Dev& d = devs[lo];
     if (tail_item<GL, kBatchTailPerLane>(d, item - prefix[lo], gl, gmask) && gl == 0) atomicAdd(&d.stats[0], 1);
+    if (groups >= total) break;
+    unsigned next = 0;
+    if (gl == 0) next = groups + atomicAdd(&ctl[2], 1u);
+    item = __shfl_sync(gmask, next, gbase);
   }
 }
 
 void launch_associate(const Dev& d, cudaStream_t st) {
-  const int ntiles = ((d.cam.W + 15) / 16) * ((d.cam.H + 15) / 16);
-  k_associate<<<min(ntiles, 4 * 152), kBlock, 0, st>>>(nullptr, nullptr, nullptr, d);
+  const int nunits = ((d.cam.W + 15) / 16) * ((d.cam.H + 1) / 2);
+  k_associate<<<min((nunits + kBlock / 32 - 1) / (kBlock / 32), 4 * 152), kBlock, 0, st>>>(nullptr, nullptr, nullptr, d);
   k_associate_tail<<<2 * 152, 32 * kTailWarps, 0, st>>>(d);
 }
 
-// One 16 x 16 tile per block: copies the frame's depth into the session's buffer and appends the tile
-// to the list if it holds a valid pixel.
+// Appends the association units (16 x 2 pixels, one per warp of a 16 x 16 tile) of this block's tile
+// that hold a valid pixel to list, one counter update per tile.
+__device__ __forceinline__ void list_units(bool valid, int session, int tx, int ty, int4* list, unsigned* count) {
+  __shared__ unsigned s_mask;
+  if (threadIdx.x == 0) s_mask = 0;
+  __syncthreads();
+  if (__ballot_sync(0xffffffffu, valid) && (threadIdx.x & 31) == 0) atomicOr(&s_mask, 1u << (threadIdx.x >> 5));
+  __syncthreads();
+  if (threadIdx.x == 0 && s_mask) {
+    unsigned m = s_mask, at = atomicAdd(count, (unsigned)__popc(m));
+    for (; m; m &= m - 1) list[at++] = make_int4(session, tx * 16, ty * 16 + 2 * (__ffs(m) - 1), 0);
+  }
+}
+
+// One 16 x 16 tile per block: copies the frame's depth into the session's buffer, marks every pixel
+// "no correspondence" (the association rewrites the pixels of its units each iteration) and lists the
+// tile's units that hold a valid pixel.
 __global__ void __launch_bounds__(kBlock) k_tiles(Dev d, const float* __restrict__ src) {
   const int gx = (d.cam.W + 15) / 16;
   const int tx = blockIdx.x % gx, ty = blockIdx.x / gx;
@@ -554,9 +561,10 @@ __global__ void __launch_bounds__(kBlock) k_tiles(Dev d, const float* __restrict
     const int k = py * d.cam.W + px;
     const float z = src[k];
     const_cast<float*>(d.depth)[k] = z;
+    d.corr[k] = -1;
     valid = z > 0.f;
   }
-  if (__syncthreads_or(valid) && threadIdx.x == 0) d.tiles[atomicAdd(&d.qctl[2], 1u)] = make_int4(0, tx, ty, gx);
+  list_units(valid, 0, tx, ty, d.tiles, &d.qctl[2]);
 }
 
 void launch_tiles(const Dev& d, const float* src, cudaStream_t st) {
@@ -582,8 +590,9 @@ void launch_associate_b(const Dev* devs, int n_sessions, const int4* tiles, unsi
 }
 
 // Copies each session's depth frame from srcs[session] into the session's own depth buffer, one 16 x 16
-// tile per block (the association's tiling), and lists the tiles that hold a valid depth.
-__global__ void __launch_bounds__(kBlock) k_gather_depth_b(BatchGrid g, const float* const* srcs, int4* tiles,
+// tile per block, marks every pixel "no correspondence" and lists the association units (16 x 2 pixels)
+// that hold a valid depth.
+__global__ void __launch_bounds__(kBlock) k_gather_depth_b(BatchGrid g, const float* const* srcs, int4* units,
                                                            unsigned* ctl) {
   const int4 m = g.map[blockIdx.x];
   const Dev& d = g.devs[m.x];
@@ -593,9 +602,10 @@ __global__ void __launch_bounds__(kBlock) k_gather_depth_b(BatchGrid g, const fl
     const int k = py * d.cam.W + px;
     const float z = srcs[m.x][k];
     const_cast<float*>(d.depth)[k] = z;
+    d.corr[k] = -1;
     valid = z > 0.f;
   }
-  if (__syncthreads_or(valid) && threadIdx.x == 0) tiles[atomicAdd(&ctl[0], 1u)] = m;
+  list_units(valid, m.x, m.y, m.z, units, &ctl[0]);
 }
 void launch_gather_depth_b(const BatchGrid& g, int nblk, const float* const* srcs, int4* tiles, unsigned* ctl,
                            cudaStream_t st) {

@@ -103,7 +103,11 @@ __device__ __forceinline__ void jacobian_row(const Dev& d, const RowSlot& rs, in
   if (!rs.inA) return;
   const Acc4 a4 = rs.a4;
   float* row = Js + rs.slot * ROW;
-  for (int k = 0; k < width; ++k) row[k] = 0.f;
+  if ((ROW & 3) == 0 && (width & 3) == 0) {  // 16-byte rows: 128-bit stores
+    for (int k = 0; k < width; k += 4) *reinterpret_cast<float4*>(row + k) = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    for (int k = 0; k < width; ++k) row[k] = 0.f;
+  }
   const float inv = 1.f / ((float)a4.w * kFix);
   const float3 pm = make_float3((float)a4.x * inv, (float)a4.y * inv, (float)a4.z * inv);
   const float3 n = f3(rs.nn);
@@ -205,11 +209,106 @@ __device__ __forceinline__ void jacobian_row(const Dev& d, const RowSlot& rs, in
   }
 }
 
+// Row stride of the staged rows: 16T columns, padded so that rows of even T start on 16 bytes (vector loads
+// of a tile's T entries) and rows of odd T fall on distinct banks.
+__host__ __device__ constexpr int jtj_row_stride(int T) { return 16 * T + (T % 2 == 0 ? 4 : 1); }
+constexpr int kMaxRowGroups = 4;
+
+// Packed FP32 pairs: fma.rn.f32x2 rounds each lane as fmaf does, so a tile updated pairwise holds the same
+// bits as one updated entry by entry.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void f2_fma(unsigned long long& acc, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+// One thread's T x T tile of the product: acc[a][b] += ra[a] rb[b] over the rows it sweeps.
+template <int T>
+struct TileAcc {
+  static constexpr bool kPaired = T % 2 == 0;
+  unsigned long long p[kPaired ? T : 1][kPaired ? T / 2 : 1];
+  float f[kPaired ? 1 : T][kPaired ? 1 : T];
+  __device__ __forceinline__ void zero() {
+    if constexpr (kPaired) {
+#pragma unroll
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T / 2; ++b) p[a][b] = 0ull;
+    } else {
+#pragma unroll
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T; ++b) f[a][b] = 0.f;
+    }
+  }
+  // adds one staged row: entries [ty T, ty T + T) and [tx T, tx T + T)
+  __device__ __forceinline__ void add_row(const float* row, int ty, int tx) {
+    float ra[T], rb[T];
+    if constexpr (T == 4) {
+      const float4 A = *reinterpret_cast<const float4*>(row + ty * 4);
+      const float4 B = *reinterpret_cast<const float4*>(row + tx * 4);
+      ra[0] = A.x, ra[1] = A.y, ra[2] = A.z, ra[3] = A.w;
+      rb[0] = B.x, rb[1] = B.y, rb[2] = B.z, rb[3] = B.w;
+    } else {
+#pragma unroll
+      for (int a = 0; a < T; ++a) {
+        ra[a] = row[ty * T + a];
+        rb[a] = row[tx * T + a];
+      }
+    }
+    if constexpr (kPaired) {
+      unsigned long long B2[T / 2];
+#pragma unroll
+      for (int b = 0; b < T / 2; ++b) B2[b] = f2_pack(rb[2 * b], rb[2 * b + 1]);
+#pragma unroll
+      for (int a = 0; a < T; ++a) {
+        const unsigned long long A2 = f2_pack(ra[a], ra[a]);
+#pragma unroll
+        for (int b = 0; b < T / 2; ++b) f2_fma(p[a][b], A2, B2[b]);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T; ++b) f[a][b] = fmaf(ra[a], rb[b], f[a][b]);
+    }
+  }
+  __device__ __forceinline__ float get(int a, int b) const {
+    if constexpr (kPaired) {
+      float lo, hi;
+      f2_unpack(p[a][b / 2], lo, hi);
+      return (b & 1) ? hi : lo;
+    } else {
+      return f[a][b];
+    }
+  }
+  __device__ __forceinline__ void add(int a, int b, float x) {
+    if constexpr (kPaired) {
+      float lo, hi;
+      f2_unpack(p[a][b / 2], lo, hi);
+      if (b & 1) hi += x; else lo += x;
+      p[a][b / 2] = f2_pack(lo, hi);
+    } else {
+      f[a][b] += x;
+    }
+  }
+};
+
 // A [J r] block covers jtj_group consecutive blocks of 256 vertices: each one's rows are formed and
 // staged in turn and added to the same tiles, so the block writes one partial for up to 256 G rows.
+// The symmetric product needs only the tiles (ty, tx) with ty <= tx among the nt x nt tiles that hold
+// columns < NP; S groups of nt (nt + 1) / 2 threads (S = 2 for NP <= 60 at T = 4) each sweep every S-th
+// staged row, and the first group adds the other groups' tiles, in group order, before the block writes
+// its partial: a fixed order, so the partial is the same in any launch.
 template <int T>
 __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int phi_buf) {
-  constexpr int ROW = 16 * T + 1;
+  constexpr int ROW = jtj_row_stride(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Js = reinterpret_cast<float*>(smem_raw);
   DQ* sHd = reinterpret_cast<DQ*>(Js + kBlock * ROW);
@@ -217,22 +316,19 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
   int* sPar = reinterpret_cast<int*>(sXi + 6 * d.L);
   __shared__ int s_warp[kBlock / 32];
   const int tid = threadIdx.x, G = d.jtj_group;
-  // the symmetric product needs only the tiles (ty, tx) with ty <= tx among the nt x nt tiles that hold
-  // columns < NP: thread k < nt (nt + 1) / 2 takes the k-th of them (row-major), the others idle; each
-  // tile is written with its mirror (the mirrored products are the same products in the same order)
   const int NP = d.NP;
   const int nt = (NP + T - 1) / T;
-  int ty = 0, k = tid;
-  while (ty < nt && k >= nt - ty) {
+  const int ntiles = nt * (nt + 1) / 2;
+  const int S = min(kMaxRowGroups, kBlock / ntiles);
+  const int h = tid / ntiles;  // this thread's row group (h >= S: idle in the product)
+  int ty = 0, k = tid - h * ntiles;
+  while (ty < nt && k >= nt - ty) {  // the k-th tile of the upper triangle, row-major
     k -= nt - ty;
     ++ty;
   }
   const int tx = ty + k;
-  float acc[T][T];
-#pragma unroll
-  for (int a = 0; a < T; ++a)
-#pragma unroll
-    for (int b = 0; b < T; ++b) acc[a][b] = 0.f;
+  TileAcc<T> acc;
+  acc.zero();
   int done = 0;  // rows added so far (the same in every thread)
   bool tables = false;
   for (int sub = 0; sub < G; ++sub) {
@@ -252,35 +348,38 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
     float r2;
     jacobian_row(d, rs, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, r2);
     __syncthreads();
-    if (ty < nt) {
-      for (int s = 0; s < total; ++s) {
-        const float* row = Js + s * ROW;
-        float ra[T], rb[T];
-#pragma unroll
-        for (int a = 0; a < T; ++a) {
-          ra[a] = row[ty * T + a];
-          rb[a] = row[tx * T + a];
-        }
-#pragma unroll
-        for (int a = 0; a < T; ++a)
-#pragma unroll
-          for (int b = 0; b < T; ++b) acc[a][b] = fmaf(ra[a], rb[b], acc[a][b]);
-      }
-    }
+    if (h < S)
+      for (int s = h; s < total; s += S) acc.add_row(Js + s * ROW, ty, tx);
     done += total;
   }
   if (done == 0) {  // nothing to add: the reduction skips this block's (unwritten) partial
     if (tid == 0) d.jtj_rows[bp.x] = 0;
     return;
   }
-  if (ty < nt) {
+  if (S > 1) {  // the groups' tiles, added into group 0's in group order
+    __syncthreads();  // every group's sweep is done: the staged rows are free
+    float* red = Js;
+    if (h >= 1 && h < S)
+#pragma unroll
+      for (int a = 0; a < T; ++a)
+#pragma unroll
+        for (int b = 0; b < T; ++b) red[((h - 1) * T * T + a * T + b) * ntiles + (tid - h * ntiles)] = acc.get(a, b);
+    __syncthreads();
+    if (h == 0)
+      for (int g2 = 1; g2 < S; ++g2)
+#pragma unroll
+        for (int a = 0; a < T; ++a)
+#pragma unroll
+          for (int b = 0; b < T; ++b) acc.add(a, b, red[((g2 - 1) * T * T + a * T + b) * ntiles + tid]);
+  }
+  if (h == 0) {
     float* out = d.partial + (size_t)bp.x * NP * NP;
 #pragma unroll
     for (int a = 0; a < T; ++a)
 #pragma unroll
       for (int b = 0; b < T; ++b) {
         const int r = ty * T + a, c = tx * T + b;
-        if (r < NP && c < NP && r <= c) out[r * NP + c] = acc[a][b];  // the upper triangle (the reduction mirrors)
+        if (r < NP && c < NP && r <= c) out[r * NP + c] = acc.get(a, b);  // the upper triangle (the reduction mirrors)
       }
   }
   if (tid == 0) {
@@ -513,7 +612,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_jtj(BatchGrid g, Dev 
 }
 
 static int jtj_smem_bytes(int T, int L) {
-  return kBlock * (16 * T + 1) * 4 + L * (int)sizeof(DQ) + 6 * L * 4 + L * 4;
+  return kBlock * jtj_row_stride(T) * 4 + L * (int)sizeof(DQ) + 6 * L * 4 + L * 4;
 }
 
 template <int PREC>

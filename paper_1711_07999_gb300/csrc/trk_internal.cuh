@@ -19,6 +19,7 @@ namespace trk {
 
 constexpr int kMaxLinks = 79;       // NP = P + 1 <= 80
 constexpr int kMaxNP = 80;
+constexpr int kUnitsPerTile = 8;   // association units (16 x 2 pixels) per 16 x 16 tile
 constexpr int kCandidates = 6;      // damping values tried per LM iteration: lambda * 10^c, c = 0..5
 constexpr float kFix = 1073741824.0f;  // 2^30: fixed-point scale of the per-vertex sums
 
@@ -234,8 +235,9 @@ size_t vmm_granularity();  // of the current device (0 if the driver's API is un
 cudaError_t vmm_alloc(size_t bytes, VmmBlock* out);
 void vmm_free(VmmBlock* b);
 size_t vmm_bytes_held();   // bytes the library holds through vmm_alloc now, over all devices
-// Copies the frame's depth from src into d.depth (src == d.depth: in place) and lists the 16 x 16 tiles
-// that hold a valid pixel (the single-session association takes its tiles from that list).
+// Copies the frame's depth from src into d.depth (src == d.depth: in place), marks every pixel "no
+// correspondence" and lists the association units (16 x 2 pixels) that hold a valid pixel (the
+// single-session association takes its units from that list).
 void launch_tiles(const Dev& d, const float* src, cudaStream_t st);
 // residual + Jacobian + [J r]^T [J r]; writes E_pose to energy[slot] (slot < 0: not recorded)
 void launch_normal_equations(const Dev& d, int phi_buf, int slot, cudaStream_t st);
@@ -297,8 +299,8 @@ struct Dev {
   float4* pixrec;  // [W*H] first vertex inserted into each pixel's bucket: x, y, z, index bits
   int* head;
   int4* queue;     // [W*H] pixels whose association search continues past the thread-owned rings
-  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take, [2] occupied tiles, [3] next tile
-  int4* tiles;     // [ceil(W/16) ceil(H/16)] 16 x 16 tiles holding a valid depth pixel (0, x, y, tiles per row)
+  unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take, [2] association units, [3] unused
+  int4* tiles;     // [8 ceil(W/16) ceil(H/16)] association units: 16 x 2 pixels holding a valid depth (0, x0, y0, 0)
   unsigned long long* zbuf;
   int* corr;
   Acc4* acc;
