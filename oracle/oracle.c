@@ -462,6 +462,10 @@ void orc_visibility(void* h, const double* v, const double* n, const int32_t* nv
                     const int32_t* zamb, int32_t* vis, int32_t* pix, int32_t* marg) {
   orc_model* m = (orc_model*)h;
   const double tol_m = 1e-5, tol_px = 1e-3;
+  /* facing: n.p < 0 is decided on normals summed from face normals of the posed mesh; on a dense mesh
+   * (edges ~1 mm long at coordinates ~1 m) an FP32 evaluation gets their direction to ~1e-5 rad, so a
+   * vertex with |n.p| < 1e-4 |p| (its normal within 1e-4 rad of the view ray's normal plane) is marginal */
+  const double tol_facing = 1e-4;
   for (int i = 0; i < m->V; ++i) {
     const double* p = v + 3 * i;
     vis[i] = 0; pix[i] = -1;
@@ -472,7 +476,8 @@ void orc_visibility(void* h, const double* v, const double* n, const int32_t* nv
     double fu = floor(u + 0.5), fv = floor(vv + 0.5);
     if (marg) {
       double ru = u + 0.5 - fu, rv = vv + 0.5 - fv;
-      if (fabs(nd) < tol_m || ru < tol_px || ru > 1 - tol_px || rv < tol_px || rv > 1 - tol_px) marg[i] = 1;
+      const double pl = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+      if (fabs(nd) < tol_facing * pl || ru < tol_px || ru > 1 - tol_px || rv < tol_px || rv > 1 - tol_px) marg[i] = 1;
     }
     if (!(nd < 0)) continue;
     if (fu < 0 || fv < 0 || fu >= m->W || fv >= m->H) continue;
