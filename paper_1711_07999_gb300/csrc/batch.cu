@@ -47,7 +47,7 @@ struct trk_batch {
   int device = 0;
   int pose_iters = 0, shape_iters = 0, shape_sweeps = 0, precision = 0, shape_solver = 0;
   int max_links = 0, max_np = 0;
-  int assoc_blocks = 608;     // persistent association blocks
+  int assoc_blocks = kAssocBlocksPerSM * 152;  // persistent association blocks
   int tail_blocks = 304;      // association-tail blocks (shared by all sessions' queues)
   Dev* d_devs = nullptr;
   unsigned* d_ctl = nullptr;  // [0] association units of the frame, [1] unused, [2] tail counter
@@ -462,7 +462,7 @@ trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const
   v.solver = p0.shape_solver;
   v.precision = p0.precision;
   v.max_links = max_links;
-  v.assoc_blocks = 4 * 152;
+  v.assoc_blocks = kAssocBlocksPerSM * 152;
   v.tail_blocks = 2 * 152;
   v.d_devs = reinterpret_cast<const Dev*>(dbuf + o_devs);
   for (int k = 0; k < kKinds; ++k) {

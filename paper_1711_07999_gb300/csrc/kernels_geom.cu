@@ -249,16 +249,6 @@ __device__ __forceinline__ void consider(int i, float3 p, float4 r, float tau2, 
   }
 }
 
-// the rest of a bucket after its first record: walk from the head until the first record is reached
-__device__ __forceinline__ void scan_rest(const Dev& d, int h, int first, float3 p, float tau2, int& best, float& bd2) {
-  // a bucket list never holds more than |V| entries; the hop bound only guards against misuse
-  for (int hops = 0; h >= 0 && h != first && hops < d.V; ++hops) {
-    const float4 r = d.rec[h];
-    consider(h, p, r, tau2, best, bd2);
-    h = __float_as_int(r.w);
-  }
-}
-
 // bucket t (0 <= t < 8r) of the ring of Chebyshev radius r around (px, py), or -1 outside the image
 __device__ __forceinline__ int ring_bucket(int px, int py, int r, int t, int W, int H) {
   int x, y;
@@ -270,22 +260,60 @@ __device__ __forceinline__ int ring_bucket(int px, int py, int r, int t, int W, 
   return (x >= 0 && y >= 0 && x < W && y < H) ? y * W + x : -1;
 }
 
-// Scans up to N buckets whose pixel indices are in q[0..N) (-1 = none) with all first loads in flight.
-template <int N>
-__device__ __forceinline__ void scan_group(const Dev& d, const int* q, float3 p, float tau2, int& best, float& bd2) {
-  int h[N];
-  float4 f[N];
-#pragma unroll
-  for (int u = 0; u < N; ++u) {
-    h[u] = q[u] >= 0 ? __ldg(&d.head[q[u]]) : -1;
-    f[u] = q[u] >= 0 ? d.pixrec[q[u]] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+// The rest of a bucket after its first record: walk from the head until the first record is reached.
+__device__ __forceinline__ void scan_rest(const Dev& d, int h, int first, float3 p, float tau2, int& best, float& bd2) {
+  // a bucket list never holds more than |V| entries; the hop bound only guards against misuse
+  for (int hops = 0; h >= 0 && h != first && hops < d.V; ++hops) {
+    const float4 r = d.rec[h];
+    consider(h, p, r, tau2, best, bd2);
+    h = __float_as_int(r.w);
   }
+}
+
+// Scans up to N buckets whose pixel indices are in q[0..N) (-1 = none), every head and first record in
+// flight at once.  The rest of the lists: one after the other (kSideBySide false: the fewest registers,
+// for the thread-per-pixel pass whose occupancy pays more) or all N side by side, one load per list still
+// open per round trip (a pixel then waits for its longest list, not for the sum of its lists).
+template <int N, bool kSideBySide>
+__device__ __forceinline__ void scan_group(const Dev& d, const int* q, float3 p, float tau2, int& best, float& bd2) {
+  int h[N], first[N];
+  {
+    float4 f[N];
 #pragma unroll
-  for (int u = 0; u < N; ++u) {
-    if (h[u] < 0) continue;
-    const int first = __float_as_int(f[u].w);
-    consider(first, p, f[u], tau2, best, bd2);
-    if (h[u] != first) scan_rest(d, h[u], first, p, tau2, best, bd2);
+    for (int u = 0; u < N; ++u) {
+      h[u] = q[u] >= 0 ? __ldg(&d.head[q[u]]) : -1;
+      f[u] = q[u] >= 0 ? d.pixrec[q[u]] : make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    }
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      first[u] = __float_as_int(f[u].w);
+      if (h[u] >= 0) consider(first[u], p, f[u], tau2, best, bd2);
+      if (h[u] == first[u]) h[u] = -1;  // h[u]: the next record of list u still to visit (-1: none)
+      if constexpr (!kSideBySide) {
+        if (h[u] >= 0) scan_rest(d, h[u], first[u], p, tau2, best, bd2);
+      }
+    }
+  }
+  if constexpr (kSideBySide) {
+    // a list never holds more than |V| entries; the round bound only guards against misuse
+#pragma unroll 1
+    for (int round = 0; round < d.V; ++round) {
+      bool open = false;
+#pragma unroll
+      for (int u = 0; u < N; ++u) open |= h[u] >= 0;
+      if (!open) break;
+      float4 r[N];
+#pragma unroll
+      for (int u = 0; u < N; ++u)
+        if (h[u] >= 0) r[u] = d.rec[h[u]];
+#pragma unroll
+      for (int u = 0; u < N; ++u)
+        if (h[u] >= 0) {
+          consider(h[u], p, r[u], tau2, best, bd2);
+          const int next = __float_as_int(r[u].w);
+          h[u] = (next == first[u] || next < 0) ? -1 : next;
+        }
+    }
   }
 }
 
@@ -338,7 +366,7 @@ __device__ __forceinline__ void associate_impl(const Dev& d, int px0, int py0) {
     open = true;
     if (c.R == 0) {
       const int q0[1] = {k};
-      scan_group<1>(d, q0, p, tau2, best, bd2);
+      scan_group<1, false>(d, q0, p, tau2, best, bd2);
       open = false;
     } else {
       // rings 0 and 1 (9 buckets) in two rounds of independent loads: the pixel's own bucket with the
@@ -347,10 +375,10 @@ __device__ __forceinline__ void associate_impl(const Dev& d, int px0, int py0) {
       q[0] = k;
 #pragma unroll
       for (int u = 0; u < 4; ++u) q[1 + u] = ring_bucket(px, py, 1, u, c.W, c.H);
-      scan_group<5>(d, q, p, tau2, best, bd2);
+      scan_group<5, false>(d, q, p, tau2, best, bd2);
 #pragma unroll
       for (int u = 0; u < 4; ++u) q[u] = ring_bucket(px, py, 1, 4 + u, c.W, c.H);
-      scan_group<4>(d, q, p, tau2, best, bd2);
+      scan_group<4, false>(d, q, p, tau2, best, bd2);
       const float lb = dep * (1.0f + 0.499f) * c.kappa;
       if (lb > c.tau || (best >= 0 && lb * lb > bd2) || c.R == 1) open = false;
     }
@@ -406,7 +434,7 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
         while (t < nb && t >= 8 * r) t -= 8 * r++;  // bucket t of the group: ring r, position t
         q[u] = t0 + gl + GL * u < nb ? ring_bucket(px, py, r, t, c.W, c.H) : -1;
       }
-      scan_group<PL>(d, q, p, tau2, wb, wd2);
+      scan_group<PL, true>(d, q, p, tau2, wb, wd2);
     }
     unsigned long long kk = key_of(wb, wd2);
     kk = kk < key ? kk : key;
@@ -434,20 +462,25 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
 // interleaving spreads the units of costly sessions over all warps.  In a batch each warp keeps its own
 // copy of its unit's session descriptor in shared memory (reloaded when the session changes).  Pixels
 // outside the units keep the "no correspondence" the frame's depth copy wrote.
-__global__ void __launch_bounds__(kBlock, 4) k_associate(const Dev* devs, const int4* units, const unsigned* ctl, Dev d0) {
+__global__ void __launch_bounds__(kBlock, kAssocBlocksPerSM) k_associate(const Dev* devs, const int4* units, const unsigned* ctl, Dev d0) {
   __shared__ Dev sd[kBlock / 32];
   const bool single = devs == nullptr;
   const unsigned n = single ? d0.qctl[2] : ctl[0];
   const int4* list = single ? d0.tiles : units;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned nw = gridDim.x * (kBlock / 32);
-  int cur = -1;
-  for (unsigned u = blockIdx.x * (kBlock / 32) + w; u < n; u += nw) {
-    const int4 t = list[u];  // (session, x0, y0, 0)
-    if (single) {
+  if (single) {
+#pragma unroll 1
+    for (unsigned u = blockIdx.x * (kBlock / 32) + w; u < n; u += nw) {
+      const int4 t = list[u];  // (session, x0, y0, 0)
       associate_impl(d0, t.y, t.z);
-      continue;
     }
+    return;
+  }
+  int cur = -1;
+#pragma unroll 1
+  for (unsigned u = blockIdx.x * (kBlock / 32) + w; u < n; u += nw) {
+    const int4 t = list[u];
     if (t.x != cur) {
       __syncwarp();  // every lane is done with the previous descriptor
       const int* src = reinterpret_cast<const int*>(devs + t.x);
@@ -531,7 +564,8 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const 
 
 void launch_associate(const Dev& d, cudaStream_t st) {
   const int nunits = ((d.cam.W + 15) / 16) * ((d.cam.H + 1) / 2);
-  k_associate<<<min((nunits + kBlock / 32 - 1) / (kBlock / 32), 4 * 152), kBlock, 0, st>>>(nullptr, nullptr, nullptr, d);
+  k_associate<<<min((nunits + kBlock / 32 - 1) / (kBlock / 32), kAssocBlocksPerSM * 152), kBlock, 0, st>>>(nullptr, nullptr,
+                                                                                                   nullptr, d);
   k_associate_tail<<<2 * 152, 32 * kTailWarps, 0, st>>>(d);
 }
 

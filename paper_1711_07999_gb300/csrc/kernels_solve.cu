@@ -300,8 +300,24 @@ struct TileAcc {
   }
 };
 
-// A [J r] block covers jtj_group consecutive blocks of 256 vertices: each one's rows are formed and
-// staged in turn and added to the same tiles, so the block writes one partial for up to 256 G rows.
+// Every input of vertex i's row (RowSlot of a vertex known to be in A; slot and base set by the caller).
+__device__ __forceinline__ void row_inputs(const Dev& d, int i, int phi_buf, RowSlot& rs) {
+  rs.i = i;
+  rs.inA = true;
+  rs.a4 = d.acc[i];
+  rs.nn = d.n[i];
+  rs.v = d.v[i];
+  rs.x0 = d.v0[i];
+  rs.ph = d.phi[phi_buf][i];
+  rs.bi = d.bidx[i];
+  rs.bw = d.bw[i];
+}
+
+// A [J r] block covers jtj_group consecutive blocks of 256 vertices.  Its vertices in A are listed first,
+// in vertex order (a vertex's thread tests c_i >= 1 and a valid normal: two small loads), and their rows
+// are then formed 256 at a time by consecutive threads -- every thread of a chunk holds a row, instead of
+// the third of a vertex block's threads whose vertices are in A -- staged, and added to the same tiles,
+// so the block writes one partial for up to 256 G rows.
 // The symmetric product needs only the tiles (ty, tx) with ty <= tx among the nt x nt tiles that hold
 // columns < NP; S groups of nt (nt + 1) / 2 threads (S = 2 for NP <= 60 at T = 4) each sweep every S-th
 // staged row, and the first group adds the other groups' tiles, in group order, before the block writes
@@ -314,8 +330,8 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
   DQ* sHd = reinterpret_cast<DQ*>(Js + kBlock * ROW);
   float* sXi = reinterpret_cast<float*>(sHd + d.L);
   int* sPar = reinterpret_cast<int*>(sXi + 6 * d.L);
-  __shared__ int s_warp[kBlock / 32];
-  const int tid = threadIdx.x, G = d.jtj_group;
+  __shared__ int s_cnt[kMaxJtjGroup * (kBlock / 32)];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, G = d.jtj_group;
   const int NP = d.NP;
   const int nt = (NP + T - 1) / T;
   const int ntiles = nt * (nt + 1) / 2;
@@ -327,35 +343,62 @@ __device__ __forceinline__ void resid_jtj_impl(const Dev& d, BlockPos bp, int ph
     ++ty;
   }
   const int tx = ty + k;
-  TileAcc<T> acc;
-  acc.zero();
-  int done = 0;  // rows added so far (the same in every thread)
-  bool tables = false;
-  for (int sub = 0; sub < G; ++sub) {
-    const int vb = bp.x * G + sub;
-    if (vb * kBlock >= d.V) break;
-    RowSlot rs;
-    const int total = block_rows(d, vb, bp.x * kBlock * G + done, phi_buf, s_warp, rs);
-    if (total == 0) {
-      __syncthreads();  // s_warp is rewritten by the next vertex block
-      continue;
-    }
-    if (!tables) {
-      load_link_tables(d, sHd, sXi, sPar);
-      tables = true;
-    }
-    __syncthreads();
-    float r2;
-    jacobian_row(d, rs, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, r2);
-    __syncthreads();
-    if (h < S)
-      for (int s = h; s < total; s += S) acc.add_row(Js + s * ROW, ty, tx);
-    done += total;
+  // the block's rows: membership of A of vertex tid of each vertex block, counted per (block, warp)
+  unsigned m[kMaxJtjGroup];
+#pragma unroll
+  for (int sub = 0; sub < kMaxJtjGroup; ++sub) {
+    const int i = (bp.x * G + sub) * kBlock + tid;
+    bool inA = false;
+    if (sub < G && i < d.V) inA = d.acc[i].w >= 1 && d.n[i].w > 0.f;
+    m[sub] = __ballot_sync(0xffffffffu, inA);
+    if (lane == 0) s_cnt[sub * (kBlock / 32) + w] = __popc(m[sub]);
   }
-  if (done == 0) {  // nothing to add: the reduction skips this block's (unwritten) partial
+  load_link_tables(d, sHd, sXi, sPar);
+  __syncthreads();
+  int total = 0;
+  for (int q = 0; q < G * (kBlock / 32); ++q) total += s_cnt[q];
+  if (total == 0) {  // nothing to add: the reduction skips this block's (unwritten) partial
     if (tid == 0) d.jtj_rows[bp.x] = 0;
     return;
   }
+  {  // the list, in vertex order, staged where the rows go (each thread takes its entries before any row)
+    int* s_idx = reinterpret_cast<int*>(Js);
+    int off = 0;
+#pragma unroll
+    for (int sub = 0; sub < kMaxJtjGroup; ++sub) {
+      if (sub >= G) break;
+      int before = off;
+      for (int q = sub * (kBlock / 32); q < sub * (kBlock / 32) + w; ++q) before += s_cnt[q];
+      if ((m[sub] >> lane) & 1u) s_idx[before + __popc(m[sub] & ((1u << lane) - 1u))] = (bp.x * G + sub) * kBlock + tid;
+      for (int q = 0; q < kBlock / 32; ++q) off += s_cnt[sub * (kBlock / 32) + q];
+    }
+  }
+  __syncthreads();
+  int mine[kMaxJtjGroup];
+#pragma unroll
+  for (int c = 0; c < kMaxJtjGroup; ++c) mine[c] = c * kBlock + tid < total ? reinterpret_cast<const int*>(Js)[c * kBlock + tid] : -1;
+  __syncthreads();
+  TileAcc<T> acc;
+  acc.zero();
+#pragma unroll
+  for (int c = 0; c < kMaxJtjGroup; ++c) {
+    const int c0 = c * kBlock;
+    if (c0 >= total) break;
+    const int rows = min(kBlock, total - c0);
+    if (c > 0) __syncthreads();  // the previous chunk's rows have been added
+    if (mine[c] >= 0) {
+      RowSlot rs;
+      row_inputs(d, mine[c], phi_buf, rs);
+      rs.slot = tid;
+      rs.base = bp.x * kBlock * G + c0;
+      float r2;
+      jacobian_row(d, rs, phi_buf, Js, ROW, 16 * T, sHd, sXi, sPar, r2);
+    }
+    __syncthreads();
+    if (h < S)
+      for (int s = h; s < rows; s += S) acc.add_row(Js + s * ROW, ty, tx);
+  }
+  const int done = total;
   if (S > 1) {  // the groups' tiles, added into group 0's in group order
     __syncthreads();  // every group's sweep is done: the staged rows are free
     float* red = Js;

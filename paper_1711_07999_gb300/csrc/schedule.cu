@@ -199,7 +199,7 @@ std::string entry_text(const trk_schedule_config& c, double ms) {
 trk_schedule_config default_config(int n) {
   trk_schedule_config c{};
   c.groups = 1;
-  c.assoc_blocks = 4 * 152;
+  c.assoc_blocks = kAssocBlocksPerSM * 152;
   c.tail_blocks = 2 * 152;
   (void)n;
   return c;
@@ -337,7 +337,7 @@ trk_status trk_schedule_autotune(trk_schedule* s, const float* const* d_depths, 
   }
   if (err == TRK_OK && best.groups < n) {
     const trk_schedule_config base = best;
-    for (int a : {2 * 152, 4 * 152, 8 * 152})
+    for (int a : {2 * 152, kAssocBlocksPerSM * 152, 2 * kAssocBlocksPerSM * 152})
       for (int t : {152, 2 * 152, 4 * 152}) {
         if (a == base.assoc_blocks && t == base.tail_blocks) continue;
         trk_schedule_config c = base;

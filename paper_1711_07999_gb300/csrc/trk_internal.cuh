@@ -19,7 +19,9 @@ namespace trk {
 
 constexpr int kMaxLinks = 79;       // NP = P + 1 <= 80
 constexpr int kMaxNP = 80;
+constexpr int kMaxJtjGroup = 4;    // vertex blocks of 256 per [J r] block at most (trk_params.jtj_group)
 constexpr int kUnitsPerTile = 8;   // association units (16 x 2 pixels) per 16 x 16 tile
+constexpr int kAssocBlocksPerSM = 4;  // resident association blocks per SM (registers sized for it)
 constexpr int kCandidates = 6;      // damping values tried per LM iteration: lambda * 10^c, c = 0..5
 constexpr float kFix = 1073741824.0f;  // 2^30: fixed-point scale of the per-vertex sums
 
