@@ -52,7 +52,7 @@ struct trk_batch {
   Dev* d_devs = nullptr;
   unsigned* d_ctl = nullptr;  // [0] association units of the frame, [1] unused, [2] tail counter
   unsigned* d_prefix = nullptr;  // [n + 1] queued pixels before each session
-  int4* d_tiles = nullptr;    // association units of the frame (session, x0, y0, 0): 16 x 2 pixels with a valid depth
+  AssocUnit* d_tiles = nullptr;  // association units of the frame (up to 32 valid pixels of a tile each)
   Table tables[kKinds];
   const float** d_srcs = nullptr;  // device copy of the per-session depth pointers of the current frame
   const float** h_srcs = nullptr;  // pinned, kSrcSlots slots of one pointer per session
@@ -106,7 +106,7 @@ struct FrameView {
   Table tables[kKinds];
   unsigned* d_ctl = nullptr;        // [3]
   unsigned* d_prefix = nullptr;     // [B + 1]
-  int4* d_tiles = nullptr;          // [tables[kAssoc].n]
+  AssocUnit* d_tiles = nullptr;     // [kUnitsPerTile tables[kAssoc].n]
   const float* const* d_srcs = nullptr;  // [B] depth of each session (device-readable)
   const Dev* const* host_devs = nullptr;  // [B] the sessions' descriptors on the host
   int reduce_threads = 32;                // the reduction's block: the largest need of the sessions
@@ -294,7 +294,7 @@ trk_status batch_create(trk_session* const* sessions, int n_sessions, int assoc_
   }
   BCK(cudaMalloc(&b->d_ctl, sizeof(unsigned) * 3));
   BCK(cudaMalloc(&b->d_prefix, sizeof(unsigned) * (n_sessions + 1)));
-  BCK(cudaMalloc(&b->d_tiles, sizeof(int4) * kUnitsPerTile * std::max(b->tables[kAssoc].n, 1)));
+  BCK(cudaMalloc(&b->d_tiles, sizeof(AssocUnit) * kUnitsPerTile * std::max(b->tables[kAssoc].n, 1)));
   BCK(cudaMalloc(&b->d_srcs, sizeof(float*) * devs.size()));
   BCK(cudaMallocHost(&b->h_srcs, sizeof(float*) * devs.size() * kSrcSlots));
   for (cudaEvent_t& e : b->src_ev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -374,7 +374,7 @@ size_t batch_step_bytes_of(const trk_session* s) {
   }
   int gx = 0, gy = 0;
   blocks_of(d, kAssoc, gx, gy);
-  return n + sizeof(int4) * kUnitsPerTile * (size_t)gx * gy;  // the step's list of association units
+  return n + sizeof(AssocUnit) * kUnitsPerTile * (size_t)gx * gy;  // the step's list of association units
 }
 
 trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const float* const* srcs,
@@ -417,7 +417,7 @@ trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const
   const size_t upload = off;
   const size_t o_ctl = off; off = align16(off + sizeof(unsigned) * 4);
   const size_t o_prefix = off; off = align16(off + sizeof(unsigned) * (n + 1));
-  const size_t o_tiles = off; off = align16(off + sizeof(int4) * kUnitsPerTile * std::max<size_t>(maps[kAssoc].size(), 1));
+  const size_t o_tiles = off; off = align16(off + sizeof(AssocUnit) * kUnitsPerTile * std::max<size_t>(maps[kAssoc].size(), 1));
   const size_t total = off;
   // the previous upload out of the pinned mirror has been done
   cudaError_t e = cudaEventSynchronize(bs->uploaded);
@@ -471,7 +471,7 @@ trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const
   }
   v.d_ctl = reinterpret_cast<unsigned*>(dbuf + o_ctl);
   v.d_prefix = reinterpret_cast<unsigned*>(dbuf + o_prefix);
-  v.d_tiles = reinterpret_cast<int4*>(dbuf + o_tiles);
+  v.d_tiles = reinterpret_cast<AssocUnit*>(dbuf + o_tiles);
   v.d_srcs = reinterpret_cast<const float* const*>(dbuf + o_srcs);
   v.host_devs = hd.data();
   v.reduce_threads = reduce_threads_for(hd.data(), n);

@@ -337,13 +337,12 @@ __device__ __forceinline__ float3 back_project(const Cam& c, int px, int py, flo
                      (float)((double)dep - (double)c.oz));
 }
 
-// One warp's unit: the 32 pixels of rows py0, py0 + 1 and columns px0 .. px0 + 15 (a lane each).
-__device__ __forceinline__ void associate_impl(const Dev& d, int px0, int py0) {
+// One lane's pixel (px, py) of a warp's unit (active false: the lane has none; it still takes part in
+// the warp's votes).
+__device__ __forceinline__ void associate_impl(const Dev& d, int px, int py, bool active) {
   const Cam c = d.cam;
   const int lane = threadIdx.x & 31;
-  const int px = px0 + (lane & 15);
-  const int py = py0 + (lane >> 4);
-  const bool inimg = px < c.W && py < c.H;
+  const bool inimg = active && px < c.W && py < c.H;
   const int k = py * c.W + px;
   const float dep = inimg ? d.depth[k] : 0.f;
   const float tau2 = c.tau * c.tau;
@@ -456,39 +455,42 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
   return best >= 0;
 }
 
-// Persistent warps take the frame's occupied units (16 x 2 pixels with a valid depth; one session's from
-// k_tiles, a batch's from the depth gather), warp w the units w, w + (warps in the grid), ...: no counter
-// and no block barrier, so a warp whose pixels are cheap goes on to its next unit at once, and the
-// interleaving spreads the units of costly sessions over all warps.  In a batch each warp keeps its own
-// copy of its unit's session descriptor in shared memory (reloaded when the session changes).  Pixels
-// outside the units keep the "no correspondence" the frame's depth copy wrote.
-__global__ void __launch_bounds__(kBlock, kAssocBlocksPerSM) k_associate(const Dev* devs, const int4* units, const unsigned* ctl, Dev d0) {
+// Persistent warps take the frame's association units (up to 32 pixels of a tile with a valid depth; one
+// session's from k_tiles, a batch's from the depth gather), warp w the units w, w + (warps in the grid),
+// ...: no counter and no block barrier, so a warp whose pixels are cheap goes on to its next unit at once,
+// and the interleaving spreads the units of costly sessions over all warps.  In a batch each warp keeps
+// its own copy of its unit's session descriptor in shared memory (reloaded when the session changes).
+// Pixels outside the units keep the "no correspondence" the frame's depth copy wrote.
+__global__ void __launch_bounds__(kBlock, kAssocBlocksPerSM) k_associate(const Dev* devs, const AssocUnit* units,
+                                                                          const unsigned* ctl, Dev d0) {
   __shared__ Dev sd[kBlock / 32];
   const bool single = devs == nullptr;
   const unsigned n = single ? d0.qctl[2] : ctl[0];
-  const int4* list = single ? d0.tiles : units;
+  const AssocUnit* list = single ? d0.units : units;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned nw = gridDim.x * (kBlock / 32);
   if (single) {
 #pragma unroll 1
     for (unsigned u = blockIdx.x * (kBlock / 32) + w; u < n; u += nw) {
-      const int4 t = list[u];  // (session, x0, y0, 0)
-      associate_impl(d0, t.y, t.z);
+      const int4 h = *reinterpret_cast<const int4*>(&list[u]);  // (session, x0, y0, pixels)
+      const int o = lane < h.w ? list[u].off[lane] : 0;
+      associate_impl(d0, h.y + (o & 15), h.z + (o >> 4), lane < h.w);
     }
     return;
   }
   int cur = -1;
 #pragma unroll 1
   for (unsigned u = blockIdx.x * (kBlock / 32) + w; u < n; u += nw) {
-    const int4 t = list[u];
-    if (t.x != cur) {
+    const int4 h = *reinterpret_cast<const int4*>(&list[u]);
+    const int o = lane < h.w ? list[u].off[lane] : 0;
+    if (h.x != cur) {
       __syncwarp();  // every lane is done with the previous descriptor
-      const int* src = reinterpret_cast<const int*>(devs + t.x);
+      const int* src = reinterpret_cast<const int*>(devs + h.x);
       for (int q = lane; q < (int)(sizeof(Dev) / 4); q += 32) reinterpret_cast<int*>(&sd[w])[q] = src[q];
       __syncwarp();
-      cur = t.x;
+      cur = h.x;
     }
-    associate_impl(sd[w], t.y, t.z);
+    associate_impl(sd[w], h.y + (o & 15), h.z + (o >> 4), lane < h.w);
   }
 }
 
@@ -569,18 +571,32 @@ void launch_associate(const Dev& d, cudaStream_t st) {
   k_associate_tail<<<2 * 152, 32 * kTailWarps, 0, st>>>(d);
 }
 
-// Appends the association units (16 x 2 pixels, one per warp of a 16 x 16 tile) of this block's tile
-// that hold a valid pixel to list, one counter update per tile.
-__device__ __forceinline__ void list_units(bool valid, int session, int tx, int ty, int4* list, unsigned* count) {
-  __shared__ unsigned s_mask;
-  if (threadIdx.x == 0) s_mask = 0;
+// Appends this block's tile's association units to list: its pixels with a valid depth, in row-major
+// order, 32 per unit (one counter update per tile).
+__device__ __forceinline__ void list_units(bool valid, int session, int tx, int ty, AssocUnit* list, unsigned* count) {
+  __shared__ int s_warp[kBlock / 32];
+  __shared__ unsigned s_first;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, valid);
+  if (lane == 0) s_warp[w] = __popc(m);
   __syncthreads();
-  if (__ballot_sync(0xffffffffu, valid) && (threadIdx.x & 31) == 0) atomicOr(&s_mask, 1u << (threadIdx.x >> 5));
-  __syncthreads();
-  if (threadIdx.x == 0 && s_mask) {
-    unsigned m = s_mask, at = atomicAdd(count, (unsigned)__popc(m));
-    for (; m; m &= m - 1) list[at++] = make_int4(session, tx * 16, ty * 16 + 2 * (__ffs(m) - 1), 0);
+  int before = 0, total = 0;
+#pragma unroll
+  for (int q = 0; q < kBlock / 32; ++q) {
+    before += q < w ? s_warp[q] : 0;
+    total += s_warp[q];
   }
+  if (total == 0) return;
+  const int nu = (total + 31) / 32;
+  if (threadIdx.x == 0) s_first = atomicAdd(count, (unsigned)nu);
+  __syncthreads();
+  if (valid) {
+    const int r = before + __popc(m & ((1u << lane) - 1u));
+    list[s_first + r / 32].off[r % 32] = (unsigned char)threadIdx.x;
+  }
+  if ((int)threadIdx.x < nu)
+    *reinterpret_cast<int4*>(&list[s_first + threadIdx.x]) =
+        make_int4(session, tx * 16, ty * 16, min(32, total - 32 * (int)threadIdx.x));
 }
 
 // One 16 x 16 tile per block: copies the frame's depth into the session's buffer, marks every pixel
@@ -598,7 +614,7 @@ __global__ void __launch_bounds__(kBlock) k_tiles(Dev d, const float* __restrict
     d.corr[k] = -1;
     valid = z > 0.f;
   }
-  list_units(valid, 0, tx, ty, d.tiles, &d.qctl[2]);
+  list_units(valid, 0, tx, ty, d.units, &d.qctl[2]);
 }
 
 void launch_tiles(const Dev& d, const float* src, cudaStream_t st) {
@@ -616,7 +632,7 @@ void launch_raster_b(const BatchGrid& g, int nblk, cudaStream_t st) {
 void launch_visibility_b(const BatchGrid& g, int nblk, cudaStream_t st) {
   if (nblk > 0) k_visibility_b<<<nblk, kBlock, 0, st>>>(g);
 }
-void launch_associate_b(const Dev* devs, int n_sessions, const int4* tiles, unsigned* ctl, unsigned* prefix,
+void launch_associate_b(const Dev* devs, int n_sessions, const AssocUnit* tiles, unsigned* ctl, unsigned* prefix,
                         int assoc_blocks, int tail_blocks, cudaStream_t st) {
   k_associate<<<assoc_blocks, kBlock, 0, st>>>(devs, tiles, ctl, Dev{});
   k_tail_prefix<<<1, 1024, 0, st>>>(devs, n_sessions, prefix);
@@ -626,7 +642,7 @@ void launch_associate_b(const Dev* devs, int n_sessions, const int4* tiles, unsi
 // Copies each session's depth frame from srcs[session] into the session's own depth buffer, one 16 x 16
 // tile per block, marks every pixel "no correspondence" and lists the association units (16 x 2 pixels)
 // that hold a valid depth.
-__global__ void __launch_bounds__(kBlock) k_gather_depth_b(BatchGrid g, const float* const* srcs, int4* units,
+__global__ void __launch_bounds__(kBlock) k_gather_depth_b(BatchGrid g, const float* const* srcs, AssocUnit* units,
                                                            unsigned* ctl) {
   const int4 m = g.map[blockIdx.x];
   const Dev& d = g.devs[m.x];
@@ -641,7 +657,7 @@ __global__ void __launch_bounds__(kBlock) k_gather_depth_b(BatchGrid g, const fl
   }
   list_units(valid, m.x, m.y, m.z, units, &ctl[0]);
 }
-void launch_gather_depth_b(const BatchGrid& g, int nblk, const float* const* srcs, int4* tiles, unsigned* ctl,
+void launch_gather_depth_b(const BatchGrid& g, int nblk, const float* const* srcs, AssocUnit* tiles, unsigned* ctl,
                            cudaStream_t st) {
   if (nblk > 0) k_gather_depth_b<<<nblk, kBlock, 0, st>>>(g, srcs, tiles, ctl);
 }

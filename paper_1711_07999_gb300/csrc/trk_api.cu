@@ -536,7 +536,7 @@ void carve_all(trk_session* s) {
   carve(s, &d.v, V); carve(s, &d.n, V); carve(s, &d.fn, F); carve(s, &d.rec, V);
   carve(s, &d.head, npx); carve(s, &d.zbuf, npx); carve(s, &d.corr, npx);
   carve(s, &d.pixrec, npx); carve(s, &d.queue, npx); carve(s, &d.qctl, 4);
-  carve(s, &d.tiles, (size_t)kUnitsPerTile * ((d.cam.W + 15) / 16) * ((d.cam.H + 15) / 16));
+  carve(s, &d.units, (size_t)kUnitsPerTile * ((d.cam.W + 15) / 16) * ((d.cam.H + 15) / 16));
   carve(s, &d.acc, V); carve(s, &d.vispix, V); carve(s, &d.rg, V); carve(s, &d.phi0, V);
   carve(s, &dadj_off, V + 1); carve(s, &dadj, s->hm.adj.size());
   d.cg_x = d.cg_r = d.cg_z = d.cg_p = d.cg_ap = nullptr;

@@ -264,6 +264,13 @@ inline S set_error(S st, const char* msg) { return static_cast<S>(set_error_code
 
 namespace trk {
 
+// A warp's share of the association: up to 32 pixels of one 16 x 16 tile that hold a valid depth, in
+// row-major order (lane l takes pixel (x0 + off[l] % 16, y0 + off[l] / 16) for l < n).
+struct __align__(16) AssocUnit {
+  int session, x0, y0, n;
+  unsigned char off[32];
+};
+
 // Device pointers and constants of one session (passed by value to every kernel).
 struct Dev {
   int V, F, L, NP;  // NP = L + 1 (the residual column of [J r])
@@ -302,7 +309,7 @@ struct Dev {
   int* head;
   int4* queue;     // [W*H] pixels whose association search continues past the thread-owned rings
   unsigned int* qctl;  // [0] queued pixels, [1] next queue entry to take, [2] association units, [3] unused
-  int4* tiles;     // [8 ceil(W/16) ceil(H/16)] association units: 16 x 2 pixels holding a valid depth (0, x0, y0, 0)
+  AssocUnit* units;  // [8 ceil(W/16) ceil(H/16)] association units of the frame (up to 32 valid pixels of a tile)
   unsigned long long* zbuf;
   int* corr;
   Acc4* acc;
@@ -353,9 +360,9 @@ struct BatchGrid;
 void launch_skin_b(const BatchGrid& g, int nblk, int max_links, int phi_buf, unsigned* ctl, cudaStream_t st);
 void launch_raster_b(const BatchGrid& g, int nblk, cudaStream_t st);
 void launch_visibility_b(const BatchGrid& g, int nblk, cudaStream_t st);
-void launch_associate_b(const Dev* devs, int n_sessions, const int4* tiles, unsigned* ctl, unsigned* prefix,
+void launch_associate_b(const Dev* devs, int n_sessions, const AssocUnit* units, unsigned* ctl, unsigned* prefix,
                         int assoc_blocks, int tail_blocks, cudaStream_t st);
-void launch_gather_depth_b(const BatchGrid& g, int nblk, const float* const* srcs, int4* tiles, unsigned* ctl,
+void launch_gather_depth_b(const BatchGrid& g, int nblk, const float* const* srcs, AssocUnit* units, unsigned* ctl,
                            cudaStream_t st);
 void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGrid& gr, int nr, int max_links,
                                int precision, int phi_buf, int slot, cudaStream_t st, int reduce_threads);
