@@ -209,17 +209,17 @@ def kernel_source_hash():
 
 def ncu_traffic(kernel):
     """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it was captured from the
-    current kernel sources (else None)."""
+    current kernel sources (an entry's own source hash, else the file's; otherwise None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    if t.get("kernel_source_hash") != kernel_source_hash():
-        return None
     e = t.get("kernels", {}).get(kernel)
-    return None if e is None else e.get("dram_bytes_per_launch_full_size")
+    if e is None or e.get("kernel_source_hash", t.get("kernel_source_hash")) != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
 
 
 # ------------------------------------------------------------------------------------------------
@@ -478,7 +478,8 @@ def run_schedule(sessions, dev_frames, n_seq, steps, warmup, flush):
         torch.cuda.synchronize()
         ev = []
         for k in range(steps):
-            flush.fill_(k & 0xFF)
+            with torch.cuda.stream(st):  # the flush is done before the step starts (same stream)
+                flush.fill_(k & 0xFF)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
             sc.track_device(ptrs(warmup + k), st.cuda_stream)
