@@ -240,12 +240,21 @@ void launch_visibility(const Dev& d, cudaStream_t st) {
 // ---------------------------------------------------------------------------------------------
 constexpr int kRingsPerThread = 1;
 
-__device__ __forceinline__ void consider(int i, float3 p, float4 r, float tau2, int& best, float& bd2) {
+// The nearest candidate so far: its vertex (-1: none), squared distance and position (the record's, which
+// holds the vertex's skinned position bit for bit, so the pixel's sums need no second load of it).
+struct Best {
+  int i;
+  float d2;
+  float3 v;
+};
+
+__device__ __forceinline__ void consider(int i, float3 p, float4 r, float tau2, Best& b) {
   const float dx = p.x - r.x, dy = p.y - r.y, dz = p.z - r.z;
   const float d2 = dx * dx + dy * dy + dz * dz;
-  if (d2 <= tau2 && (best < 0 || d2 < bd2 || (d2 == bd2 && i < best))) {
-    best = i;
-    bd2 = d2;
+  if (d2 <= tau2 && (b.i < 0 || d2 < b.d2 || (d2 == b.d2 && i < b.i))) {
+    b.i = i;
+    b.d2 = d2;
+    b.v = make_float3(r.x, r.y, r.z);
   }
 }
 
@@ -261,11 +270,11 @@ __device__ __forceinline__ int ring_bucket(int px, int py, int r, int t, int W, 
 }
 
 // The rest of a bucket after its first record: walk from the head until the first record is reached.
-__device__ __forceinline__ void scan_rest(const Dev& d, int h, int first, float3 p, float tau2, int& best, float& bd2) {
+__device__ __forceinline__ void scan_rest(const Dev& d, int h, int first, float3 p, float tau2, Best& best) {
   // a bucket list never holds more than |V| entries; the hop bound only guards against misuse
   for (int hops = 0; h >= 0 && h != first && hops < d.V; ++hops) {
     const float4 r = d.rec[h];
-    consider(h, p, r, tau2, best, bd2);
+    consider(h, p, r, tau2, best);
     h = __float_as_int(r.w);
   }
 }
@@ -275,7 +284,7 @@ __device__ __forceinline__ void scan_rest(const Dev& d, int h, int first, float3
 // for the thread-per-pixel pass whose occupancy pays more) or all N side by side, one load per list still
 // open per round trip (a pixel then waits for its longest list, not for the sum of its lists).
 template <int N, bool kSideBySide>
-__device__ __forceinline__ void scan_group(const Dev& d, const int* q, float3 p, float tau2, int& best, float& bd2) {
+__device__ __forceinline__ void scan_group(const Dev& d, const int* q, float3 p, float tau2, Best& best) {
   int h[N], first[N];
   {
     float4 f[N];
@@ -287,10 +296,10 @@ __device__ __forceinline__ void scan_group(const Dev& d, const int* q, float3 p,
 #pragma unroll
     for (int u = 0; u < N; ++u) {
       first[u] = __float_as_int(f[u].w);
-      if (h[u] >= 0) consider(first[u], p, f[u], tau2, best, bd2);
+      if (h[u] >= 0) consider(first[u], p, f[u], tau2, best);
       if (h[u] == first[u]) h[u] = -1;  // h[u]: the next record of list u still to visit (-1: none)
       if constexpr (!kSideBySide) {
-        if (h[u] >= 0) scan_rest(d, h[u], first[u], p, tau2, best, bd2);
+        if (h[u] >= 0) scan_rest(d, h[u], first[u], p, tau2, best);
       }
     }
   }
@@ -309,7 +318,7 @@ __device__ __forceinline__ void scan_group(const Dev& d, const int* q, float3 p,
 #pragma unroll
       for (int u = 0; u < N; ++u)
         if (h[u] >= 0) {
-          consider(h[u], p, r[u], tau2, best, bd2);
+          consider(h[u], p, r[u], tau2, best);
           const int next = __float_as_int(r[u].w);
           h[u] = (next == first[u] || next < 0) ? -1 : next;
         }
@@ -321,8 +330,8 @@ __device__ __forceinline__ unsigned long long key_of(int best, float bd2) {
   return best < 0 ? ~0ull : (((unsigned long long)__float_as_uint(bd2) << 32) | (unsigned)best);
 }
 
-__device__ __forceinline__ void commit_pixel(const Dev& d, int best, float3 p) {
-  const float4 vb = d.v[best];
+// Adds pixel p's offset from its vertex (position vb) to the vertex's fixed-point sums.
+__device__ __forceinline__ void commit_pixel(const Dev& d, int best, float3 p, float3 vb) {
   unsigned long long* a = reinterpret_cast<unsigned long long*>(&d.acc[best]);
   atomicAdd(a + 0, (unsigned long long)__float2ll_rn((p.x - vb.x) * kFix));
   atomicAdd(a + 1, (unsigned long long)__float2ll_rn((p.y - vb.y) * kFix));
@@ -346,8 +355,7 @@ __device__ __forceinline__ void associate_impl(const Dev& d, int px, int py, boo
   const int k = py * c.W + px;
   const float dep = inimg ? d.depth[k] : 0.f;
   const float tau2 = c.tau * c.tau;
-  int best = -1;
-  float bd2 = 0.f;
+  Best best{-1, 0.f, make_float3(0.f, 0.f, 0.f)};
   float3 p = make_float3(0.f, 0.f, 0.f);
   bool open = false;
   if (dep > 0.f && d.association == 1) {
@@ -356,16 +364,16 @@ __device__ __forceinline__ void associate_impl(const Dev& d, int px, int py, boo
     const unsigned long long key = d.zbuf[k];
     if (key != ~0ull) {
       const int4 t = d.tris[(int)(unsigned)(key & 0xffffffffu)];
-      consider(t.x, p, d.v[t.x], tau2, best, bd2);
-      consider(t.y, p, d.v[t.y], tau2, best, bd2);
-      consider(t.z, p, d.v[t.z], tau2, best, bd2);
+      consider(t.x, p, d.v[t.x], tau2, best);
+      consider(t.y, p, d.v[t.y], tau2, best);
+      consider(t.z, p, d.v[t.z], tau2, best);
     }
   } else if (dep > 0.f) {
     p = back_project(c, px, py, dep);
     open = true;
     if (c.R == 0) {
       const int q0[1] = {k};
-      scan_group<1, false>(d, q0, p, tau2, best, bd2);
+      scan_group<1, false>(d, q0, p, tau2, best);
       open = false;
     } else {
       // rings 0 and 1 (9 buckets) in two rounds of independent loads: the pixel's own bucket with the
@@ -374,12 +382,12 @@ __device__ __forceinline__ void associate_impl(const Dev& d, int px, int py, boo
       q[0] = k;
 #pragma unroll
       for (int u = 0; u < 4; ++u) q[1 + u] = ring_bucket(px, py, 1, u, c.W, c.H);
-      scan_group<5, false>(d, q, p, tau2, best, bd2);
+      scan_group<5, false>(d, q, p, tau2, best);
 #pragma unroll
       for (int u = 0; u < 4; ++u) q[u] = ring_bucket(px, py, 1, 4 + u, c.W, c.H);
-      scan_group<4, false>(d, q, p, tau2, best, bd2);
+      scan_group<4, false>(d, q, p, tau2, best);
       const float lb = dep * (1.0f + 0.499f) * c.kappa;
-      if (lb > c.tau || (best >= 0 && lb * lb > bd2) || c.R == 1) open = false;
+      if (lb > c.tau || (best.i >= 0 && lb * lb > best.d2) || c.R == 1) open = false;
     }
   }
   // queue the open pixels (one atomic per warp)
@@ -387,10 +395,10 @@ __device__ __forceinline__ void associate_impl(const Dev& d, int px, int py, boo
   unsigned base = 0;
   if (lane == 0 && om) base = atomicAdd(&d.qctl[0], __popc(om));
   base = __shfl_sync(0xffffffffu, base, 0);
-  if (open) d.queue[base + __popc(om & ((1u << lane) - 1u))] = make_int4(k, best, __float_as_int(bd2), 0);
-  if (inimg && !open) d.corr[k] = best;
-  const bool done = !open && best >= 0;
-  if (done) commit_pixel(d, best, p);
+  if (open) d.queue[base + __popc(om & ((1u << lane) - 1u))] = make_int4(k, best.i, __float_as_int(best.d2), 0);
+  if (inimg && !open) d.corr[k] = best.i;
+  const bool done = !open && best.i >= 0;
+  if (done) commit_pixel(d, best.i, p, best.v);
   const unsigned m = __ballot_sync(0xffffffffu, done);
   if (lane == 0 && m) atomicAdd(&d.stats[0], __popc(m));
 }
@@ -417,8 +425,7 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
   const float dep = d.depth[k];
   const float3 p = back_project(c, px, py, dep);
   unsigned long long key = key_of(e.y, __int_as_float(e.z));
-  int wb = -1;
-  float wd2 = 0.f;
+  Best w{-1, 0.f, make_float3(0.f, 0.f, 0.f)};
   // rings r0..r1 at a time, as many whole rings as the group's load slots hold (at least one): scanning
   // rings past the one whose bound ends the search only confirms the argmin, so the result is the same
   constexpr int kSlots = GL * PL;
@@ -433,9 +440,9 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
         while (t < nb && t >= 8 * r) t -= 8 * r++;  // bucket t of the group: ring r, position t
         q[u] = t0 + gl + GL * u < nb ? ring_bucket(px, py, r, t, c.W, c.H) : -1;
       }
-      scan_group<PL, true>(d, q, p, tau2, wb, wd2);
+      scan_group<PL, true>(d, q, p, tau2, w);
     }
-    unsigned long long kk = key_of(wb, wd2);
+    unsigned long long kk = key_of(w.i, w.d2);
     kk = kk < key ? kk : key;
 #pragma unroll
     for (int o = GL / 2; o > 0; o >>= 1) {
@@ -450,7 +457,10 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
   const int best = key == ~0ull ? -1 : (int)(unsigned)(key & 0xffffffffu);
   if (gl == 0) {
     d.corr[k] = best;
-    if (best >= 0) commit_pixel(d, best, p);
+    if (best >= 0) {
+      const float4 vb = d.v[best];
+      commit_pixel(d, best, p, make_float3(vb.x, vb.y, vb.z));
+    }
   }
   return best >= 0;
 }
