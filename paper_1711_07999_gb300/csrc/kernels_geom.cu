@@ -18,8 +18,6 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 // Sec. 3.1: FK of the current Theta -> H_{j,Delta} and the joint twists Xi_j (one thread per link)
 // ---------------------------------------------------------------------------------------------
 __global__ void k_fk(Dev d) {
-  pdl_wait();
-  pdl_allow();
   __shared__ LinkTable lt;
   __shared__ DQ H0[kMaxLinks];
   for (int t = threadIdx.x; t < (int)(sizeof(LinkTable) / 4); t += blockDim.x)
@@ -69,9 +67,8 @@ __global__ void __launch_bounds__(kBlock) k_skin(BatchGrid g, Dev d0, int phi_bu
     return;
   }
   __shared__ Dev sd;
-  const BlockPos bp = batch_block(g, sd);
   if (ctl && blockIdx.x == 0 && threadIdx.x < 2) ctl[1 + threadIdx.x] = 0;  // tile and tail counters
-  skin_impl(sd, bp, phi_buf);
+  skin_impl(sd, batch_block(g, sd), phi_buf);
 }
 
 static int grid_for(int n, int block) { return (n + block - 1) / block; }
@@ -476,8 +473,6 @@ __device__ __forceinline__ bool tail_item(const Dev& d, unsigned item, int gl, u
 // Pixels outside the units keep the "no correspondence" the frame's depth copy wrote.
 __global__ void __launch_bounds__(kBlock, kAssocBlocksPerSM) k_associate(const Dev* devs, const AssocUnit* units,
                                                                           const unsigned* ctl, Dev d0) {
-  pdl_wait();
-  pdl_allow();
   __shared__ Dev sd[kBlock / 32];
   const bool single = devs == nullptr;
   const unsigned n = single ? d0.qctl[2] : ctl[0];
@@ -512,8 +507,6 @@ __global__ void __launch_bounds__(kBlock, kAssocBlocksPerSM) k_associate(const D
 // One session: the warps of all blocks take its queue entries, warp w the w-th, then the rest from the
 // session's counter (no counter traffic when the queue is no longer than the grid's warps).
 __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
-  pdl_wait();
-  pdl_allow();
   const int lane = threadIdx.x & 31, gl = lane, gbase = 0;
   const unsigned gmask = 0xffffffffu;
   const unsigned n = *(volatile unsigned*)&d.qctl[0];
@@ -531,8 +524,6 @@ __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail(Dev d) {
 
 // A batch: prefix[s] = queued pixels of the sessions before s (one block; at most 1024 x 4 sessions).
 __global__ void __launch_bounds__(1024) k_tail_prefix(const Dev* devs, int n_sessions, unsigned* prefix) {
-  pdl_wait();
-  pdl_allow();
   __shared__ unsigned part[1024];
   const int t = threadIdx.x;
   unsigned v[4], sum = 0;
@@ -563,8 +554,6 @@ __global__ void __launch_bounds__(1024) k_tail_prefix(const Dev* devs, int n_ses
 // the cache.
 __global__ void __launch_bounds__(32 * kTailWarps) k_associate_tail_batch(const Dev* devs, int n_sessions,
                                                                           const unsigned* prefix, unsigned* ctl) {
-  pdl_wait();
-  pdl_allow();
   constexpr int GL = kBatchTailLanes;
   const int lane = threadIdx.x & 31, gl = lane % GL, gbase = lane - gl;
   const unsigned gmask = ((1u << GL) - 1u) << gbase;
@@ -645,19 +634,19 @@ void launch_tiles(const Dev& d, const float* src, cudaStream_t st) {
 
 // ---- batched launches (one launch over the blocks of all sessions of a batch) ---------------------
 void launch_skin_b(const BatchGrid& g, int nblk, int max_links, int phi_buf, unsigned* ctl, cudaStream_t st) {
-  if (nblk > 0) launch_pdl(k_skin, nblk, kBlock, max_links * sizeof(DQ), st, g, Dev{}, phi_buf, ctl);
+  if (nblk > 0) k_skin<<<nblk, kBlock, max_links * sizeof(DQ), st>>>(g, Dev{}, phi_buf, ctl);
 }
 void launch_raster_b(const BatchGrid& g, int nblk, cudaStream_t st) {
-  if (nblk > 0) launch_pdl(k_raster_b, nblk, kBlock, 0, st, g);
+  if (nblk > 0) k_raster_b<<<nblk, kBlock, 0, st>>>(g);
 }
 void launch_visibility_b(const BatchGrid& g, int nblk, cudaStream_t st) {
-  if (nblk > 0) launch_pdl(k_visibility_b, nblk, kBlock, 0, st, g);
+  if (nblk > 0) k_visibility_b<<<nblk, kBlock, 0, st>>>(g);
 }
 void launch_associate_b(const Dev* devs, int n_sessions, const AssocUnit* tiles, unsigned* ctl, unsigned* prefix,
                         int assoc_blocks, int tail_blocks, cudaStream_t st) {
-  launch_pdl(k_associate, assoc_blocks, kBlock, 0, st, devs, tiles, ctl, Dev{});
-  launch_pdl(k_tail_prefix, 1, 1024, 0, st, devs, n_sessions, prefix);
-  launch_pdl(k_associate_tail_batch, tail_blocks, 32 * kTailWarps, 0, st, devs, n_sessions, prefix, ctl);
+  k_associate<<<assoc_blocks, kBlock, 0, st>>>(devs, tiles, ctl, Dev{});
+  k_tail_prefix<<<1, 1024, 0, st>>>(devs, n_sessions, prefix);
+  k_associate_tail_batch<<<tail_blocks, 32 * kTailWarps, 0, st>>>(devs, n_sessions, prefix, ctl);
 }
 
 // Copies each session's depth frame from srcs[session] into the session's own depth buffer, one 16 x 16

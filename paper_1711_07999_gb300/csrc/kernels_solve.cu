@@ -1649,24 +1649,24 @@ void launch_normal_equations_b(const BatchGrid* gj, const int* nj, const BatchGr
     } else {
       const int sm = jtj_smem_bytes(T, max_links);
       switch (T) {
-        case 1: launch_pdl(k_resid_jtj<1>, n, kBlock, sm, st, g, Dev{}, phi_buf); break;
-        case 2: launch_pdl(k_resid_jtj<2>, n, kBlock, sm, st, g, Dev{}, phi_buf); break;
-        case 3: launch_pdl(k_resid_jtj<3>, n, kBlock, sm, st, g, Dev{}, phi_buf); break;
-        case 4: launch_pdl(k_resid_jtj<4>, n, kBlock, sm, st, g, Dev{}, phi_buf); break;
-        default: launch_pdl(k_resid_jtj<5>, n, kBlock, sm, st, g, Dev{}, phi_buf); break;
+        case 1: k_resid_jtj<1><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+        case 2: k_resid_jtj<2><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+        case 3: k_resid_jtj<3><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+        case 4: k_resid_jtj<4><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
+        default: k_resid_jtj<5><<<n, kBlock, sm, st>>>(g, Dev{}, phi_buf); break;
       }
     }
   }
-  if (nr > 0) launch_pdl(k_reduce_jtj, nr, reduce_threads, 0, st, gr, Dev{}, slot);
+  if (nr > 0) k_reduce_jtj<<<nr, reduce_threads, 0, st>>>(gr, Dev{}, slot);
 }
 
 void launch_lm_b(const BatchGrid& glm, int nlm, const BatchGrid& gv, int nv, int max_links, int phi_buf,
                  cudaStream_t st) {
-  if (nlm > 0) launch_pdl(k_lm_solve, nlm, kSolveThreads, lm_solve_smem(max_links), st, glm, Dev{});
+  if (nlm > 0) k_lm_solve<<<nlm, kSolveThreads, lm_solve_smem(max_links), st>>>(glm, Dev{});
   if (nv > 0) {
     const size_t sm = kCandidates * max_links * sizeof(DQ);
-    launch_pdl(k_lm_eval, nv, kBlock, sm, st, gv, Dev{}, 0, kFirstPass);
-    launch_pdl(k_lm_eval, nv, kBlock, sm, st, gv, Dev{}, kFirstPass, kCandidates);
+    k_lm_eval<<<nv, kBlock, sm, st>>>(gv, Dev{}, 0, kFirstPass);
+    k_lm_eval<<<nv, kBlock, sm, st>>>(gv, Dev{}, kFirstPass, kCandidates);
   }
 }
 
@@ -1676,10 +1676,10 @@ int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int s
     launch_shape_pcg(gv, nv, Dev{}, max_links, sweeps, phi_src, slot, st);
     return 1 - phi_src;
   }
-  if (nv > 0) launch_pdl(k_shape_b, nv, kBlock, max_links * sizeof(DQ), st, gv, phi_src, slot);
+  if (nv > 0) k_shape_b<<<nv, kBlock, max_links * sizeof(DQ), st>>>(gv, phi_src, slot);
   int cur = 1 - phi_src;
   for (int s = 1; s < sweeps; ++s) {
-    if (nv > 0) launch_pdl(k_shape_sweep, nv, kBlock, 0, st, gv, Dev{}, cur);
+    if (nv > 0) k_shape_sweep<<<nv, kBlock, 0, st>>>(gv, Dev{}, cur);
     cur = 1 - cur;
   }
   return cur;

@@ -376,39 +376,7 @@ int launch_shape_b(const BatchGrid& gv, int nv, int max_links, int sweeps, int s
 struct BlockPos {
   int x, y, gx;
 };
-// Programmatic dependent launch (a batch's stage launches; one session's frame graph keeps ordinary
-// launches, which measured faster there).  A kernel launched by launch_pdl may start while the kernel before
-// it in the stream is still running: its blocks take SM slots the earlier kernel's last wave leaves free and do
-// their set-up, then pdl_wait() holds them until that kernel has completed and its writes are visible.
-// Every kernel so launched calls pdl_wait() before it reads (or writes) anything an earlier kernel touches,
-// and pdl_allow() after it: the next kernel may then start once every block of this one is past its wait
-// (calling it before the wait would let a whole chain of waiting kernels take the SMs' slots).  Both are
-// no-ops for a kernel launched the ordinary way.
-__device__ __forceinline__ void pdl_allow() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-template <typename... P, typename... A>
-inline void launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
-                       A&&... args) {
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
-}
-
-// A one-session launch: block position from the grid (after the earlier kernel of the stream is done).
-__device__ __forceinline__ BlockPos grid_pos() {
-  pdl_wait();
-  pdl_allow();
-  return BlockPos{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x};
-}
+__device__ __forceinline__ BlockPos grid_pos() { return BlockPos{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x}; }
 
 // A batched launch: block b works for session map[b].x at position (map[b].y, map[b].z) of a grid of
 // map[b].w blocks along x.
@@ -442,14 +410,10 @@ trk_status batch_step_launch(BatchStep* bs, trk_session* const* ss, int n, const
 // the two inlined copies of a stage body round identically: a session computes bit for bit the same
 // alone and in a batch.
 __device__ __forceinline__ BlockPos batch_block(const BatchGrid& g, Dev& sd) {
-  // the map and the descriptors are the batch's own (written before its first kernel): read while the
-  // earlier kernel of the stream may still run
   const int4 m = g.map[blockIdx.x];
   const int* src = reinterpret_cast<const int*>(g.devs + m.x);
   for (int t = threadIdx.x; t < (int)(sizeof(Dev) / 4); t += blockDim.x) reinterpret_cast<int*>(&sd)[t] = src[t];
   __syncthreads();
-  pdl_wait();
-  pdl_allow();
   return BlockPos{m.y, m.z, m.w};
 }
 constexpr BatchGrid kSingle{nullptr, nullptr};
