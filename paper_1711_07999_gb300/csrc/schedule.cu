@@ -294,6 +294,8 @@ trk_status trk_schedule_get_config(const trk_schedule* s, trk_schedule_config* o
   return TRK_OK;
 }
 
+constexpr int kSettleSteps = 4;  // frames tracked before the autotuner's timed trials
+
 trk_status trk_schedule_autotune(trk_schedule* s, const float* const* d_depths, int32_t reps, const char* cache_path,
                                  trk_schedule_config* chosen, double* ms_per_step) {
   if (!s || !d_depths || reps < 1) return set_error(TRK_ERR_INVALID_ARG, "trk_schedule_autotune: bad arguments");
@@ -317,10 +319,21 @@ trk_status trk_schedule_autotune(trk_schedule* s, const float* const* d_depths, 
     ms = t / reps;
     return TRK_OK;
   };
-  // coordinate search: the group count first (default blocks), then the association block counts
+  // coordinate search: the group count first (default blocks), then the association block counts.  The
+  // trials all track the same frame, so the sessions first settle on it under the default schedule: every
+  // candidate is then timed from the same converged state (without this, the first candidates would be
+  // timed on the frame's harder first visits and the later ones would be favoured).
   trk_schedule_config best = default_config(n);
   double best_ms = 1e30;
-  trk_status err = TRK_OK;
+  trk_status err = build(s, best);
+  for (int w = 0; err == TRK_OK && w < kSettleSteps; ++w) err = step(s, d_depths, st);
+  if (err != TRK_OK) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return err;
+  }
   std::vector<int> gs;
   for (int g : {1, 2, 4, 8, 16, 32})
     if (g < n) gs.push_back(g);
