@@ -23,7 +23,7 @@ import numpy as np
 
 import oracle
 
-TIE_M = 1e-5  # correspondence tie tolerance (spec tolerances, Sec. 4.1)
+TIE_M = 1e-5  # correspondence tie tolerance: two candidates closer than this are a tie (Sec. 4.1)
 
 
 def state_blob(theta, lam, phi, frames_done=1) -> bytes:

@@ -6,7 +6,7 @@ Before every frame the GPU session is put into the oracle's state (Theta, Phi, t
 R14, through trk_session_import) and both run that frame in lockstep (tests/sequence.py): at every
 iteration the GPU's correspondence map must equal the oracle's except at pixels the oracle flags as
 ties within 1e-5 m (Sec. 4.1), where the GPU's vertex must be a valid near argmin and the oracle takes
-the GPU's choice.  Then, on ALL joints and ALL vertices, with the benchmark spec's tolerances:
+the GPU's choice.  Then, on ALL joints and ALL vertices, with the tolerances the method is held to:
   joint values      1e-3 rad (measured: ~1e-5 rad)
   offsets           0.05 mm (measured: ~0.001 mm)
   energy            1e-5 relative per iteration, at the same state and correspondence map
