@@ -1,6 +1,7 @@
 """Frame-by-frame parity with the FP64 oracle on the benchmark sequence (50k vertices / 640x480, ten
-consecutive frames) and on the high-resolution case (200k vertices / 1280x720, three frames), plus the
-correspondence maps of a fused batch of uneven sessions.
+consecutive frames; two in each tensor-core mode) and on the high-resolution case (200k vertices /
+1280x720, three frames; one in each tensor-core mode), plus the correspondence maps of a fused batch of
+uneven sessions.
 
 Before every frame the GPU session is put into the oracle's state (Theta, Phi, the LM damping lambda of
 R14, through trk_session_import) and both run that frame in lockstep (tests/sequence.py): at every
@@ -114,6 +115,21 @@ def test_config2_tensor_core_modes_match_the_oracle(prec):
         for f, (d, (th, phi, lam)) in enumerate(zip(frames, starts)):
             res = seq.follow_frame(o, s, d, th, phi, lam, frames_done=f)
             _check_frame(res, f"cfg2 prec {prec} frame {f}")
+
+
+@pytest.mark.parametrize("prec", [trk.PRECISION_TF32X3, trk.PRECISION_BF16X3])
+def test_config3_tensor_core_modes_match_the_oracle(prec):
+    """The high-resolution case (200k vertices / 1280x720, the largest [J r] row count) with J^T J and
+    J^T r on the tensor cores: its first frame, from the perturbed start, in lockstep with the oracle
+    and with the FP32 tolerances (all joints, all vertices, every iteration's energy, the LM
+    decisions)."""
+    m = synth.make_model(3, precision=prec)
+    o = oracle.Oracle(m)
+    d = synth.add_noise(o.render(synth.gt_theta(m, 0.0), synth.gt_offsets(m, 0.0)), 3, np.random.default_rng(13))
+    th, phi, lam = synth.start_theta(m), np.zeros((o.V, 3), np.float32), m["params"]["lambda_k0"]
+    with trk.Session(m) as s:
+        res = seq.follow_frame(o, s, d, th, phi, lam, frames_done=0)
+    _check_frame(res, f"cfg3 prec {prec} frame 0")
 
 
 def test_free_running_paths_part_only_at_ties(cfg2_seq):
