@@ -310,6 +310,104 @@ def test_near_ties_are_flagged():
     assert run(1e-3) == (0, 0)
 
 
+def _facing_normal(p, s):
+    """A unit normal whose dot product with the view ray p is s |p| (s = sine of its angle to the plane
+    normal to the ray; negative: front-facing)."""
+    ph = p / np.linalg.norm(p)
+    e = np.cross(ph, [1.0, 0.0, 0.0])
+    e /= np.linalg.norm(e)
+    return math.sqrt(1.0 - s * s) * e + s * ph
+
+
+def test_visibility_flags_exactly_its_marginal_decisions():
+    # R7's decisions that an FP32 evaluation may take the other way are flagged marginal, and only those:
+    # the facing test within 1e-4 rad (|n.p| < 1e-4 |p|), the pixel rounding within 1e-3 px of a pixel
+    # edge, the depth test within 1e-5 m of Z + eps_vis, a pixel whose z-buffer winner is ambiguous.
+    # Camera fx = fy = 40, principal point (20, 20), depth 2: u = 20 x + 20, v = 20 y + 20; each case in a
+    # pixel of its own.
+    cases = []  # (p, n, nvalid, Z at its pixel or inf, ambiguous pixel, expected vis, expected marg)
+    def add(u, v, s=-1.0, z=2.0, Z=np.inf, amb=0, nvalid=1, vis=1, marg=0):
+        p = np.array([(u - 20.0) * z / 40.0, (v - 20.0) * z / 40.0, z])
+        cases.append((p, _facing_normal(p, s), nvalid, Z, amb, vis, marg))
+    add(5, 5)                                  # plain front-facing, pixel centre
+    add(7, 5, s=-0.7e-4, marg=1)               # facing within the band, front
+    add(9, 5, s=+0.7e-4, vis=0, marg=1)        # facing within the band, back
+    add(11, 5, s=-3e-4)                        # facing outside the band
+    add(13, 5, s=+3e-4, vis=0)                 # back-facing outside the band
+    add(15.4996, 5, marg=1)                    # 0.4 mpx below a pixel edge
+    add(17.5004, 5, marg=1)                    # 0.4 mpx above one
+    add(19.498, 5)                             # 2 mpx from it
+    add(5, 9.5004, marg=1)                     # the same in v
+    add(7, 9.498)
+    add(5, 13, z=2.0, Z=2.0 - 0.01 - 0.5e-5, vis=0, marg=1)   # 5 um behind Z + eps_vis
+    add(7, 13, z=2.0, Z=2.0 - 0.01 + 0.5e-5, vis=1, marg=1)   # 5 um in front of it
+    add(9, 13, z=2.0, Z=2.0 - 0.01 - 3e-5, vis=0)             # 30 um behind
+    add(11, 13, z=2.0, Z=2.0 - 0.01 + 3e-5, vis=1)            # 30 um in front
+    add(13, 13, z=2.0, Z=1.5, vis=0)                          # well behind an occluder
+    add(15, 13, Z=2.5, amb=1, marg=1)                         # ambiguous z-buffer winner
+    add(17, 13, Z=2.5)                                        # the same pixel state, unambiguous
+    add(5, 17, s=-0.7e-4, nvalid=0, vis=0)                    # no normal: never visible, never marginal
+    add(7, 17, z=0.04, vis=0)                                 # before the near plane
+    add(-0.6, 17, vis=0)                                      # rounds to pixel -1: outside the image
+    add(39.4, 17, vis=1)                                      # the last column
+    nV = len(cases)
+    verts = np.array([c[0] for c in cases])
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 1, 2]], [[0, 0, 0, 0]] * nV,
+                     [[1, 0, 0, 0]] * nV, W=40, H=40, fx=40.0, fy=40.0, cx=20.0, cy=20.0)
+    assert m["params"]["eps_vis"] == 0.01 and m["params"]["z_near"] == 0.05
+    o = oracle.Oracle(m)
+    z = np.full((40, 40), np.inf)
+    amb = np.zeros((40, 40), np.int32)
+    for p, _, _, Z, a, _, _ in cases:
+        if p[2] > 0.05:
+            u, v = 40.0 * p[0] / p[2] + 20.0, 40.0 * p[1] / p[2] + 20.0
+            k = (int(math.floor(v + 0.5)), int(math.floor(u + 0.5)))
+            if 0 <= k[0] < 40 and 0 <= k[1] < 40:
+                z[k], amb[k] = Z, a
+    n = np.array([c[1] for c in cases])
+    ok = np.array([c[2] for c in cases], np.int32)
+    vis, pix, marg = o.visibility(verts, n, ok, z, amb, with_marg=True)
+    assert list(vis) == [c[5] for c in cases]
+    assert list(marg) == [c[6] for c in cases]
+    assert (pix[vis == 0] == -1).all()
+    # without the flags the decisions are the same
+    vis2, pix2, _ = o.visibility(verts, n, ok, z, amb)
+    assert np.array_equal(vis, vis2) and np.array_equal(pix, pix2)
+
+
+def test_marginal_vertices_make_their_pixels_ties():
+    # A pixel is a tie where a marginal vertex (visible or not, its bucket one pixel beyond the window
+    # included) could be the argmin: within the cutoff + 1e-5 m and within 1e-5 m of the best distance.
+    # Camera fx = fy = 100, principal point (15, 15), window 1 (1 px = 2 cm at depth 2); the pixel (15, 15)
+    # at depth 2 has p = (0, 0, 2).
+    verts = np.array([[0.004, 0.0, 2.0],     # 0: visible, 4 mm from p: the argmin
+                      [0.0, 0.0035, 2.0],    # 1: marginal, hidden, nearer than 0
+                      [0.0, -0.006, 2.0],    # 2: marginal, 2 mm farther than 0
+                      [0.04, 0.0, 2.0]])     # 3: marginal, 2 px out (one beyond the window), 4 cm away
+    m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 1, 2]], [[0, 0, 0, 0]] * 4,
+                     [[1, 0, 0, 0]] * 4, W=31, H=31, fx=100.0, fy=100.0, cx=15.0, cy=15.0, window_half=1,
+                     cutoff=0.05)
+    o = oracle.Oracle(m)
+    depth = np.zeros((31, 31), np.float32)
+    depth[15, 15] = 2.0
+    pix = np.array([15 * 31 + 15, -1, -1, -1], np.int32)
+
+    def tie_at(vis, marg):
+        corr, _, _, tie = o.associate(verts, np.array(vis, np.int32), pix, depth, np.array(marg, np.int32),
+                                      with_tie=True)
+        return corr[15, 15], tie[15, 15]
+    assert tie_at([1, 0, 0, 0], [0, 0, 0, 0]) == (0, 0)
+    assert tie_at([1, 0, 0, 0], [0, 1, 0, 0]) == (0, 1)   # could be nearer than the argmin
+    assert tie_at([1, 0, 0, 0], [0, 0, 1, 0]) == (0, 0)   # farther than the argmin by more than 1e-5 m
+    assert tie_at([1, 0, 0, 0], [0, 0, 0, 1]) == (0, 0)
+    assert tie_at([1, 0, 0, 0], [1, 0, 0, 0]) == (0, 1)   # the argmin itself marginal
+    # no visible candidate: a marginal vertex within the cutoff makes the empty result a tie, also one
+    # whose bucket lies one pixel beyond the window
+    assert tie_at([0, 0, 0, 0], [0, 0, 0, 0]) == (-1, 0)
+    assert tie_at([0, 0, 0, 0], [0, 0, 1, 0]) == (-1, 1)
+    assert tie_at([0, 0, 0, 0], [0, 0, 0, 1]) == (-1, 1)
+
+
 def test_knn_equals_brute_force():
     m = synth.make_model(1, V=800)
     o = oracle.Oracle(m)

@@ -219,6 +219,37 @@ MUTANTS = [
     ("association: near-equal candidates not flagged as ties",
      "if (tie && d2nd <= tau + tol && d2nd - d1 < tol) tie[k] = 1;", "",
      [geo.test_near_ties_are_flagged]),
+    ("visibility: the facing decision never marginal",
+     "if (fabs(nd) < tol_facing * pl || ru < tol_px", "if (ru < tol_px",
+     [geo.test_visibility_flags_exactly_its_marginal_decisions]),
+    ("visibility: facing band an absolute 1e-4 m instead of 1e-4 |p|",
+     "if (fabs(nd) < tol_facing * pl ||", "if (fabs(nd) < tol_facing ||",
+     [geo.test_visibility_flags_exactly_its_marginal_decisions]),
+    ("visibility: pixel rounding marginal on one side of the edge only",
+     "|| ru < tol_px || ru > 1 - tol_px ||", "|| ru > 1 - tol_px ||",
+     [geo.test_visibility_flags_exactly_its_marginal_decisions]),
+    ("visibility: pixel rounding marginal in u only",
+     "|| rv < tol_px || rv > 1 - tol_px) marg[i] = 1;", ") marg[i] = 1;",
+     [geo.test_visibility_flags_exactly_its_marginal_decisions]),
+    ("visibility: the depth test never marginal",
+     "if (marg && ((isfinite(Z) && fabs(p[2] - (Z + m->p.eps_vis)) < tol_m) || (zamb && zamb[k]))) marg[i] = 1;",
+     "if (marg && zamb && zamb[k]) marg[i] = 1;",
+     [geo.test_visibility_flags_exactly_its_marginal_decisions]),
+    ("visibility: an ambiguous z-buffer pixel not marginal",
+     "|| (zamb && zamb[k]))) marg[i] = 1;", ")) marg[i] = 1;",
+     [geo.test_visibility_flags_exactly_its_marginal_decisions]),
+    ("visibility: every vertex flagged marginal",
+     "    if (marg) marg[i] = 0;\n", "    if (marg) marg[i] = 1;\n",
+     [geo.test_visibility_flags_exactly_its_marginal_decisions]),
+    ("association: marginal vertices not looked for one pixel beyond the window",
+     "for (int qx = px - R - 1; qx <= px + R + 1; ++qx) {", "for (int qx = px - R; qx <= px + R; ++qx) {",
+     [geo.test_marginal_vertices_make_their_pixels_ties]),
+    ("association: a marginal vertex makes a tie at any distance",
+     "if (dist <= tau + tol && (best < 0 || dist <= sqrt(bd2) + tol)) tie[k] = 1;", "if (dist <= tau + tol) tie[k] = 1;",
+     [geo.test_marginal_vertices_make_their_pixels_ties]),
+    ("association: marginal vertices ignored by the tie flags",
+     "if (tie && mstart) {", "if (0) {",
+     [geo.test_marginal_vertices_make_their_pixels_ties]),
     ("frame: shape iterations without re-association (R18)",
      "    associate_pass(m, &w, depth);\n    energy[m->p.pose_iters + s]", "    energy[m->p.pose_iters + s]",
      [opt.test_frame_is_the_schedule_of_its_steps]),
