@@ -95,3 +95,17 @@ def random_tree(rng, L=6, prism_every=3):
     offs = [rng.uniform(-0.3, 0.3, 3) for _ in range(L)]
     offs[0] = np.array([0.0, 0.0, 2.0])
     return parent, jtype, axis, offs
+
+
+def assert_free_running_offsets(phi, phi_ref):
+    """Offsets of a free-running GPU frame against the oracle's.  The two paths may part at a
+    correspondence tie (a pixel whose two nearest vertices lie within ~1e-7 m of each other goes to the
+    other vertex); the shape step of those vertices then sees that pixel's offset p_k - v_i move from one
+    to the other: at most the pixel's distance to them (about half a mesh edge: ~1 cm at 5k vertices,
+    ~4 mm at 50k) shared with the vertex's other pixels and damped by the offset regularisers.  So: the
+    99th percentile within 0.05 mm, at most 0.5 % of the vertices beyond it, none beyond 6 mm (about one
+    pixel footprint at 3 m and 525 px, a third of one at 2.5 m and 140 px)."""
+    d = np.abs(np.asarray(phi, np.float64) - np.asarray(phi_ref, np.float64)).max(axis=1)
+    assert np.percentile(d, 99) < 5e-5, np.percentile(d, 99)
+    assert (d > 5e-5).mean() <= 5e-3, (d > 5e-5).sum()
+    assert d.max() < 6e-3, d.max()

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from paper_1711_07999_gb300 import synth
+from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
@@ -196,17 +197,7 @@ def test_render_depth_matches_oracle(cfg1):
         assert np.array_equal(s.read(f), before), f
 
 
-def _assert_offsets_close(phi, phi_ref):
-    """Free-running offsets.  The frame-by-frame lockstep tests (test_gpu_sequence.py) hold every vertex
-    to 0.05 mm; here the two paths may part at a correspondence tie (a pixel whose two nearest vertices
-    lie within ~1e-7 m of each other goes to the other vertex), and the shape step of the vertices around
-    such a pixel then sees a residual that differs by that pixel's offset: up to about one pixel
-    footprint (< 2.5 mm at 2.5 m and 140 px focal length, < 6 mm at 3 m and 525 px).  So: the 99th
-    percentile within 0.05 mm, at most 0.5 % of the vertices beyond it, none beyond 6 mm."""
-    d = np.abs(phi - phi_ref).max(axis=1)
-    assert np.percentile(d, 99) < 5e-5, np.percentile(d, 99)
-    assert (d > 5e-5).mean() <= 5e-3, (d > 5e-5).sum()
-    assert d.max() < 6e-3, d.max()
+_assert_offsets_close = H.assert_free_running_offsets
 
 
 def _track_both(m, o, depth, th0, frames=1):
