@@ -61,6 +61,7 @@ def test_raster_equals_brute_force_ray_casting(seed):
         tris.append([3 * f, 3 * f + 1, 3 * f + 2])
     v = np.array(verts)
     z, zt, amb = oracle.raster(W, Hh, fx, fy, cx, cy, 0.05, v, tris, with_amb=True)
+    assert amb.sum() <= 3
     for py in range(Hh):
         for px in range(W):
             d = np.array([(px - cx) / fx, (py - cy) / fy, 1.0])
@@ -70,12 +71,33 @@ def test_raster_equals_brute_force_ray_casting(seed):
                 if t is not None and t < best:
                     best, bt = t, f
             if amb[py, px]:
-                continue  # coverage decided at rounding level
+                continue  # coverage decided at rounding level (flagged pixels: a handful at most)
             if bt < 0:
                 assert not np.isfinite(z[py, px])
             else:
                 assert z[py, px] == pytest.approx(best, rel=1e-12)
                 assert zt[py, px] == bt
+
+
+def test_zbuffer_flags_exactly_the_pixels_on_an_edge():
+    # R6: a pixel centre within 1e-3 px of a triangle's edge (on the triangle's side of the other two
+    # edges) has a coverage that rounding decides, and is flagged ambiguous; no other pixel is.  Camera
+    # fx = fy = 20, principal point (10, 10), depth 2: u = 10 x + 10.  The triangle's corners project to
+    # (5, 5), (15, 5), (5, 15), shifted by `off` pixels in u and v.
+    def amb_at(off, corners=((5.0, 5.0), (15.0, 5.0), (5.0, 15.0))):
+        uv = np.array(corners) + off
+        v = np.array([[(u - 10.0) / 10.0, (w - 10.0) / 10.0, 2.0] for u, w in uv])
+        _, _, amb = oracle.raster(20, 20, 20.0, 20.0, 10.0, 10.0, 0.05, v, [[0, 1, 2]], with_amb=True)
+        return {(int(px), int(py)) for py, px in zip(*np.nonzero(amb))}
+    edges = ({(px, 5) for px in range(5, 16)} | {(5, py) for py in range(5, 16)}
+             | {(px, 20 - px) for px in range(5, 16)})
+    assert len(edges) == 30
+    assert amb_at(0.0) == edges        # the centres on the edges and corners
+    assert amb_at(0.0005) == edges     # 0.5 mpx from them (0.7 mpx from the slanted edge)
+    assert amb_at(0.005) == set()      # 5 mpx from them
+    # corners (5, 5), (10, 8), (15, 15): the line of the edge (5, 5)-(10, 8) passes the centre (15, 11)
+    # inside the bounding box but beyond the corner, outside the triangle: not flagged
+    assert amb_at(0.0, ((5.0, 5.0), (10.0, 8.0), (15.0, 15.0))) == {(k, k) for k in range(5, 16)} | {(10, 8)}
 
 
 def test_fronto_parallel_quad_has_constant_depth():

@@ -250,6 +250,19 @@ MUTANTS = [
     ("association: marginal vertices ignored by the tie flags",
      "if (tie && mstart) {", "if (0) {",
      [geo.test_marginal_vertices_make_their_pixels_ties]),
+    ("z-buffer: every pixel of the bounding box flagged ambiguous",
+     "if (near0 || near1 || near2) amb[k] = 1;", "amb[k] = 1;",
+     [geo.test_zbuffer_flags_exactly_the_pixels_on_an_edge, geo.test_raster_equals_brute_force_ray_casting]),
+    ("z-buffer: edge band of 1e-2 px",
+     "double tol = 1e-3;\n", "double tol = 1e-2;\n",
+     [geo.test_zbuffer_flags_exactly_the_pixels_on_an_edge]),
+    ("z-buffer: one edge never ambiguous",
+     "if (near0 || near1 || near2) amb[k] = 1;", "if (near0 || near1) amb[k] = 1;",
+     [geo.test_zbuffer_flags_exactly_the_pixels_on_an_edge]),
+    ("z-buffer: an edge line flagged beyond the triangle",
+     "int near2 = d2 < tol && (w0 * area >= -tol * lbc * fabs(area)) && (w1 * area >= -tol * lca * fabs(area));",
+     "int near2 = d2 < tol;",
+     [geo.test_zbuffer_flags_exactly_the_pixels_on_an_edge]),
     ("frame: shape iterations without re-association (R18)",
      "    associate_pass(m, &w, depth);\n    energy[m->p.pose_iters + s]", "    energy[m->p.pose_iters + s]",
      [opt.test_frame_is_the_schedule_of_its_steps]),
