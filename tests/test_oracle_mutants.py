@@ -263,6 +263,19 @@ MUTANTS = [
      "int near2 = d2 < tol && (w0 * area >= -tol * lbc * fabs(area)) && (w1 * area >= -tol * lca * fabs(area));",
      "int near2 = d2 < tol;",
      [geo.test_zbuffer_flags_exactly_the_pixels_on_an_edge]),
+    ("raster-ID: a corner at the cutoff not a tie",
+     "          if (fabs(dist[c] - tau) < tol) tie[k] = 1;\n", "",
+     [rid.test_ties_are_flagged]),
+    ("raster-ID: equidistant corners not a tie",
+     "if (fabs(dist[c] - dist[e]) < tol && fmin(dist[c], dist[e]) <= tau + tol) tie[k] = 1;", ";",
+     [rid.test_ties_are_flagged]),
+    ("raster-ID: equidistant corners a tie beyond the cutoff too",
+     "if (fabs(dist[c] - dist[e]) < tol && fmin(dist[c], dist[e]) <= tau + tol) tie[k] = 1;",
+     "if (fabs(dist[c] - dist[e]) < tol) tie[k] = 1;",
+     [rid.test_ties_are_flagged]),
+    ("raster-ID: an ambiguous z-buffer pixel not a tie",
+     "if (tie) tie[k] = zamb ? zamb[k] : 0;", "if (tie) tie[k] = 0;",
+     [rid.test_ties_are_flagged]),
     ("frame: shape iterations without re-association (R18)",
      "    associate_pass(m, &w, depth);\n    energy[m->p.pose_iters + s]", "    energy[m->p.pose_iters + s]",
      [opt.test_frame_is_the_schedule_of_its_steps]),

@@ -87,3 +87,33 @@ def test_equidistant_corners_go_to_the_smaller_index():
     corr, _, cnt, _ = o.associate_rid(v, ztri, depth)
     assert corr[15, 15] == 0 and cnt[0] == 1 and cnt[1] == 0
 
+
+
+def test_ties_are_flagged():
+    # The raster-ID map is compared with the GPU's except where its decision is a rounding-level one:
+    # two corners within 1e-5 m of each other (within the cutoff), a corner within 1e-5 m of the cutoff,
+    # or a pixel whose z-buffer winner is ambiguous.  p = (0, 0, 2) as above; corner 0 is 14.14 mm away.
+    def flags(dx1, cutoff, amb=0):
+        verts = np.array([[-0.01, -0.01, 2.0], [0.01 + dx1, -0.01, 2.0], [0.0, 0.02, 2.0]])
+        m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 2, 1]], [[0, 0, 0, 0]] * 3,
+                         [[1, 0, 0, 0]] * 3, W=31, H=31, fx=100.0, fy=100.0, cx=15.0, cy=15.0, cutoff=cutoff)
+        o = oracle.Oracle(m)
+        v = verts.astype(np.float64)
+        _, ztri, _ = o.raster(v)
+        assert ztri[15, 15] == 0
+        depth = np.zeros((31, 31), np.float32)
+        depth[15, 15] = 2.0
+        zamb = np.zeros((31, 31), np.int32)
+        zamb[15, 15] = amb
+        corr, _, _, tie = o.associate_rid(v, ztri, depth, zamb=zamb, with_tie=True)
+        assert tie.sum() == tie[15, 15]  # only the one pixel with a depth can be flagged
+        return int(corr[15, 15]), int(tie[15, 15])
+    d0 = float(np.hypot(0.01, 0.01))
+    assert flags(0.0, 0.05) == (0, 1)           # corners 0 and 1 equidistant
+    assert flags(4e-6, 0.05) == (0, 1)          # 2.8 um apart
+    assert flags(1e-3, 0.05) == (0, 0)          # 0.7 mm apart
+    assert flags(1e-3, d0 + 5e-6) == (0, 1)     # corner 0 5 um inside the cutoff
+    assert flags(1e-3, d0 - 5e-6) == (-1, 1)    # 5 um outside it
+    assert flags(1e-3, d0 + 5e-5) == (0, 0)     # 50 um inside it
+    assert flags(1e-3, 0.05, amb=1) == (0, 1)   # an ambiguous z-buffer pixel
+    assert flags(0.0, 0.01) == (-1, 0)          # equidistant corners both beyond the cutoff
