@@ -492,8 +492,9 @@ void orc_visibility(void* h, const double* v, const double* n, const int32_t* nv
 /* Sec. 4.1 projective association.  Each valid pixel back-projects to p_k; the closest visible vertex
  * whose bucket lies in the (2W+1)^2 window, within the cutoff, is its correspondence (R8, R9).
  * acc_i = sum over assigned pixels of (p_k - v_i), cnt_i = their number (the average gives p~_i).
- * tie (optional): 1 where the decision is within 1e-5 m of another outcome, or involves a vertex whose
- * visibility / bucket is marginal (marg from orc_visibility). */
+ * tie (optional): 1 where the decision is within 1e-5 m of another outcome (the nearest two candidates, or
+ * the nearest one and the cutoff), or involves a vertex whose visibility / bucket is marginal (marg from
+ * orc_visibility) and that could be the nearest. */
 void orc_associate(void* h, const double* v, const int32_t* vis, const int32_t* pix, const int32_t* marg,
                    const float* depth, int32_t* corr, double* acc, int32_t* cnt, int32_t* tie) {
   orc_model* m = (orc_model*)h;
@@ -550,7 +551,6 @@ void orc_associate(void* h, const double* v, const int32_t* vis, const int32_t* 
             double dd = dx * dx + dy * dy + dz * dz;
             double dist = sqrt(dd);
             if (dist < d1) { d2nd = d1; d1 = dist; } else if (dist < d2nd) { d2nd = dist; }
-            if (tie && fabs(dist - tau) < tol) tie[k] = 1;
             if (dd <= tau2 && (best < 0 || dd < bd2 || (dd == bd2 && i < best))) { best = i; bd2 = dd; }
           }
         }
@@ -571,7 +571,10 @@ void orc_associate(void* h, const double* v, const int32_t* vis, const int32_t* 
           }
         }
       }
+      /* the outcome is a rounding-level one where the nearest two candidates are within tol of each other, or
+       * the nearest one is within tol of the cutoff (a farther candidate's cutoff decision cannot change it) */
       if (tie && d2nd <= tau + tol && d2nd - d1 < tol) tie[k] = 1;
+      if (tie && fabs(d1 - tau) < tol) tie[k] = 1;
       corr[k] = best;
       if (best >= 0) {
         acc[3 * best] += p[0] - v[3 * best];

@@ -332,6 +332,27 @@ def test_near_ties_are_flagged():
     assert run(1e-3) == (0, 0)
 
 
+def test_cutoff_ties_are_those_of_the_nearest_candidate():
+    # The cutoff can change a pixel's correspondence only through its nearest candidate: a pixel is a tie
+    # where that candidate lies within 1e-5 m of the cutoff (5 cm), not where a farther one does.
+    def run(d_near, d_far):
+        verts = np.array([[d_near, 0.0, 2.0], [0.0, d_far, 2.0], [0.0, 0.3, 2.0]])
+        m = H.make_model([-1], [0], [[0, 0, 1]], [[0, 0, 0]], verts, [[0, 2, 1]], [[0, 0, 0, 0]] * 3,
+                         [[1, 0, 0, 0]] * 3, W=31, H=31, fx=100.0, fy=100.0, cx=15.0, cy=15.0, window_half=5,
+                         cutoff=0.05)
+        o = oracle.Oracle(m)
+        depth = np.zeros((31, 31), np.float32)
+        depth[15, 15] = 2.0
+        corr, _, _, tie = o.associate(verts, np.array([1, 1, 0], np.int32),
+                                      np.array([15 * 31 + 15, 17 * 31 + 15, -1], np.int32), depth, with_tie=True)
+        return int(corr[15, 15]), int(tie[15, 15])
+    assert run(0.004, 0.05) == (0, 0)           # a farther candidate exactly at the cutoff
+    assert run(0.004, 0.05 + 3e-6) == (0, 0)    # ... or just beyond it
+    assert run(0.05 - 5e-6, 0.2) == (0, 1)      # the nearest 5 um inside the cutoff
+    assert run(0.05 + 5e-6, 0.2) == (-1, 1)     # 5 um beyond it
+    assert run(0.05 - 5e-5, 0.2) == (0, 0)      # 50 um inside it
+
+
 def _facing_normal(p, s):
     """A unit normal whose dot product with the view ray p is s |p| (s = sine of its angle to the plane
     normal to the ray; negative: front-facing)."""

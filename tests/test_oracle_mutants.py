@@ -276,6 +276,12 @@ MUTANTS = [
     ("raster-ID: an ambiguous z-buffer pixel not a tie",
      "if (tie) tie[k] = zamb ? zamb[k] : 0;", "if (tie) tie[k] = 0;",
      [rid.test_ties_are_flagged]),
+    ("association: a farther candidate at the cutoff makes a tie",
+     "if (tie && fabs(d1 - tau) < tol) tie[k] = 1;", "if (tie && fabs(d2nd - tau) < tol) tie[k] = 1;",
+     [geo.test_cutoff_ties_are_those_of_the_nearest_candidate]),
+    ("association: the nearest candidate at the cutoff not a tie",
+     "if (tie && fabs(d1 - tau) < tol) tie[k] = 1;", "",
+     [geo.test_cutoff_ties_are_those_of_the_nearest_candidate]),
     ("frame: shape iterations without re-association (R18)",
      "    associate_pass(m, &w, depth);\n    energy[m->p.pose_iters + s]", "    energy[m->p.pose_iters + s]",
      [opt.test_frame_is_the_schedule_of_its_steps]),
